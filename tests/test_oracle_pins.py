@@ -1,0 +1,303 @@
+"""Pins of the CPU oracle against things other than itself (no GPU).
+
+Each test names the pin it implements: closed forms of the 2D Ising model
+(Onsager free energy, Yang magnetisation, nearest-neighbour correlation),
+brute-force enumeration and exact contraction of finite networks, exact special
+cases (D = 1 product states), and invariants of the projector construction.
+"""
+import numpy as np
+import pytest
+
+import ctm_synth as S
+from oracle import ctmrg, exact, ising
+
+HEIS = S.heisenberg_bond()
+
+
+# ------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("beta", [0.30, 0.40, 0.50, 0.60])
+def test_onsager_single_vs_double_integral(beta):
+    """The two textbook forms of Onsager's -beta f agree."""
+    assert abs(ising.onsager_lnz(beta) - ising.onsager_lnz_double(beta)) < 1e-12
+
+
+@pytest.mark.parametrize("beta", [0.30, 0.40, 0.50])
+def test_nn_correlation_is_half_the_energy_derivative(beta):
+    """<s s>_nn (elliptic-integral form) = (1/2) d(-beta f)/d beta."""
+    h = 3e-4
+    f = ising.onsager_lnz
+    d = (-f(beta + 2 * h) + 8 * f(beta + h) - 8 * f(beta - h) + f(beta - 2 * h)) / (12 * h)
+    assert abs(ising.nn_correlation(beta) - 0.5 * d) < 1e-9
+
+
+# ------------------------------------------- Ising network vs enumeration
+
+@pytest.mark.parametrize("L", [3, 4])
+@pytest.mark.parametrize("beta", [0.30, 0.44])
+def test_ising_network_equals_enumeration(L, beta):
+    """P9: contracting the a-network on an L x L torus gives the brute-force
+    partition function."""
+    a = S.ising_tensor(beta)
+    z_net = exact.network_torus_z([[a] * L for _ in range(L)])
+    z_enum = exact.ising_torus_z_enum(L, beta)
+    assert abs(z_net / z_enum - 1) < 1e-13
+
+
+@pytest.mark.parametrize("sites", [[(1, 1)], [(1, 1), (2, 1)], [(0, 0), (2, 3)]])
+def test_ising_impurity_equals_enumeration(sites):
+    """P9: impurity tensors give the brute-force spin correlations."""
+    beta, L = 0.41, 4
+    a, b = S.ising_tensor(beta), S.ising_tensor(beta, impurity=True)
+    grid = [[a] * L for _ in range(L)]
+    imp = [list(row) for row in grid]
+    for (x, y) in sites:
+        imp[y][x] = b
+    ratio = exact.network_torus_z(imp) / exact.network_torus_z(grid)
+    assert abs(ratio - exact.ising_torus_corr_enum(L, beta, sites)) < 1e-13
+
+
+# --------------------------------------------------- CTM vs closed forms
+
+def _ising_ctm(beta, chi, method, seed=1, rounds=2):
+    ket, bra = S.classical_as_ket(S.ising_tensor(beta))
+    C, T = S.initial_env(1, 1, chi, 2, 1, seed=seed)
+    N, k = 2 * chi, min(chi + 5, 2 * chi)
+    X0, W0 = S.initial_rangefinders(1, 1, N, k, seed=2)
+    return ctmrg.CTM(1, 1, [ket], [bra], C, T, chi, method=method, p=5,
+                     si_rounds=rounds, X0=X0, W0=W0)
+
+
+@pytest.mark.parametrize("method", ["svd", "si"])
+def test_ctm_onsager_beta040(method):
+    """P1: free energy and nearest-neighbour correlation at beta = 0.40,
+    chi = 27, both projector constructions."""
+    beta = 0.40
+    ctm = _ising_ctm(beta, 27, method)
+    ctm.converge(1e-11, 300)
+    assert abs(ctm.free_energy() - ising.onsager_lnz(beta)) < 1e-11
+    imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)
+    for direction in (0, 1):
+        ss = ctm.bond_ratio(0, 0, direction, imp, imp)
+        assert abs(ss - ising.nn_correlation(beta)) < 1e-9
+    assert abs(ctm.site_ratio(0, 0, imp)) < 1e-4      # disordered phase: m -> 0
+
+
+@pytest.mark.parametrize("method", ["svd", "si"])
+def test_ctm_yang_beta050(method):
+    """P2: spontaneous magnetisation (Yang) at beta = 0.50, chi = 27."""
+    beta = 0.50
+    ctm = _ising_ctm(beta, 27, method)
+    ctm.converge(1e-11, 300)
+    imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)
+    assert abs(abs(ctm.site_ratio(0, 0, imp)) - ising.yang_m(beta)) < 1e-10
+    assert abs(ctm.free_energy() - ising.onsager_lnz(beta)) < 1e-12
+    assert abs(ctm.bond_ratio(0, 0, 0, imp, imp) - ising.nn_correlation(beta)) < 1e-10
+
+
+def _gauge_cell(beta, Lx, Ly, seed=7):
+    """Ising network on an Lx x Ly cell with a random invertible matrix on
+    every bond (G on one end, G^-1 on the other): a different tensor on every
+    site, the same infinite network."""
+    rng = np.random.default_rng(seed)
+    a, b = S.ising_tensor(beta), S.ising_tensor(beta, impurity=True)
+    Gh = [[np.eye(2) + 0.3 * rng.standard_normal((2, 2)) for _ in range(Lx)] for _ in range(Ly)]
+    Gv = [[np.eye(2) + 0.3 * rng.standard_normal((2, 2)) for _ in range(Lx)] for _ in range(Ly)]
+    kets, imps = [], []
+    for y in range(Ly):
+        for x in range(Lx):
+            gr = Gh[y][x]                                   # right leg of (x,y)
+            gl = np.linalg.inv(Gh[y][(x - 1) % Lx])        # left leg
+            gd = Gv[y][x]                                   # down leg
+            gu = np.linalg.inv(Gv[(y - 1) % Ly][x])        # up leg
+            tr = lambda t: np.einsum("uldr,Uu,Ll,dD,rR->ULDR", t, gu, gl, gd, gr)
+            kets.append(tr(a).reshape(1, 2, 2, 2, 2))
+            imps.append(tr(b).reshape(1, 2, 2, 2, 2))
+    return kets, imps
+
+
+def test_ctm_gauge_transformed_unit_cell():
+    """P1/P2 on a 3x2 cell with distinct tensors on every site: <s> at every
+    site equals Yang's m and <s s> on every bond equals the closed form, so
+    every site and bond of the unit-cell bookkeeping is exercised."""
+    beta, Lx, Ly, chi = 0.50, 3, 2, 12
+    kets, imps = _gauge_cell(beta, Lx, Ly)
+    bras = [np.ones((1, 1, 1, 1, 1))] * (Lx * Ly)
+    C, T = S.initial_env(Lx, Ly, chi, 2, 1, seed=1)
+    N, k = 2 * chi, chi + 5
+    X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, seed=2)
+    ctm = ctmrg.CTM(Lx, Ly, kets, bras, C, T, chi, method="si", p=5,
+                    si_rounds=1, X0=X0, W0=W0)
+    ctm.converge(1e-10, 200)
+    m = ising.yang_m(beta)
+    ms = [ctm.site_ratio(x, y, imps[y * Lx + x]) for y in range(Ly) for x in range(Lx)]
+    assert max(abs(abs(v) - m) for v in ms) < 1e-8
+    assert max(ms) * min(ms) > 0                       # one phase everywhere
+    ss = ising.nn_correlation(beta)
+    for y in range(Ly):
+        for x in range(Lx):
+            i = y * Lx + x
+            ir = y * Lx + (x + 1) % Lx
+            idn = ((y + 1) % Ly) * Lx + x
+            assert abs(ctm.bond_ratio(x, y, 0, imps[i], imps[ir]) - ss) < 1e-8
+            assert abs(ctm.bond_ratio(x, y, 1, imps[i], imps[idn]) - ss) < 1e-8
+
+
+# ------------------------------------------------- exact finite growth
+
+def _growth(method, kets, bras, chi0, Dk, Db, niter, cplx):
+    C, T = S.initial_env(1, 1, chi0, Dk, Db, complex_=cplx, seed=3)
+    C0 = [c[0].copy() for c in C]
+    T0 = [t[0].copy() for t in T]
+    ctm = ctmrg.CTM(1, 1, kets, bras, C, T, chi=10 ** 6, method=method, p=5,
+                    cutoff=0.0, normalize=False)
+    for _ in range(niter):
+        ctm.iteration()
+    return ctm, C0, T0
+
+
+@pytest.mark.parametrize("method", ["svd", "si"])
+def test_exact_growth_quantum(method):
+    """P3: with no truncation (k = chi + p >= N, projectors exact) and no
+    normalisation, one iteration of four moves turns the boundary ring into
+    the exact 3x3 patch: Z and the two-site density matrices (both
+    directions) equal a brute-force contraction of that finite network."""
+    A = S.ipeps_tensors(1, 1, 2, 2, complex_=True, seed=11)
+    B = [a.conj() for a in A]
+    ctm, C0, T0 = _growth(method, A, B, 2, 2, 2, 1, True)
+    z_ex = exact.finite_patch(C0, T0, A[0], B[0], 3, 3)
+    assert abs(ctm.z_one_site() / z_ex - 1) < 1e-9
+    for direction, (pw, ph), sites in ((0, (4, 3), ((1, 1), (2, 1))),
+                                       (1, (3, 4), ((1, 1), (1, 2)))):
+        R = exact.finite_patch(C0, T0, A[0], B[0], pw, ph, open_sites=sites)
+        R = R.reshape(4, 4)
+        R = R / np.trace(R)
+        assert np.abs(ctm.rdm2(0, 0, direction) - R).max() < 1e-9
+
+
+@pytest.mark.parametrize("method", ["svd", "si"])
+def test_exact_growth_classical_two_iterations(method):
+    """P3: a positive random classical network grown for two iterations
+    from a chi = 1 boundary equals the exact 5x5 patch."""
+    rng = np.random.default_rng(5)
+    ket, bra = S.classical_as_ket(np.abs(rng.standard_normal((2, 2, 2, 2))) + 0.1)
+    ctm, C0, T0 = _growth(method, [ket], [bra], 1, 2, 1, 2, False)
+    z_ex = exact.finite_patch(C0, T0, ket, bra, 5, 5)
+    assert abs(ctm.z_one_site() / z_ex - 1) < 1e-8
+
+
+# ------------------------------------------------------ product states
+
+@pytest.mark.parametrize("method", ["svd", "si"])
+def test_product_states_unit_cell(method):
+    """P4: a D = 1 product state on a 3x2 cell (distinct random phi per site)
+    is contracted exactly; chi = 4 > 1 exercises the s^-1/2 cutoff. The one-
+    site density matrices are |phi><phi| and every bond energy S.S equals
+    <S>_i . <S>_j."""
+    Lx, Ly, chi = 3, 2, 4
+    A = S.product_state_tensors(Lx, Ly, seed=4)
+    B = [a.conj() for a in A]
+    C, T = S.initial_env(Lx, Ly, chi, 1, 1, complex_=True, seed=1)
+    X0, W0 = S.initial_rangefinders(Lx, Ly, chi, chi, complex_=True, seed=2)
+    ctm = ctmrg.CTM(Lx, Ly, A, B, C, T, chi, method=method, p=5, X0=X0, W0=W0)
+    for _ in range(3):
+        ctm.iteration()
+    ops = S.spin_ops()
+    phis = [a.reshape(2) for a in A]
+    svec = [np.array([np.vdot(p, o @ p).real for o in ops]) for p in phis]
+    for y in range(Ly):
+        for x in range(Lx):
+            i = y * Lx + x
+            assert np.abs(ctm.rdm1(x, y) - np.outer(phis[i], phis[i].conj())).max() < 1e-12
+            for direction, j in ((0, y * Lx + (x + 1) % Lx), (1, ((y + 1) % Ly) * Lx + x)):
+                e = ctm.expect2(HEIS, x, y, direction)
+                assert abs(e - svec[i] @ svec[j]) < 1e-12
+
+
+# ------------------------------------------------------------ invariants
+
+def _random_cell(method, Lx=2, Ly=2, D=2, chi=10, cplx=True, rounds=1, seed=21):
+    A = S.ipeps_tensors(Lx, Ly, 2, D, complex_=cplx, seed=seed)
+    B = [a.conj() for a in A]
+    C, T = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx, seed=1)
+    N = chi * D * D
+    X0, W0 = S.initial_rangefinders(Lx, Ly, N, min(chi + 5, N), complex_=cplx, seed=2)
+    return ctmrg.CTM(Lx, Ly, A, B, C, T, chi, method=method, p=5,
+                     si_rounds=rounds, X0=X0, W0=W0)
+
+
+@pytest.mark.parametrize("method", ["svd", "si"])
+def test_projectors_are_oblique_inverses(method):
+    """P5: P_r P_l = I_chi for every cut of every move."""
+    ctm = _random_cell(method)
+    for _ in range(2):
+        ctm.iteration()
+    assert len(ctm.last) == 4 * 4
+    for d in ctm.last.values():
+        err = np.abs(d["Pr"] @ d["Pl"] - np.eye(d["Pl"].shape[1])).max()
+        assert err < 1e-10
+
+
+def test_si_projectors_depend_only_on_spans():
+    """P6: replacing X by X Qx and W by W Qw (random unitaries) leaves the
+    projectors and the recycled bases unchanged."""
+    ctm = _random_cell("si")
+    ctm.iteration()
+    f = ctmrg.Frame(2, 2, 0)
+    Q = ctm.cut_corners(f, 0, 0)
+    X, W = ctm.rf[(0, 0)]
+    rng = np.random.default_rng(3)
+    k = X.shape[1]
+    Qx = np.linalg.qr(rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k)))[0]
+    Qw = np.linalg.qr(rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k)))[0]
+    a = ctmrg.projectors_si(*Q, X, W, ctm.chi, 1)
+    b = ctmrg.projectors_si(*Q, X @ Qx, W @ Qw, ctm.chi, 1)
+    for i in (0, 1, 3, 4):
+        assert np.abs(a[i] - b[i]).max() / np.abs(a[i]).max() < 1e-10
+
+
+def test_si_converges_to_svd_fixed_point():
+    """P7: with a gapped spectrum SI-CTMRG and standard CTMRG reach the same
+    fixed point: corner spectra, bond energies and, with the sign fix, the
+    corners themselves agree element-wise up to one phase per tensor."""
+    res = {}
+    for method in ("svd", "si"):
+        ctm = _random_cell(method, Lx=1, Ly=1, D=2, chi=12, cplx=False, rounds=2, seed=4)
+        it, delta = ctm.converge(1e-13, 400)
+        assert delta < 1e-12
+        res[method] = ctm
+    a, b = res["svd"], res["si"]
+    for lab in range(4):
+        sa = a.spectra()[lab][0]
+        sb = b.spectra()[lab][0]
+        assert np.abs(sa - sb).max() < 1e-10
+        # element-wise up to one overall phase per tensor (normalising C and
+        # T leaves that phase to the history of the iteration)
+        ca, cb = a.C[lab][0], b.C[lab][0]
+        ph = np.vdot(cb, ca) / abs(np.vdot(cb, ca))
+        assert np.abs(ca - ph * cb).max() < 1e-8
+    for direction in (0, 1):
+        assert abs(a.expect2(HEIS, 0, 0, direction) - b.expect2(HEIS, 0, 0, direction)) < 1e-10
+    assert max(d["sin2"] for d in b.last.values()) < 1e-12
+
+
+def test_unit_cell_of_identical_tensors_repeats_the_single_site_move():
+    """Column bookkeeping: on a 2x2 cell of identical tensors and identical
+    environments, one left move (two column steps) equals two left moves of
+    the 1x1 cell, column by column (standard projectors)."""
+    A = S.ipeps_tensors(1, 1, 2, 2, complex_=False, seed=8)
+    B = [a.conj() for a in A]
+    chi = 6
+    C, T = S.initial_env(1, 1, chi, 2, 2, seed=1)
+    one = ctmrg.CTM(1, 1, A, B, C, T, chi, method="svd")
+    C4 = [[C[l][0]] * 4 for l in range(4)]
+    T4 = [[T[l][0]] * 4 for l in range(4)]
+    cell = ctmrg.CTM(2, 2, A * 4, B * 4, C4, T4, chi, method="svd")
+    cell.left_move(0)
+    one.left_move(0)
+    first = [one.C[l][0].copy() for l in range(4)]
+    one.left_move(0)
+    for y in range(2):
+        for lab in (0, 3):
+            assert np.abs(cell.C[lab][y * 2 + 1] - first[lab]).max() < 1e-12
+            assert np.abs(cell.C[lab][y * 2 + 0] - one.C[lab][0]).max() < 1e-12
