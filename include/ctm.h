@@ -1,0 +1,186 @@
+/*
+ * ctm.h -- C ABI of the GB300 (sm_103a) SI-CTMRG library (libctm.so).
+ *
+ * Contracts an infinite square-lattice tensor network (the norm of an iPEPS,
+ * or a classical network such as the 2D Ising model) with the corner transfer
+ * matrix renormalisation group, building the truncation projectors either by
+ * subspace iteration (SI-CTMRG: "QR-based projector", steps 1-4 of Zhang &
+ * Corboz, arXiv 2607.15158) or, for comparison, by the standard truncated SVD
+ * of the effective environment M (paper section "Standard CTMRG").
+ *
+ * Conventions
+ *   - Unit cell of Lx x Ly sites; site index i = y * Lx + x.
+ *   - On-site ket tensor A[s][u][l][d][r] (physical, up, left, down, right),
+ *     row-major; bra tensor B of the same shape with bond Db. For an iPEPS
+ *     B = conj(A) (pass bra = NULL); for a classical network a[u][l][d][r]
+ *     use ctm_init_network (d = 1, Db = 1, B = 1).
+ *   - Corners C_i[prev][next] (chi x chi) and edges T_i[prev][next][ket][bra]
+ *     (chi x chi x Dk x Db), legs ordered along the clockwise ring
+ *     C1 T1 C2 T2 C3 T3 C4 T4 (C1 upper-left, T1 up, C2 upper-right, T2 right,
+ *     C3 lower-right, T3 down, C4 lower-left, T4 left). Host arrays of all
+ *     corners are laid out [label 0..3][site][chi][chi], edges
+ *     [label][site][chi][chi][Dk][Db].
+ *   - Rangefinders X (columns in M's column space) and W = Y^dagger (M's row
+ *     space), N x k each with N = chi*Dk*Db, k = min(chi + p, N), laid out
+ *     [direction 0..3][cut][N][k]; cut = upper-left site of the 2x2 block in
+ *     the frame of that direction.
+ *   - Real data is double; complex data is interleaved (re, im) double pairs.
+ *
+ * Ownership and errors
+ *   - Every input is copied; the caller keeps its buffers. Outputs are written
+ *     to caller buffers (host memory unless stated).
+ *   - Calls are synchronous on the context's stream and never abort. Argument
+ *     errors are reported before any device work. A failed call returns a
+ *     status and leaves a message readable with ctm_last_error().
+ *   - Device-side iterations (Jacobi sweeps, Cholesky) are bounded; running
+ *     out of sweeps returns CTM_ENOCONV, a non-positive pivot CTM_ENUMERIC.
+ */
+#ifndef CTM_H
+#define CTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctm_ctx ctm_ctx;
+
+typedef enum {
+  CTM_OK = 0,
+  CTM_EINVAL = 1,       /* bad argument or call order */
+  CTM_ENOMEM = 2,       /* device allocation failed */
+  CTM_ECUDA = 3,        /* CUDA runtime or launch error */
+  CTM_ENOCONV = 4,      /* iteration budget exhausted (not fatal) */
+  CTM_ETIMEOUT = 5,     /* device wait budget exhausted */
+  CTM_ENUMERIC = 6,     /* breakdown: non-positive Cholesky pivot, NaN */
+  CTM_EUNSUPPORTED = 7  /* configuration not supported by this build */
+} ctm_status;
+
+typedef enum { CTM_F64 = 0, CTM_C128 = 1 } ctm_dtype;
+
+/* Arithmetic of the large contractions. FP64: every product in double.
+ * SPLIT_BF16: corner x block products and enlarged-corner / absorption
+ * contractions as sums of bf16 slice products on the tensor cores with fp32
+ * accumulation and fp64 reduction; QR, small SVD and s^-1/2 stay fp64. */
+typedef enum { CTM_PREC_FP64 = 0, CTM_PREC_SPLIT_BF16 = 1 } ctm_prec;
+
+typedef enum { CTM_LEFT = 0, CTM_UP = 1, CTM_RIGHT = 2, CTM_DOWN = 3 } ctm_dir;
+
+/* Projector construction: subspace iteration (QR-based projector) or the
+ * standard truncated SVD of M (comparison baseline). */
+typedef enum { CTM_PROJ_SI = 0, CTM_PROJ_SVD = 1 } ctm_method;
+
+typedef struct {
+  int p;                  /* oversampling, k = chi + p (paper: p = 5) */
+  int si_rounds;          /* subspace-iteration rounds per projector */
+  ctm_method method;      /* CTM_PROJ_SI or CTM_PROJ_SVD */
+  ctm_prec prec;          /* arithmetic of the large contractions */
+  double svd_rel_cutoff;  /* s^-1/2 := 0 for s_i <= cutoff * s_1 */
+  int normalize;          /* divide C, T by their Frobenius norm per move */
+  int sign_fix;           /* fix the phase of every singular vector */
+  uint64_t seed;          /* seed of the default random C, T, X, W */
+  void* stream;           /* cudaStream_t to run on, NULL = a private stream */
+} ctm_opts;
+
+/* Defaults: p = 5, si_rounds = 1, SI, FP64, cutoff 1e-14, normalize = 1,
+ * sign_fix = 1, seed = 0, stream = NULL. */
+void ctm_default_opts(ctm_opts* opts);
+
+/* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz
+ * and the double layer of Eq. double_layer; End Matter for Lx x Ly cells).
+ * A: Lx*Ly host pointers to A[d][D][D][D][D] (dtype elements). bra: NULL for
+ * conj(A), else Lx*Ly host pointers to B of the same shape. The environment
+ * and rangefinders start from seeded random normal draws (replace them with
+ * ctm_set_env / ctm_set_rangefinders). Returns CTM_EINVAL for Lx, Ly, d, D,
+ * chi < 1, CTM_ENOMEM when the state does not fit on the device. */
+ctm_status ctm_init(ctm_ctx** out, int Lx, int Ly, const void* const* A,
+                    const void* const* bra, ctm_dtype dtype, int d, int D,
+                    int chi, const ctm_opts* opts);
+
+/* Create a context for a classical network: a[u][l][d][r] real, bond k, one
+ * tensor per site (Lx*Ly host pointers). Edges have shape chi x chi x k x 1. */
+ctm_status ctm_init_network(ctm_ctx** out, int Lx, int Ly,
+                            const double* const* a, int k, int chi,
+                            const ctm_opts* opts);
+
+/* Replace the environment: C [4][Lx*Ly][chi][chi], T [4][Lx*Ly][chi][chi][Dk][Db]
+ * (host, dtype of the context). */
+ctm_status ctm_set_env(ctm_ctx* ctx, const void* C, const void* T);
+
+/* Copy the environment out (same layouts as ctm_set_env). */
+ctm_status ctm_get_env(ctm_ctx* ctx, void* C, void* T);
+
+/* Replace the raw rangefinder blocks X, W ([4][Lx*Ly][N][k], host); they are
+ * orthonormalised on their first use (QR of a Gaussian block, step 1). */
+ctm_status ctm_set_rangefinders(ctm_ctx* ctx, const void* X, const void* W);
+
+/* Query N = chi*Dk*Db and k = min(chi + p, N). */
+ctm_status ctm_dims(const ctm_ctx* ctx, int* N, int* k);
+
+/* One directional move over the whole cell (End Matter, left move; up /
+ * right / down are the left move of the cell turned by 1 / 2 / 3
+ * counter-clockwise quarter turns): column by column, the projectors of all
+ * cuts of a column are built, then C1, T4, C4 of the next column are
+ * absorbed, truncated and normalised. */
+ctm_status ctm_move(ctm_ctx* ctx, ctm_dir dir);
+
+/* Iterations of the four moves (left, up, right, down) until the
+ * corner-spectrum change Delta < tol or max_iter; Delta = max over corners
+ * and sites of ||s_new - s_old||_2 of unit-normalised spectra. Returns
+ * CTM_ENOCONV (not fatal) when max_iter is reached. */
+ctm_status ctm_converge(ctm_ctx* ctx, double tol, int max_iter,
+                        int* iters_out, double* delta_out);
+
+/* Normalised singular values (descending, unit 2-norm) of corner C_label
+ * (label 1..4) at site (x, y); s_out has chi entries. */
+ctm_status ctm_spectrum(ctm_ctx* ctx, int x, int y, int label, double* s_out);
+
+/* Two-site expectation <O> = Tr(O rho) / Tr(rho) on the bond from (x, y) to
+ * its right (dir = 0) or lower (dir = 1) neighbour; op is d^2 x d^2,
+ * row-major O[(s1', s2')][(s1, s2)] (row = bra), dtype of the context; site 1
+ * is (x, y). out = (re, im). */
+ctm_status ctm_expect(ctm_ctx* ctx, const void* op, int x, int y, int dir,
+                      double out[2]);
+
+/* Two-site reduced density matrix rho[(s1 s2)][(t1 t2)] (ket, bra), trace 1,
+ * complex (re, im) pairs, d^4 entries. */
+ctm_status ctm_rdm2(ctm_ctx* ctx, int x, int y, int dir, double* rho_out);
+
+/* Ratio Z(ket at (x,y) replaced by imp) / Z on the one-site patch; imp has the
+ * ket's shape and dtype. For a classical network with an impurity tensor this
+ * is the local observable (e.g. the Ising magnetisation). */
+ctm_status ctm_expect_site(ctm_ctx* ctx, const void* imp, int x, int y,
+                           double out[2]);
+
+/* Ratio Z(kets at both ends of the bond replaced) / Z on the two-site patch
+ * (e.g. a nearest-neighbour spin correlation of a classical network). */
+ctm_status ctm_expect_bond(ctm_ctx* ctx, const void* imp1, const void* imp2,
+                           int x, int y, int dir, double out[2]);
+
+/* ln kappa per site of a 1x1 cell, kappa = Z1 Z0 / (Z13 Z24): one-site patch,
+ * four corners, corners with T1-T3 joined, corners with T2-T4 joined
+ * (-beta f for a classical partition function). CTM_EINVAL for larger cells. */
+ctm_status ctm_free_energy(ctm_ctx* ctx, double* ln_kappa);
+
+/* The projectors of the last move in direction dir for cut (x, y) of that
+ * direction's frame: P_l (N x chi) and P_r^dagger (N x chi), host, dtype of
+ * the context. */
+ctm_status ctm_get_projectors(ctm_ctx* ctx, ctm_dir dir, int x, int y,
+                              void* Pl, void* PrH);
+
+/* Device milliseconds of the last ctm_move / ctm_converge call and the
+ * number of kernels it launched. */
+ctm_status ctm_last_timing(const ctm_ctx* ctx, double* ms, long* launches);
+
+void ctm_free(ctm_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed creation when
+ * ctx is NULL); owned by the library, valid until the next call. */
+const char* ctm_last_error(const ctm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTM_H */

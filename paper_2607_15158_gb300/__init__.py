@@ -1,0 +1,260 @@
+"""Python binding of libctm, the GB300 SI-CTMRG library (C ABI in include/ctm.h).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name; all contraction work runs in the library's CUDA kernels. Inputs are
+numpy arrays (or anything ``np.ascontiguousarray`` accepts) in host memory; the
+library copies them. Loading fails loudly when the library has not been built
+(``python -m paper_2607_15158_gb300.build``): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libctm.so")
+
+CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENOCONV, CTM_ETIMEOUT, \
+    CTM_ENUMERIC, CTM_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["CTM_OK", "CTM_EINVAL", "CTM_ENOMEM", "CTM_ECUDA", "CTM_ENOCONV",
+                "CTM_ETIMEOUT", "CTM_ENUMERIC", "CTM_EUNSUPPORTED"]
+CTM_F64, CTM_C128 = 0, 1
+CTM_PREC_FP64, CTM_PREC_SPLIT_BF16 = 0, 1
+CTM_LEFT, CTM_UP, CTM_RIGHT, CTM_DOWN = 0, 1, 2, 3
+CTM_PROJ_SI, CTM_PROJ_SVD = 0, 1
+
+
+class ctm_opts(C.Structure):
+    _fields_ = [("p", C.c_int), ("si_rounds", C.c_int), ("method", C.c_int),
+                ("prec", C.c_int), ("svd_rel_cutoff", C.c_double),
+                ("normalize", C.c_int), ("sign_fix", C.c_int),
+                ("seed", C.c_uint64), ("stream", C.c_void_p)]
+
+
+class CTMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libctm.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libctm.so not built ({LIB_PATH}); run "
+                          "`python -m paper_2607_15158_gb300.build` on a machine with nvcc")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, VP = C.POINTER, C.c_int, C.c_double, C.c_void_p
+    ctx_p = VP
+    sig = {
+        "ctm_default_opts": (None, [P(ctm_opts)]),
+        "ctm_init": (I, [P(ctx_p), I, I, P(VP), P(VP), I, I, I, I, P(ctm_opts)]),
+        "ctm_init_network": (I, [P(ctx_p), I, I, P(VP), I, I, P(ctm_opts)]),
+        "ctm_set_env": (I, [ctx_p, VP, VP]),
+        "ctm_get_env": (I, [ctx_p, VP, VP]),
+        "ctm_set_rangefinders": (I, [ctx_p, VP, VP]),
+        "ctm_dims": (I, [ctx_p, P(I), P(I)]),
+        "ctm_move": (I, [ctx_p, I]),
+        "ctm_converge": (I, [ctx_p, D, I, P(I), P(D)]),
+        "ctm_spectrum": (I, [ctx_p, I, I, I, P(D)]),
+        "ctm_expect": (I, [ctx_p, VP, I, I, I, P(D)]),
+        "ctm_rdm2": (I, [ctx_p, I, I, I, P(D)]),
+        "ctm_expect_site": (I, [ctx_p, VP, I, I, P(D)]),
+        "ctm_expect_bond": (I, [ctx_p, VP, VP, I, I, I, P(D)]),
+        "ctm_free_energy": (I, [ctx_p, P(D)]),
+        "ctm_get_projectors": (I, [ctx_p, I, I, I, VP, VP]),
+        "ctm_last_timing": (I, [ctx_p, P(D), P(C.c_long)]),
+        "ctm_free": (None, [ctx_p]),
+        "ctm_last_error": (C.c_char_p, [ctx_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(lib, ctx, st, allow=()):
+    if st != CTM_OK and st not in allow:
+        raise CTMError(st, (lib.ctm_last_error(ctx) or b"").decode())
+    return st
+
+
+def _host(a, cplx):
+    return np.ascontiguousarray(a, dtype=np.complex128 if cplx else np.float64)
+
+
+def ctm_default_opts(**kw):
+    lib = load()
+    o = ctm_opts()
+    lib.ctm_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """Owns one ctm_ctx; methods are the C entry points of the same names."""
+
+    def __init__(self, ptr, Lx, Ly, d, Dk, Db, chi, cplx):
+        self.ptr = ptr
+        self.Lx, self.Ly, self.d, self.Dk, self.Db, self.chi = Lx, Ly, d, Dk, Db, chi
+        self.cplx = cplx
+        self.lib = load()
+        Nv, kv = C.c_int(), C.c_int()
+        _check(self.lib, self.ptr, self.lib.ctm_dims(self.ptr, C.byref(Nv), C.byref(kv)))
+        self.N, self.k = Nv.value, kv.value
+
+    # -- lifetime
+    def ctm_free(self):
+        if self.ptr:
+            self.lib.ctm_free(self.ptr)
+            self.ptr = None
+
+    close = ctm_free
+
+    def __del__(self):
+        try:
+            self.ctm_free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.ctm_free()
+
+    @property
+    def dtype(self):
+        return np.complex128 if self.cplx else np.float64
+
+    # -- state
+    def ctm_set_env(self, Cs, Ts):
+        """Cs: [4][S][chi][chi], Ts: [4][S][chi][chi][Dk][Db] (nested lists or arrays)."""
+        c = _host(np.asarray(Cs), self.cplx)
+        t = _host(np.asarray(Ts), self.cplx)
+        _check(self.lib, self.ptr, self.lib.ctm_set_env(self.ptr, c.ctypes.data, t.ctypes.data))
+
+    def ctm_get_env(self):
+        S = self.Lx * self.Ly
+        c = np.empty((4, S, self.chi, self.chi), self.dtype)
+        t = np.empty((4, S, self.chi, self.chi, self.Dk, self.Db), self.dtype)
+        _check(self.lib, self.ptr, self.lib.ctm_get_env(self.ptr, c.ctypes.data, t.ctypes.data))
+        return c, t
+
+    def ctm_set_rangefinders(self, X, W):
+        x = _host(np.asarray(X), self.cplx)
+        w = _host(np.asarray(W), self.cplx)
+        _check(self.lib, self.ptr,
+               self.lib.ctm_set_rangefinders(self.ptr, x.ctypes.data, w.ctypes.data))
+
+    # -- iteration
+    def ctm_move(self, direction):
+        _check(self.lib, self.ptr, self.lib.ctm_move(self.ptr, int(direction)))
+
+    def ctm_converge(self, tol, max_iter):
+        it, delta = C.c_int(), C.c_double()
+        st = self.lib.ctm_converge(self.ptr, float(tol), int(max_iter), C.byref(it),
+                                   C.byref(delta))
+        _check(self.lib, self.ptr, st, allow=(CTM_ENOCONV,))
+        return it.value, delta.value, st == CTM_OK
+
+    # -- observables
+    def ctm_spectrum(self, x, y, label):
+        s = np.empty(self.chi)
+        _check(self.lib, self.ptr, self.lib.ctm_spectrum(
+            self.ptr, x, y, label, s.ctypes.data_as(C.POINTER(C.c_double))))
+        return s
+
+    def ctm_expect(self, op, x, y, direction):
+        o = _host(op, self.cplx)
+        out = np.empty(2)
+        _check(self.lib, self.ptr, self.lib.ctm_expect(
+            self.ptr, o.ctypes.data, x, y, direction, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return complex(out[0], out[1])
+
+    def ctm_rdm2(self, x, y, direction):
+        d2 = self.d * self.d
+        out = np.empty((d2, d2, 2))
+        _check(self.lib, self.ptr, self.lib.ctm_rdm2(
+            self.ptr, x, y, direction, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def ctm_expect_site(self, imp, x, y):
+        o = _host(imp, self.cplx)
+        out = np.empty(2)
+        _check(self.lib, self.ptr, self.lib.ctm_expect_site(
+            self.ptr, o.ctypes.data, x, y, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return complex(out[0], out[1])
+
+    def ctm_expect_bond(self, imp1, imp2, x, y, direction):
+        o1, o2 = _host(imp1, self.cplx), _host(imp2, self.cplx)
+        out = np.empty(2)
+        _check(self.lib, self.ptr, self.lib.ctm_expect_bond(
+            self.ptr, o1.ctypes.data, o2.ctypes.data, x, y, direction,
+            out.ctypes.data_as(C.POINTER(C.c_double))))
+        return complex(out[0], out[1])
+
+    def ctm_free_energy(self):
+        v = C.c_double()
+        _check(self.lib, self.ptr, self.lib.ctm_free_energy(self.ptr, C.byref(v)))
+        return v.value
+
+    def ctm_get_projectors(self, direction, x, y):
+        Pl = np.empty((self.N, self.chi), self.dtype)
+        PrH = np.empty((self.N, self.chi), self.dtype)
+        _check(self.lib, self.ptr, self.lib.ctm_get_projectors(
+            self.ptr, int(direction), x, y, Pl.ctypes.data, PrH.ctypes.data))
+        return Pl, PrH
+
+    def ctm_last_timing(self):
+        ms, n = C.c_double(), C.c_long()
+        _check(self.lib, self.ptr, self.lib.ctm_last_timing(self.ptr, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+
+def ctm_init(Lx, Ly, A, d, D, chi, cplx=None, bra=None, opts=None):
+    """Create a context for an iPEPS cell: A is a list of Lx*Ly arrays
+    [d, D, D, D, D]; bra=None means conj(A)."""
+    lib = load()
+    if cplx is None:
+        cplx = any(np.iscomplexobj(a) for a in A)
+    arrs = [_host(a, cplx) for a in A]
+    ptrs = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    bptrs = None
+    if bra is not None:
+        barrs = [_host(b, cplx) for b in bra]
+        bptrs = (C.c_void_p * len(barrs))(*[b.ctypes.data for b in barrs])
+    o = opts if opts is not None else ctm_default_opts()
+    ptr = C.c_void_p()
+    st = lib.ctm_init(C.byref(ptr), Lx, Ly, ptrs, bptrs, CTM_C128 if cplx else CTM_F64, d, D,
+                      chi, C.byref(o))
+    _check(lib, None, st)
+    ctx = Context(ptr, Lx, Ly, d, D, D, chi, cplx)
+    ctx._keep = (arrs, o)
+    return ctx
+
+
+def ctm_init_network(Lx, Ly, a, chi, opts=None):
+    """Create a context for a classical network: a is a list of Lx*Ly real
+    arrays [k, k, k, k] (u, l, d, r)."""
+    lib = load()
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in a]
+    k = arrs[0].shape[0]
+    ptrs = (C.c_void_p * len(arrs))(*[x.ctypes.data for x in arrs])
+    o = opts if opts is not None else ctm_default_opts()
+    ptr = C.c_void_p()
+    st = lib.ctm_init_network(C.byref(ptr), Lx, Ly, ptrs, k, chi, C.byref(o))
+    _check(lib, None, st)
+    ctx = Context(ptr, Lx, Ly, 1, k, 1, chi, False)
+    ctx._keep = (arrs, o)
+    return ctx

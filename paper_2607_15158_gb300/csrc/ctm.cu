@@ -1,0 +1,1220 @@
+// libctm: SI-CTMRG on one GB300 -- context, move orchestration and C ABI.
+//
+// Paper: Zhang & Corboz, "Fast two-dimensional tensor-network contraction via
+// subspace iteration" (arXiv 2607.15158). Every step runs in this library's
+// kernels (permute.cu, gemm64.cu, linalg.cu, split_gemm.cu) on one stream;
+// the host only sequences them.
+//
+// Layout in HBM (one allocation per array, all row-major):
+//   ket / bra tensors, 4 rotations x sites      A[r][site][s][u][l][d][r]
+//   corners  C[label][site][chi][chi]
+//   edges    T[label][site][chi][chi][Dk][Db]
+//   rangefinders X, W[direction][cut][N][k]
+//   workspace: four enlarged corners Q[4][N][N], two pipeline buffers and a
+//   scratch arena for the permutes of the pairwise contractions, the N x k
+//   blocks of the subspace iteration and the k x k small problem.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ctm.h"
+#include "kernels.h"
+#include "split_gemm.h"
+
+using namespace ctm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Tn {
+  void* p = nullptr;
+  int r = 0;
+  long d[8] = {0};
+  long size() const {
+    long s = 1;
+    for (int i = 0; i < r; ++i) s *= d[i];
+    return s;
+  }
+};
+
+Tn tn(void* p, std::initializer_list<long> dims) {
+  Tn t;
+  t.p = p;
+  for (long x : dims) t.d[t.r++] = x;
+  return t;
+}
+
+struct StatusError {
+  ctm_status st;
+  std::string msg;
+};
+
+}  // namespace
+
+struct ctm_ctx {
+  int Lx = 0, Ly = 0, S = 0, d = 0, Dk = 0, Db = 0, chi = 0, N = 0, k = 0;
+  bool cx = false;
+  size_t es = 8;
+  ctm_opts opts{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+  // tensors
+  void* ket[4] = {nullptr};  // [S][d Dk^4] per rotation
+  void* bra[4] = {nullptr};  // [S][d Db^4]
+  void* C = nullptr;         // [4][S][chi^2]
+  void* T = nullptr;         // [4][S][chi^2 Dk Db]
+  void* X = nullptr;         // [4][S][N k]
+  void* W = nullptr;
+  std::vector<char> rf_ready;
+  // workspace
+  void* Q[4] = {nullptr};
+  void* pipe[2] = {nullptr};
+  size_t pipe_elems = 0;
+  char* scratch = nullptr;
+  size_t scratch_bytes = 0, scratch_off = 0;
+  void* Pl = nullptr;        // [Lmax][N chi] current column
+  void* PrH = nullptr;
+  void* lastPl = nullptr;    // [S][N chi] of the last move
+  void* lastPrH = nullptr;
+  int last_dir = -1;
+  void* Z[4] = {nullptr};    // N x k blocks
+  void* Xn = nullptr;
+  void* Wn = nullptr;
+  void* G = nullptr;         // k x k
+  void* Linv = nullptr;
+  void* rho = nullptr;
+  void* u = nullptr;
+  void* v = nullptr;
+  void* jw = nullptr;        // Jacobi work, max(2 k^2, 8 S chi^2) elements
+  void* ph = nullptr;
+  void* Vs = nullptr;        // k x chi
+  void* Us = nullptr;
+  double* sv = nullptr;      // max(k, 4 S chi)
+  void* stC1 = nullptr;      // staging [Lmax][chi^2]
+  void* stC4 = nullptr;
+  void* stT4 = nullptr;      // [Lmax][chi^2 Dk Db]
+  double* spec_old = nullptr;  // [4 S][chi]
+  double* spec_new = nullptr;
+  double* dscal = nullptr;     // small device scalars
+  void* op = nullptr;          // d^4 operator
+  void* rho2 = nullptr;        // d^4 two-site density matrix
+  void* imp[2] = {nullptr};    // impurity kets
+  int* err = nullptr;
+  bool spectra_init = false;
+  // split-precision state
+  SplitCtx* split = nullptr;
+  // bookkeeping
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double last_ms = 0.0;
+  long launches = 0, last_launches = 0;
+  std::string msg;
+};
+
+namespace ctm {
+ctm_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line);
+}
+
+namespace {
+
+thread_local ctm_ctx* g_cur = nullptr;
+
+ctm_status fail(ctm_ctx* c, ctm_status st, const std::string& m) {
+  if (c) c->msg = m;
+  else g_create_error = m;
+  return st;
+}
+
+}  // namespace
+
+namespace ctm {
+ctm_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %s (%s) at %s:%d in %s", cudaGetErrorName(e),
+           cudaGetErrorString(e), file, line, expr);
+  if (g_cur) g_cur->msg = buf;
+  else g_create_error = buf;
+  return e == cudaErrorMemoryAllocation ? CTM_ENOMEM : CTM_ECUDA;
+}
+}  // namespace ctm
+
+#define CK(expr)                                \
+  do {                                          \
+    ctm_status st__ = (expr);                   \
+    if (st__ != CTM_OK) return st__;            \
+  } while (0)
+
+namespace {
+
+// ------------------------------------------------------------ helpers
+size_t elems_C(const ctm_ctx* c) { return (size_t)c->chi * c->chi; }
+size_t elems_T(const ctm_ctx* c) { return (size_t)c->chi * c->chi * c->Dk * c->Db; }
+size_t elems_ket(const ctm_ctx* c) { return (size_t)c->d * c->Dk * c->Dk * c->Dk * c->Dk; }
+size_t elems_bra(const ctm_ctx* c) { return (size_t)c->d * c->Db * c->Db * c->Db * c->Db; }
+
+char* at(void* base, size_t elems, const ctm_ctx* c) {
+  return static_cast<char*>(base) + elems * c->es;
+}
+
+ctm_status dalloc(ctm_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof buf, "device allocation of %zu bytes failed (%s)", bytes,
+             cudaGetErrorString(e));
+    return fail(c, CTM_ENOMEM, buf);
+  }
+  c->allocs.push_back(*p);
+  return CTM_OK;
+}
+
+// Frame of the cell after r counter-clockwise quarter turns: frame position
+// (x, y) -> original site; one turn sends site (x, y) to (y, -x mod Lx).
+int frame_site(const ctm_ctx* c, int r, int x, int y) {
+  const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
+  x = ((x % Lxf) + Lxf) % Lxf;
+  y = ((y % Lyf) + Lyf) % Lyf;
+  for (int k = r; k > 0; --k) {
+    const int lx_prev = ((k - 1) & 1) ? c->Ly : c->Lx;
+    const int nx = (((-y) % lx_prev) + lx_prev) % lx_prev;
+    y = x;
+    x = nx;
+  }
+  return y * c->Lx + x;
+}
+int frame_label(int r, int i) { return (i + r) & 3; }
+
+void* Cp(ctm_ctx* c, int label, int site) { return at(c->C, (size_t)(label * c->S + site) * elems_C(c), c); }
+void* Tp(ctm_ctx* c, int label, int site) { return at(c->T, (size_t)(label * c->S + site) * elems_T(c), c); }
+void* KETp(ctm_ctx* c, int rot, int site) { return at(c->ket[rot & 3], (size_t)site * elems_ket(c), c); }
+void* BRAp(ctm_ctx* c, int rot, int site) { return at(c->bra[rot & 3], (size_t)site * elems_bra(c), c); }
+
+// frame accessors
+void* fC(ctm_ctx* c, int r, int i, int x, int y) { return Cp(c, frame_label(r, i), frame_site(c, r, x, y)); }
+void* fT(ctm_ctx* c, int r, int i, int x, int y) { return Tp(c, frame_label(r, i), frame_site(c, r, x, y)); }
+
+void* scratch_alloc(ctm_ctx* c, size_t bytes) {
+  size_t off = (c->scratch_off + 255) & ~(size_t)255;
+  if (off + bytes > c->scratch_bytes) return nullptr;
+  c->scratch_off = off + bytes;
+  return c->scratch + off;
+}
+
+ctm_status gemm(ctm_ctx* c, GemmDesc& g) {
+  g.cx = c->cx;
+  const size_t wb = gemm64_work_bytes(g);
+  void* work = nullptr;
+  const size_t mark = c->scratch_off;
+  if (wb) {
+    work = scratch_alloc(c, wb);
+    if (!work) return fail(c, CTM_ENOMEM, "scratch arena too small for split-K partials");
+  }
+  CTM_CUDA_OK(gemm64(g, work, wb, c->stream, &c->launches));
+  c->scratch_off = mark;
+  return CTM_OK;
+}
+
+// ------------------------------------------------ pairwise contractions
+// out[lo] = sum over shared labels of A[la] B[lb] (conj on request): at most
+// one permute of each operand into a matrix view, one fp64 GEMM (or a dot
+// product for a scalar result), one permute of the result.
+ctm_status ein(ctm_ctx* c, const char* spec, const Tn& A, bool cA, const Tn& B, bool cB,
+               const Tn& out) {
+  std::string s(spec);
+  const size_t comma = s.find(','), arrow = s.find("->");
+  if (comma == std::string::npos || arrow == std::string::npos)
+    return fail(c, CTM_EINVAL, std::string("bad contraction spec ") + spec);
+  const std::string la = s.substr(0, comma), lb = s.substr(comma + 1, arrow - comma - 1),
+                    lo = s.substr(arrow + 2);
+  if ((int)la.size() != A.r || (int)lb.size() != B.r || (int)lo.size() != out.r)
+    return fail(c, CTM_EINVAL, std::string("rank mismatch in ") + spec);
+  long dim[128] = {0};
+  auto setdim = [&](char ch, long v) -> bool {
+    if (dim[(int)ch] && dim[(int)ch] != v) return false;
+    dim[(int)ch] = v;
+    return true;
+  };
+  for (int i = 0; i < A.r; ++i)
+    if (!setdim(la[i], A.d[i])) return fail(c, CTM_EINVAL, std::string("dim mismatch in ") + spec);
+  for (int i = 0; i < B.r; ++i)
+    if (!setdim(lb[i], B.d[i])) return fail(c, CTM_EINVAL, std::string("dim mismatch in ") + spec);
+  for (int i = 0; i < out.r; ++i)
+    if (!setdim(lo[i], out.d[i])) return fail(c, CTM_EINVAL, std::string("dim mismatch in ") + spec);
+  std::string fa, fb, ca, cb;
+  for (char ch : lo) {
+    const bool ia = la.find(ch) != std::string::npos, ib = lb.find(ch) != std::string::npos;
+    if (ia && ib) return fail(c, CTM_EINVAL, std::string("batch labels unsupported: ") + spec);
+    if (ia) fa += ch;
+    else if (ib) fb += ch;
+    else return fail(c, CTM_EINVAL, std::string("unknown output label in ") + spec);
+  }
+  for (char ch : la)
+    if (lb.find(ch) != std::string::npos && lo.find(ch) == std::string::npos) ca += ch;
+  for (char ch : lb)
+    if (la.find(ch) != std::string::npos && lo.find(ch) == std::string::npos) cb += ch;
+  for (char ch : la)
+    if (lo.find(ch) == std::string::npos && lb.find(ch) == std::string::npos)
+      return fail(c, CTM_EINVAL, std::string("traced label unsupported: ") + spec);
+  for (char ch : lb)
+    if (lo.find(ch) == std::string::npos && la.find(ch) == std::string::npos)
+      return fail(c, CTM_EINVAL, std::string("traced label unsupported: ") + spec);
+  long M = 1, Nn = 1, K = 1;
+  for (char ch : fa) M *= dim[(int)ch];
+  for (char ch : fb) Nn *= dim[(int)ch];
+  for (char ch : ca) K *= dim[(int)ch];
+  // layout options for a given contraction order
+  struct Plan { int opA, opB; bool permA, permB; std::string ordA, ordB; long cost; };
+  auto plan_for = [&](const std::string& co) {
+    Plan p{};
+    if (la == fa + co) { p.opA = OP_N; p.permA = false; }
+    else if (la == co + fa) { p.opA = OP_T; p.permA = false; }
+    else { p.opA = OP_N; p.permA = true; p.ordA = fa + co; }
+    if (lb == co + fb) { p.opB = OP_N; p.permB = false; }
+    else if (lb == fb + co) { p.opB = OP_T; p.permB = false; }
+    else { p.opB = OP_N; p.permB = true; p.ordB = co + fb; }
+    p.cost = (p.permA ? A.size() : 0) + (p.permB ? B.size() : 0);
+    return p;
+  };
+  Plan p1 = plan_for(ca), p2 = plan_for(cb);
+  Plan p = p2.cost < p1.cost ? p2 : p1;
+  const size_t mark = c->scratch_off;
+  const void* Am = A.p;
+  const void* Bm = B.p;
+  auto do_perm = [&](const Tn& X, const std::string& lx, const std::string& ord, bool conj,
+                     const void** dst) -> ctm_status {
+    void* buf = scratch_alloc(c, X.size() * c->es);
+    if (!buf) return fail(c, CTM_ENOMEM, std::string("scratch arena too small in ") + spec);
+    int perm[8];
+    for (int j = 0; j < X.r; ++j) perm[j] = (int)lx.find(ord[j]);
+    CTM_CUDA_OK(permute(X.p, buf, X.r, X.d, perm, c->cx, conj && c->cx, c->stream, &c->launches));
+    *dst = buf;
+    return CTM_OK;
+  };
+  bool conjA_in_gemm = false, conjB_in_gemm = false;
+  if (p.permA) CK(do_perm(A, la, p.ordA, cA, &Am));
+  else conjA_in_gemm = cA;
+  if (p.permB) CK(do_perm(B, lb, p.ordB, cB, &Bm));
+  else conjB_in_gemm = cB;
+  if (c->cx) {
+    if (conjA_in_gemm) p.opA = (p.opA == OP_T) ? OP_C : OP_R;
+    if (conjB_in_gemm) p.opB = (p.opB == OP_T) ? OP_C : OP_R;
+  }
+  const std::string want = fa + fb;
+  const bool final_perm = (want != lo);
+  void* Cm = out.p;
+  if (final_perm) {
+    Cm = scratch_alloc(c, (size_t)M * Nn * c->es);
+    if (!Cm) return fail(c, CTM_ENOMEM, std::string("scratch arena too small in ") + spec);
+  }
+  if (M == 1 && Nn == 1) {
+    // scalar: a dot product; both operands are in contraction order
+    if (p.opA == OP_R || p.opA == OP_C || p.opB == OP_R || p.opB == OP_C) {
+      // conjugation outside a permute: materialise it
+      if (p.opA == OP_R || p.opA == OP_C) CK(do_perm(tn((void*)Am, {K}), "k", "k", true, &Am));
+      if (p.opB == OP_R || p.opB == OP_C) CK(do_perm(tn((void*)Bm, {K}), "k", "k", true, &Bm));
+    }
+    const size_t wb = (size_t)304 * c->es;
+    void* w = scratch_alloc(c, wb);
+    if (!w) return fail(c, CTM_ENOMEM, "scratch arena too small for a dot product");
+    CTM_CUDA_OK(dot64(c->cx, false, K, Am, 0, Bm, 0, Cm, 1, w, wb, c->stream, &c->launches));
+  } else {
+    GemmDesc g;
+    g.opA = p.opA;
+    g.opB = p.opB;
+    g.M = M; g.N = Nn; g.K = K;
+    g.A = Am; g.lda = (p.opA == OP_N || p.opA == OP_R) ? K : M;
+    g.B = Bm; g.ldb = (p.opB == OP_N || p.opB == OP_R) ? Nn : K;
+    g.C = Cm; g.ldc = Nn;
+    CK(gemm(c, g));
+  }
+  if (final_perm) {
+    Tn tmp;
+    tmp.p = Cm;
+    tmp.r = (int)want.size();
+    for (int j = 0; j < tmp.r; ++j) tmp.d[j] = dim[(int)want[j]];
+    int perm[8];
+    for (int j = 0; j < out.r; ++j) perm[j] = (int)want.find(lo[j]);
+    CTM_CUDA_OK(permute(Cm, out.p, tmp.r, tmp.d, perm, c->cx, false, c->stream, &c->launches));
+  }
+  c->scratch_off = mark;
+  return CTM_OK;
+}
+
+// ------------------------------------------------------ enlarged corners
+// Q[(t,d,d'),(n,r,r')] = sum C[p,m] Ta[m,n,u,u'] Tb[t,p,l,l'] A[s,u,l,d,r]
+// B[s,u',l',d',r'] (paper Eq. rho_M_diag): corner i of the cut whose
+// upper-left frame position is (x, y) is this upper-left form applied to the
+// tensors turned by i more quarter turns.
+ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
+  const long chi = c->chi, Dk = c->Dk, Db = c->Db, d = c->d;
+  static const int dx[4] = {0, 1, 1, 0}, dy[4] = {0, 0, 1, 1};
+  const int sx = x + dx[i], sy = y + dy[i];
+  const int site = frame_site(c, r, sx, sy);
+  void* Cc = fC(c, r, i, sx, sy);
+  void* Tb = fT(c, r, (i + 3) & 3, sx, sy);
+  void* Ta = fT(c, r, i, sx, sy);
+  void* A = KETp(c, r + i, site);
+  void* B = BRAp(c, r + i, site);
+  Tn CT = tn(c->pipe[0], {chi, chi, Dk, Db});
+  CK(ein(c, "pm,mnuv->pnuv", tn(Cc, {chi, chi}), false, tn(Ta, {chi, chi, Dk, Db}), false, CT));
+  Tn CTT = tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db});
+  CK(ein(c, "tplw,pnuv->tlwnuv", tn(Tb, {chi, chi, Dk, Db}), false, CT, false, CTT));
+  Tn R1 = tn(c->pipe[0], {chi, Db, chi, Db, d, Dk, Dk});
+  CK(ein(c, "tlwnuv,sulde->twnvsde", CTT, false, tn(A, {d, Dk, Dk, Dk, Dk}), false, R1));
+  CK(ein(c, "twnvsde,svwDE->tdDneE", R1, false, tn(B, {d, Db, Db, Db, Db}), false,
+         tn(Qout, {chi, Dk, Db, chi, Dk, Db})));
+  return CTM_OK;
+}
+
+// ------------------------------------------------- subspace iteration
+// Y = op(Q) Z for an N x N corner and an N x k block.
+ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, void* Zout) {
+  if (c->opts.prec == CTM_PREC_SPLIT_BF16 && c->split) {
+    const ctm_status st = split_apply(c->split, Qm, herm, Zin, Zout, c->N, c->k, c->stream,
+                                      &c->launches);
+    if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+    return CTM_OK;
+  }
+  GemmDesc g;
+  g.opA = herm ? OP_C : OP_N;
+  g.opB = OP_N;
+  g.M = c->N; g.N = c->k; g.K = c->N;
+  g.A = Qm; g.lda = c->N;
+  g.B = Zin; g.ldb = c->k;
+  g.C = Zout; g.ldc = c->k;
+  return gemm(c, g);
+}
+
+// Orthonormal basis of span(Z) in place (N x k): shifted CholeskyQR followed
+// by two CholeskyQR passes (CholeskyQR3, Fukaya et al. 2020). Only the span
+// enters the projectors (paper step 1), so R is not kept.
+ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp) {
+  for (int pass = 0; pass < 3; ++pass) {
+    GemmDesc g;
+    g.opA = c->cx ? OP_C : OP_T;
+    g.opB = OP_N;
+    g.M = c->k; g.N = c->k; g.K = c->N;
+    g.A = Zm; g.lda = c->k;
+    g.B = Zm; g.ldb = c->k;
+    g.C = c->G; g.ldc = c->k;
+    CK(gemm(c, g));
+    CTM_CUDA_OK(chol_inv(c->cx, c->k, c->N, pass == 0, c->G, c->Linv, 1, c->err, c->stream,
+                         &c->launches));
+    GemmDesc h;
+    h.opA = OP_N;
+    h.opB = c->cx ? OP_C : OP_T;
+    h.M = c->N; h.N = c->k; h.K = c->k;
+    h.A = Zm; h.lda = c->k;
+    h.B = c->Linv; h.ldb = c->k;
+    h.C = tmp; h.ldc = c->k;
+    CK(gemm(c, h));
+    CTM_CUDA_OK(cudaMemcpyAsync(Zm, tmp, (size_t)c->N * c->k * c->es, cudaMemcpyDeviceToDevice,
+                                c->stream));
+  }
+  return CTM_OK;
+}
+
+ctm_status mm_small(ctm_ctx* c, int opA, int opB, long M, long Nn, long K, const void* A,
+                    long lda, const void* B, long ldb, void* Cm, long ldc) {
+  GemmDesc g;
+  g.opA = opA; g.opB = opB;
+  g.M = M; g.N = Nn; g.K = K;
+  g.A = A; g.lda = lda;
+  g.B = B; g.ldb = ldb;
+  g.C = Cm; g.ldc = ldc;
+  return gemm(c, g);
+}
+
+// SI projectors of one cut (paper "QR-based projector", steps 1-4): rounds of
+// X <- qr(M^H M X), W <- qr(M M^H W) with M = Q3 Q4 Q1 Q2 applied one corner
+// at a time; Z_R = Q1 Q2 X, Z_L = (Q3 Q4)^H W, rho = Z_L^H Z_R = u s v^H;
+// phases fixed on the columns of W u; P_l = Z_R v_chi s^-1/2,
+// P_r^H = Z_L u_chi s^-1/2; X <- X v, W <- W u.
+ctm_status si_projectors(ctm_ctx* c, int r, int cut, void* Pl, void* PrH) {
+  const size_t Nk = (size_t)c->N * c->k;
+  void* X = at(c->X, (size_t)(r * c->S + cut) * Nk, c);
+  void* W = at(c->W, (size_t)(r * c->S + cut) * Nk, c);
+  void** Q = c->Q;
+  void** Z = c->Z;
+  char& ready = c->rf_ready[r * c->S + cut];
+  if (!ready) {
+    CK(qr_inplace(c, X, Z[0]));
+    CK(qr_inplace(c, W, Z[0]));
+    ready = 1;
+  }
+  for (int round = 0; round < c->opts.si_rounds; ++round) {
+    CK(apply_corner(c, Q[1], false, X, Z[0]));
+    CK(apply_corner(c, Q[0], false, Z[0], Z[1]));
+    CK(apply_corner(c, Q[3], false, Z[1], Z[0]));
+    CK(apply_corner(c, Q[2], false, Z[0], Z[1]));
+    CK(apply_corner(c, Q[2], true, Z[1], Z[0]));
+    CK(apply_corner(c, Q[3], true, Z[0], Z[1]));
+    CK(apply_corner(c, Q[0], true, Z[1], Z[0]));
+    CK(apply_corner(c, Q[1], true, Z[0], X));
+    CK(qr_inplace(c, X, Z[0]));
+    CK(apply_corner(c, Q[2], true, W, Z[0]));
+    CK(apply_corner(c, Q[3], true, Z[0], Z[1]));
+    CK(apply_corner(c, Q[0], true, Z[1], Z[0]));
+    CK(apply_corner(c, Q[1], true, Z[0], Z[1]));
+    CK(apply_corner(c, Q[1], false, Z[1], Z[0]));
+    CK(apply_corner(c, Q[0], false, Z[0], Z[1]));
+    CK(apply_corner(c, Q[3], false, Z[1], Z[0]));
+    CK(apply_corner(c, Q[2], false, Z[0], W));
+    CK(qr_inplace(c, W, Z[0]));
+  }
+  // Z_R = Q1 (Q2 X) in Z[2], Z_L = Q4^H (Q3^H W) in Z[3]
+  CK(apply_corner(c, Q[1], false, X, Z[0]));
+  CK(apply_corner(c, Q[0], false, Z[0], Z[2]));
+  CK(apply_corner(c, Q[2], true, W, Z[0]));
+  CK(apply_corner(c, Q[3], true, Z[0], Z[3]));
+  const int k = c->k, chi = c->chi;
+  const int opH = c->cx ? OP_C : OP_T;
+  CK(mm_small(c, opH, OP_N, k, k, c->N, Z[3], k, Z[2], k, c->rho, k));
+  CTM_CUDA_OK(jacobi_svd(c->cx, k, c->rho, 0, c->sv, c->u, c->v, true, c->jw, 1, 80, c->err,
+                         c->stream, &c->launches));
+  CK(mm_small(c, OP_N, OP_N, c->N, k, k, X, k, c->v, k, c->Xn, k));
+  CK(mm_small(c, OP_N, OP_N, c->N, k, k, W, k, c->u, k, c->Wn, k));
+  if (c->opts.sign_fix) {
+    CTM_CUDA_OK(column_phase(c->cx, c->N, k, k, c->Wn, c->ph, 1, 0, c->stream, &c->launches));
+    CTM_CUDA_OK(scale_columns_conj(c->cx, c->N, k, k, c->Wn, c->ph, c->stream, &c->launches));
+    CTM_CUDA_OK(scale_columns_conj(c->cx, c->N, k, k, c->Xn, c->ph, c->stream, &c->launches));
+    CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, c->u, c->ph, c->stream, &c->launches));
+    CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, c->v, c->ph, c->stream, &c->launches));
+  }
+  CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, c->v, c->sv, c->opts.svd_rel_cutoff, c->Vs,
+                                c->stream, &c->launches));
+  CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, c->u, c->sv, c->opts.svd_rel_cutoff, c->Us,
+                                c->stream, &c->launches));
+  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, Z[2], k, c->Vs, chi, Pl, chi));
+  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, Z[3], k, c->Us, chi, PrH, chi));
+  CTM_CUDA_OK(cudaMemcpyAsync(X, c->Xn, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
+  CTM_CUDA_OK(cudaMemcpyAsync(W, c->Wn, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
+  return CTM_OK;
+}
+
+// -------------------------------------------------------------- absorb
+// New C1, T4, C4 of column x+1 (End Matter, left move): C1' = P_r (C1 T1)
+// with the projector of the cut above, C4' = (T3 C4) P_l with the one below,
+// T4' = P_r (T4 A B) P_l with the cut below (P_r) and above (P_l).
+ctm_status absorb_site(ctm_ctx* c, int r, int x, int y, int Lyf) {
+  const long chi = c->chi, Dk = c->Dk, Db = c->Db, d = c->d;
+  const size_t NC = (size_t)c->N * c->chi;
+  const int up = (y - 1 + Lyf) % Lyf, dn = y;
+  void* PrH_up = at(c->PrH, up * NC, c);
+  void* Pl_up = at(c->Pl, up * NC, c);
+  void* PrH_dn = at(c->PrH, dn * NC, c);
+  void* Pl_dn = at(c->Pl, dn * NC, c);
+  const int site = frame_site(c, r, x, y);
+  void* C1 = fC(c, r, 0, x, y);
+  void* T1 = fT(c, r, 0, x, y);
+  void* T3 = fT(c, r, 2, x, y);
+  void* C4 = fC(c, r, 3, x, y);
+  void* T4 = fT(c, r, 3, x, y);
+  void* A = KETp(c, r, site);
+  void* B = BRAp(c, r, site);
+  void* oC1 = at(c->stC1, (size_t)y * elems_C(c), c);
+  void* oC4 = at(c->stC4, (size_t)y * elems_C(c), c);
+  void* oT4 = at(c->stT4, (size_t)y * elems_T(c), c);
+  // C1'
+  Tn E1 = tn(c->pipe[0], {chi, chi, Dk, Db});
+  CK(ein(c, "pm,mnuv->pnuv", tn(C1, {chi, chi}), false, tn(T1, {chi, chi, Dk, Db}), false, E1));
+  CK(ein(c, "puva,pnuv->an", tn(PrH_up, {chi, Dk, Db, chi}), true, E1, false,
+         tn(oC1, {chi, chi})));
+  // C4'
+  Tn E4 = tn(c->pipe[0], {chi, chi, Dk, Db});
+  CK(ein(c, "tmdD,mn->tndD", tn(T3, {chi, chi, Dk, Db}), false, tn(C4, {chi, chi}), false, E4));
+  CK(ein(c, "tndD,ndDc->tc", E4, false, tn(Pl_dn, {chi, Dk, Db, chi}), false,
+         tn(oC4, {chi, chi})));
+  // T4'
+  Tn Y1 = tn(c->pipe[0], {chi, Dk, Db, Dk, Db, chi});
+  CK(ein(c, "tqlw,quvc->tlwuvc", tn(T4, {chi, chi, Dk, Db}), false,
+         tn(Pl_up, {chi, Dk, Db, chi}), false, Y1));
+  Tn R1 = tn(c->pipe[1], {chi, Db, Db, chi, d, Dk, Dk});
+  CK(ein(c, "tlwuvc,sulde->twvcsde", Y1, false, tn(A, {d, Dk, Dk, Dk, Dk}), false, R1));
+  Tn R2 = tn(c->pipe[0], {chi, Dk, Db, chi, Dk, Db});
+  CK(ein(c, "twvcsde,svwDE->tdDceE", R1, false, tn(B, {d, Db, Db, Db, Db}), false, R2));
+  CK(ein(c, "tdDa,tdDceE->aceE", tn(PrH_dn, {chi, Dk, Db, chi}), true, R2, false,
+         tn(oT4, {chi, chi, Dk, Db})));
+  return CTM_OK;
+}
+
+ctm_status check_err(ctm_ctx* c) {
+  int h = 0;
+  CTM_CUDA_OK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  if (h) {
+    CTM_CUDA_OK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    if (h & DEV_CHOL_PIVOT) return fail(c, CTM_ENUMERIC, "non-positive Cholesky pivot in CholeskyQR");
+    if (h & DEV_NONFINITE) return fail(c, CTM_ENUMERIC, "non-finite value in the small SVD");
+    if (h & DEV_MBAR_TIMEOUT) return fail(c, CTM_ETIMEOUT, "tensor-core pipeline wait gave up");
+    if (h & DEV_JACOBI_NOCONV) return fail(c, CTM_ENOCONV, "Jacobi SVD sweep budget exhausted");
+  }
+  return CTM_OK;
+}
+
+ctm_status move_impl(ctm_ctx* c, int r) {
+  const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
+  const size_t NC = (size_t)c->N * c->chi;
+  if (c->opts.method != CTM_PROJ_SI)
+    return fail(c, CTM_EUNSUPPORTED, "standard-SVD projectors are not built on the device");
+  for (int x = 0; x < Lxf; ++x) {
+    for (int y = 0; y < Lyf; ++y) {
+      for (int i = 0; i < 4; ++i) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
+      if (c->split) {
+        const ctm_status st = split_prepare_corners(c->split, c->Q, c->N, c->stream, &c->launches);
+        if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+      }
+      const int cut = y * Lxf + x;
+      CK(si_projectors(c, r, cut, at(c->Pl, y * NC, c), at(c->PrH, y * NC, c)));
+      CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPl, cut * NC, c), at(c->Pl, y * NC, c), NC * c->es,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPrH, cut * NC, c), at(c->PrH, y * NC, c),
+                                  NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    for (int y = 0; y < Lyf; ++y) CK(absorb_site(c, r, x, y, Lyf));
+    for (int y = 0; y < Lyf; ++y) {
+      void* dC1 = fC(c, r, 0, x + 1, y);
+      void* dT4 = fT(c, r, 3, x + 1, y);
+      void* dC4 = fC(c, r, 3, x + 1, y);
+      CTM_CUDA_OK(cudaMemcpyAsync(dC1, at(c->stC1, y * elems_C(c), c), elems_C(c) * c->es,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      CTM_CUDA_OK(cudaMemcpyAsync(dT4, at(c->stT4, y * elems_T(c), c), elems_T(c) * c->es,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      CTM_CUDA_OK(cudaMemcpyAsync(dC4, at(c->stC4, y * elems_C(c), c), elems_C(c) * c->es,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      if (c->opts.normalize) {
+        const size_t mark = c->scratch_off;
+        void* w = scratch_alloc(c, 152 * sizeof(double));
+        if (!w) return fail(c, CTM_ENOMEM, "scratch arena too small for the norms");
+        CTM_CUDA_OK(normalize(c->cx, elems_C(c), dC1, 0, 1, c->dscal, true, w, c->stream, &c->launches));
+        CTM_CUDA_OK(normalize(c->cx, elems_T(c), dT4, 0, 1, c->dscal, true, w, c->stream, &c->launches));
+        CTM_CUDA_OK(normalize(c->cx, elems_C(c), dC4, 0, 1, c->dscal, true, w, c->stream, &c->launches));
+        c->scratch_off = mark;
+      }
+    }
+  }
+  c->last_dir = r;
+  return CTM_OK;
+}
+
+ctm_status corner_spectra(ctm_ctx* c, double* out) {
+  // unnormalised singular values of all 4 S corners, [label][site][chi]
+  CTM_CUDA_OK(jacobi_svd(c->cx, c->chi, c->C, (long)elems_C(c), out, nullptr, nullptr, false,
+                         c->jw, 4 * c->S, 80, c->err, c->stream, &c->launches));
+  return CTM_OK;
+}
+
+void fill_normal(std::vector<double>& v, uint64_t seed, uint64_t stream_id, double scale) {
+  // splitmix64 counter stream -> Box-Muller normals (default initial state)
+  uint64_t ctr = seed * 0x9E3779B97F4A7C15ull + stream_id * 0xD1B54A32D192ED03ull;
+  auto next = [&]() {
+    uint64_t z = (ctr += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  for (size_t i = 0; i < v.size(); i += 2) {
+    const double u1 = next(), u2 = next();
+    const double rr = std::sqrt(-2.0 * std::log(u1));
+    v[i] = rr * std::cos(6.283185307179586 * u2) * scale;
+    if (i + 1 < v.size()) v[i + 1] = rr * std::sin(6.283185307179586 * u2) * scale;
+  }
+}
+
+ctm_status upload_default_state(ctm_ctx* c) {
+  const size_t per = c->cx ? 2 : 1;
+  const double sc = c->cx ? std::sqrt(0.5) : 1.0;
+  std::vector<double> h;
+  // corners and edges, each normalised to unit Frobenius norm
+  for (int kind = 0; kind < 2; ++kind) {
+    const size_t n = kind == 0 ? elems_C(c) : elems_T(c);
+    h.assign(n * per * 4 * c->S, 0.0);
+    fill_normal(h, c->opts.seed, 1 + kind, sc);
+    for (int t = 0; t < 4 * c->S; ++t) {
+      double s2 = 0.0;
+      for (size_t i = 0; i < n * per; ++i) s2 += h[t * n * per + i] * h[t * n * per + i];
+      const double inv = 1.0 / std::sqrt(s2);
+      for (size_t i = 0; i < n * per; ++i) h[t * n * per + i] *= inv;
+    }
+    CTM_CUDA_OK(cudaMemcpy(kind == 0 ? c->C : c->T, h.data(), h.size() * sizeof(double),
+                           cudaMemcpyHostToDevice));
+  }
+  const size_t nrf = (size_t)4 * c->S * c->N * c->k * per;
+  h.assign(nrf, 0.0);
+  fill_normal(h, c->opts.seed, 3, sc);
+  CTM_CUDA_OK(cudaMemcpy(c->X, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice));
+  fill_normal(h, c->opts.seed, 4, sc);
+  CTM_CUDA_OK(cudaMemcpy(c->W, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice));
+  std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
+  c->spectra_init = false;
+  return CTM_OK;
+}
+
+ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi, bool cx,
+                  const ctm_opts* opts, const void* const* kets, const void* const* bras,
+                  bool classical) {
+  if (!out) return fail(nullptr, CTM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (Lx < 1 || Ly < 1 || d < 1 || Dk < 1 || Db < 1 || chi < 1)
+    return fail(nullptr, CTM_EINVAL, "Lx, Ly, d, D and chi must be >= 1");
+  if (!kets) return fail(nullptr, CTM_EINVAL, "tensor pointers are NULL");
+  for (int i = 0; i < Lx * Ly; ++i)
+    if (!kets[i]) return fail(nullptr, CTM_EINVAL, "a tensor pointer is NULL");
+  ctm_ctx* c = new ctm_ctx();
+  g_cur = c;
+  c->Lx = Lx; c->Ly = Ly; c->S = Lx * Ly;
+  c->d = d; c->Dk = Dk; c->Db = Db; c->chi = chi; c->cx = cx;
+  c->es = cx ? 16 : 8;
+  if (opts) c->opts = *opts;
+  else ctm_default_opts(&c->opts);
+  if (c->opts.p < 0 || c->opts.si_rounds < 0) {
+    delete c;
+    g_cur = nullptr;
+    return fail(nullptr, CTM_EINVAL, "p and si_rounds must be >= 0");
+  }
+  c->N = chi * Dk * Db;
+  c->k = std::min(chi + c->opts.p, c->N);
+  if (chi > c->N) {
+    delete c;
+    g_cur = nullptr;
+    return fail(nullptr, CTM_EINVAL, "chi must not exceed chi*Dk*Db");
+  }
+  auto bail = [&](ctm_status st) {
+    std::string m = c->msg;
+    ctm_free(c);
+    g_cur = nullptr;
+    g_create_error = m;
+    return st;
+  };
+  if (c->opts.stream) {
+    c->stream = static_cast<cudaStream_t>(c->opts.stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__));
+    c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
+    return bail(fail(c, CTM_ECUDA, "cudaEventCreate failed"));
+  const size_t S = c->S, N = c->N, k = c->k, es = c->es;
+  const size_t nk = elems_ket(c), nb = elems_bra(c);
+  const size_t NN = N * N;
+  const size_t maxT = (size_t)d * d * NN + 64;
+  c->pipe_elems = maxT;
+  ctm_status st = CTM_OK;
+#define AL(ptr, bytes) \
+  if ((st = dalloc(c, (void**)&(ptr), (bytes))) != CTM_OK) return bail(st)
+  for (int r = 0; r < 4; ++r) {
+    AL(c->ket[r], S * nk * es);
+    AL(c->bra[r], S * nb * es);
+  }
+  AL(c->C, 4 * S * elems_C(c) * es);
+  AL(c->T, 4 * S * elems_T(c) * es);
+  AL(c->X, 4 * S * N * k * es);
+  AL(c->W, 4 * S * N * k * es);
+  for (int i = 0; i < 4; ++i) AL(c->Q[i], NN * es);
+  AL(c->pipe[0], maxT * es);
+  AL(c->pipe[1], maxT * es);
+  c->scratch_bytes = 3 * maxT * es + ((size_t)64 << 20);
+  AL(c->scratch, c->scratch_bytes);
+  const int Lmax = std::max(Lx, Ly);
+  AL(c->Pl, Lmax * N * chi * es);
+  AL(c->PrH, Lmax * N * chi * es);
+  AL(c->lastPl, S * N * chi * es);
+  AL(c->lastPrH, S * N * chi * es);
+  for (int i = 0; i < 4; ++i) AL(c->Z[i], N * k * es);
+  AL(c->Xn, N * k * es);
+  AL(c->Wn, N * k * es);
+  AL(c->G, k * k * es);
+  AL(c->Linv, k * k * es);
+  AL(c->rho, k * k * es);
+  AL(c->u, k * k * es);
+  AL(c->v, k * k * es);
+  AL(c->jw, std::max(2 * k * k, 8 * S * (size_t)chi * chi) * es);
+  AL(c->ph, std::max(k, (size_t)chi) * es);
+  AL(c->Vs, k * chi * es);
+  AL(c->Us, k * chi * es);
+  AL(c->sv, std::max(k, 4 * S * (size_t)chi) * sizeof(double));
+  AL(c->stC1, Lmax * elems_C(c) * es);
+  AL(c->stC4, Lmax * elems_C(c) * es);
+  AL(c->stT4, Lmax * elems_T(c) * es);
+  AL(c->spec_old, 4 * S * chi * sizeof(double));
+  AL(c->spec_new, 4 * S * chi * sizeof(double));
+  AL(c->dscal, 64 * sizeof(double));
+  AL(c->op, (size_t)d * d * d * d * es);
+  AL(c->rho2, (size_t)d * d * d * d * es);
+  AL(c->imp[0], nk * es);
+  AL(c->imp[1], nk * es);
+  AL(c->err, sizeof(int));
+#undef AL
+  if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess)
+    return bail(fail(c, CTM_ECUDA, "cudaMemset failed"));
+  c->rf_ready.assign(4 * S, 0);
+  // tensors: upload rotation 0, derive the other three on the device
+  for (int i = 0; i < c->S; ++i) {
+    if (cudaMemcpy(at(c->ket[0], i * nk, c), kets[i], nk * es, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(c, CTM_ECUDA, "upload of A failed"));
+    if (classical) {
+      const double one[2] = {1.0, 0.0};
+      if (cudaMemcpy(at(c->bra[0], i * nb, c), one, es, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(c, CTM_ECUDA, "upload of B failed"));
+    } else if (bras) {
+      if (cudaMemcpy(at(c->bra[0], i * nb, c), bras[i], nb * es, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(c, CTM_ECUDA, "upload of B failed"));
+    } else {
+      const long dims1[1] = {(long)nk};
+      const int perm1[1] = {0};
+      cudaError_t e = permute(at(c->ket[0], i * nk, c), at(c->bra[0], i * nb, c), 1, dims1, perm1,
+                              cx, true, c->stream, &c->launches);
+      if (e != cudaSuccess) return bail(cuda_fail(e, "conj(A)", __FILE__, __LINE__));
+    }
+  }
+  static const int rot[4][5] = {{0, 1, 2, 3, 4}, {0, 4, 1, 2, 3}, {0, 3, 4, 1, 2}, {0, 2, 3, 4, 1}};
+  for (int r = 1; r < 4; ++r) {
+    for (int i = 0; i < c->S; ++i) {
+      const long dk[5] = {d, Dk, Dk, Dk, Dk}, db[5] = {d, Db, Db, Db, Db};
+      cudaError_t e = permute(at(c->ket[0], i * nk, c), at(c->ket[r], i * nk, c), 5, dk, rot[r],
+                              cx, false, c->stream, &c->launches);
+      if (e == cudaSuccess)
+        e = permute(at(c->bra[0], i * nb, c), at(c->bra[r], i * nb, c), 5, db, rot[r], cx, false,
+                    c->stream, &c->launches);
+      if (e != cudaSuccess) return bail(cuda_fail(e, "rotate A", __FILE__, __LINE__));
+    }
+  }
+  if ((st = upload_default_state(c)) != CTM_OK) return bail(st);
+  if (c->opts.prec == CTM_PREC_SPLIT_BF16) {
+    st = split_create(&c->split, cx, (int)N, (int)k, c->stream);
+    if (st != CTM_OK) {
+      c->msg = "split-precision setup failed";
+      return bail(st);
+    }
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(fail(c, CTM_ECUDA, "initialisation failed on the device"));
+  *out = c;
+  g_cur = nullptr;
+  return CTM_OK;
+}
+
+struct Guard {
+  explicit Guard(ctm_ctx* c) { g_cur = c; }
+  ~Guard() { g_cur = nullptr; }
+};
+
+// one-site patch with the ket at (x, y) of frame 0 replaced by K (device);
+// result: scalar Z at out (open = false) or rho[s][t] (open = true)
+ctm_status one_site(ctm_ctx* c, int x, int y, void* K, bool open, void* out) {
+  const long chi = c->chi, Dk = c->Dk, Db = c->Db, d = c->d;
+  const int r = 0;
+  const int site = frame_site(c, r, x, y);
+  void* B = BRAp(c, 0, site);
+  Tn E1 = tn(c->pipe[0], {chi, chi, Dk, Db});
+  CK(ein(c, "ab,bcuU->acuU", tn(fC(c, r, 0, x, y), {chi, chi}), false,
+         tn(fT(c, r, 0, x, y), {chi, chi, Dk, Db}), false, E1));
+  Tn E2 = tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db});
+  CK(ein(c, "ialL,acuU->ilLcuU", tn(fT(c, r, 3, x, y), {chi, chi, Dk, Db}), false, E1, false, E2));
+  Tn E3 = tn(c->pipe[0], {chi, Db, chi, Db, d, Dk, Dk});
+  CK(ein(c, "ilLcuU,sulwr->iLcUswr", E2, false, tn(K, {d, Dk, Dk, Dk, Dk}), false, E3));
+  Tn Qx;
+  if (open) {
+    Qx = tn(c->pipe[1], {chi, chi, Dk, Db, Dk, Db, d, d});
+    CK(ein(c, "iLcUswr,tULWR->icwWrRst", E3, false, tn(B, {d, Db, Db, Db, Db}), false, Qx));
+  } else {
+    Qx = tn(c->pipe[1], {chi, chi, Dk, Db, Dk, Db});
+    CK(ein(c, "iLcUswr,sULWR->icwWrR", E3, false, tn(B, {d, Db, Db, Db, Db}), false, Qx));
+  }
+  // rest of the ring: C2 T2 C3 T3 C4 -> F[c, r, R, w, W, i]; keep Qx in pipe[1]
+  // and build F in the Q[0]/Q[1] buffers (N^2 elements each)
+  Tn F1 = tn(c->Q[0], {chi, chi, Dk, Db});
+  CK(ein(c, "ce,efrR->cfrR", tn(fC(c, r, 1, x, y), {chi, chi}), false,
+         tn(fT(c, r, 1, x, y), {chi, chi, Dk, Db}), false, F1));
+  Tn F2 = tn(c->Q[1], {chi, Dk, Db, chi});
+  CK(ein(c, "cfrR,fg->crRg", F1, false, tn(fC(c, r, 2, x, y), {chi, chi}), false, F2));
+  Tn F3 = tn(c->Q[0], {chi, Dk, Db, chi, Dk, Db});
+  CK(ein(c, "crRg,ghwW->crRhwW", F2, false, tn(fT(c, r, 2, x, y), {chi, chi, Dk, Db}), false, F3));
+  Tn F4 = tn(c->Q[1], {chi, Dk, Db, Dk, Db, chi});
+  CK(ein(c, "crRhwW,hi->crRwWi", F3, false, tn(fC(c, r, 3, x, y), {chi, chi}), false, F4));
+  if (open)
+    CK(ein(c, "icwWrRst,crRwWi->st", Qx, false, F4, false, tn(out, {d, d})));
+  else
+    CK(ein(c, "icwWrR,crRwWi->", Qx, false, F4, false, tn(out, {})));
+  return CTM_OK;
+}
+
+// two-site patch of frame r at (x, y), (x+1, y); kets K1, K2 are frame
+// rotated; result rho[s1][s2][t1][t2] at out (unnormalised)
+ctm_status two_site(ctm_ctx* c, int r, int x, int y, void* K1, void* K2, void* out) {
+  const long chi = c->chi, Dk = c->Dk, Db = c->Db, d = c->d;
+  void* B1 = BRAp(c, r, frame_site(c, r, x, y));
+  void* B2 = BRAp(c, r, frame_site(c, r, x + 1, y));
+  const Tn tC = tn(nullptr, {chi, chi}), tT = tn(nullptr, {chi, chi, Dk, Db});
+  auto C_ = [&](int i, int xx) { Tn t = tC; t.p = fC(c, r, i, xx, y); return t; };
+  auto T_ = [&](int i, int xx) { Tn t = tT; t.p = fT(c, r, i, xx, y); return t; };
+  // the two halves live in the scratch arena (chi^2 d^2 Dk Db elements each)
+  const size_t mark = c->scratch_off;
+  const size_t half = (size_t)chi * chi * d * d * Dk * Db * c->es;
+  void* Lbuf = scratch_alloc(c, half);
+  void* Rbuf = scratch_alloc(c, half);
+  if (!Lbuf || !Rbuf) return fail(c, CTM_ENOMEM, "scratch arena too small for the two-site patch");
+  // left half L[i, c, s, m, t, M]
+  CK(ein(c, "ab,bcuU->acuU", C_(0, x), false, T_(0, x), false, tn(c->pipe[0], {chi, chi, Dk, Db})));
+  CK(ein(c, "kalL,acuU->klLcuU", T_(3, x), false, tn(c->pipe[0], {chi, chi, Dk, Db}), false,
+         tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db})));
+  CK(ein(c, "klLcuU,sulxm->kLcUsxm", tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db}), false,
+         tn(K1, {d, Dk, Dk, Dk, Dk}), false, tn(c->pipe[0], {chi, Db, chi, Db, d, Dk, Dk})));
+  CK(ein(c, "kLcUsxm,tULXM->kcsxmtXM", tn(c->pipe[0], {chi, Db, chi, Db, d, Dk, Dk}), false,
+         tn(B1, {d, Db, Db, Db, Db}), false, tn(c->pipe[1], {chi, chi, d, Dk, Dk, d, Db, Db})));
+  CK(ein(c, "kcsxmtXM,jk->jcsxmtXM", tn(c->pipe[1], {chi, chi, d, Dk, Dk, d, Db, Db}), false,
+         C_(3, x), false, tn(c->pipe[0], {chi, chi, d, Dk, Dk, d, Db, Db})));
+  Tn L = tn(Lbuf, {chi, chi, d, Dk, d, Db});
+  CK(ein(c, "jcsxmtXM,ijxX->icsmtM", tn(c->pipe[0], {chi, chi, d, Dk, Dk, d, Db, Db}), false,
+         T_(2, x), false, L));
+  // right half R[c, i, q, m, v, M]
+  CK(ein(c, "ceoO,ef->cfoO", T_(0, x + 1), false, C_(1, x + 1), false,
+         tn(c->pipe[0], {chi, chi, Dk, Db})));
+  CK(ein(c, "cfoO,fgrR->cgoOrR", tn(c->pipe[0], {chi, chi, Dk, Db}), false, T_(1, x + 1), false,
+         tn(c->pipe[1], {chi, chi, Dk, Db, Dk, Db})));
+  CK(ein(c, "cgoOrR,qomwr->cgORqmw", tn(c->pipe[1], {chi, chi, Dk, Db, Dk, Db}), false,
+         tn(K2, {d, Dk, Dk, Dk, Dk}), false, tn(c->pipe[0], {chi, chi, Db, Db, d, Dk, Dk})));
+  CK(ein(c, "cgORqmw,vOMWR->cgqmwvMW", tn(c->pipe[0], {chi, chi, Db, Db, d, Dk, Dk}), false,
+         tn(B2, {d, Db, Db, Db, Db}), false, tn(c->pipe[1], {chi, chi, d, Dk, Dk, d, Db, Db})));
+  CK(ein(c, "cgqmwvMW,gh->chqmwvMW", tn(c->pipe[1], {chi, chi, d, Dk, Dk, d, Db, Db}), false,
+         C_(2, x + 1), false, tn(c->pipe[0], {chi, chi, d, Dk, Dk, d, Db, Db})));
+  Tn R = tn(Rbuf, {chi, chi, d, Dk, d, Db});
+  CK(ein(c, "chqmwvMW,hiwW->ciqmvM", tn(c->pipe[0], {chi, chi, d, Dk, Dk, d, Db, Db}), false,
+         T_(2, x + 1), false, R));
+  CK(ein(c, "icsmtM,ciqmvM->sqtv", L, false, R, false, tn(out, {d, d, d, d})));
+  c->scratch_off = mark;
+  return CTM_OK;
+}
+
+// frame and frame positions of the bond (x, y) -> right (dir 0) / down (dir 1)
+void bond_frame(const ctm_ctx* c, int x, int y, int dir, int* r, int* fx, int* fy) {
+  if (dir == 0) { *r = 0; *fx = x; *fy = y; }
+  else { *r = 1; *fx = y; *fy = ((-x) % c->Lx + c->Lx) % c->Lx; }
+}
+
+ctm_status rho2_device(ctm_ctx* c, int x, int y, int dir, const void* h1, const void* h2,
+                       void* out) {
+  int r, fx, fy;
+  bond_frame(c, x, y, dir, &r, &fx, &fy);
+  void* K1 = KETp(c, r, frame_site(c, r, fx, fy));
+  void* K2 = KETp(c, r, frame_site(c, r, fx + 1, fy));
+  static const int rot[4][5] = {{0, 1, 2, 3, 4}, {0, 4, 1, 2, 3}, {0, 3, 4, 1, 2}, {0, 2, 3, 4, 1}};
+  const long dk[5] = {c->d, c->Dk, c->Dk, c->Dk, c->Dk};
+  const size_t nk = elems_ket(c);
+  if (h1) {
+    CTM_CUDA_OK(cudaMemcpyAsync(c->pipe[1], h1, nk * c->es, cudaMemcpyHostToDevice, c->stream));
+    CTM_CUDA_OK(permute(c->pipe[1], c->imp[0], 5, dk, rot[r], c->cx, false, c->stream, &c->launches));
+    K1 = c->imp[0];
+  }
+  if (h2) {
+    CTM_CUDA_OK(cudaMemcpyAsync(c->pipe[1], h2, nk * c->es, cudaMemcpyHostToDevice, c->stream));
+    CTM_CUDA_OK(permute(c->pipe[1], c->imp[1], 5, dk, rot[r], c->cx, false, c->stream, &c->launches));
+    K2 = c->imp[1];
+  }
+  return two_site(c, r, fx, fy, K1, K2, out);
+}
+
+bool valid_site(const ctm_ctx* c, int x, int y) {
+  return x >= 0 && y >= 0 && x < c->Lx && y < c->Ly;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+void ctm_default_opts(ctm_opts* o) {
+  if (!o) return;
+  o->p = 5;
+  o->si_rounds = 1;
+  o->method = CTM_PROJ_SI;
+  o->prec = CTM_PREC_FP64;
+  o->svd_rel_cutoff = 1e-14;
+  o->normalize = 1;
+  o->sign_fix = 1;
+  o->seed = 0;
+  o->stream = nullptr;
+}
+
+ctm_status ctm_init(ctm_ctx** out, int Lx, int Ly, const void* const* A, const void* const* bra,
+                    ctm_dtype dtype, int d, int D, int chi, const ctm_opts* opts) {
+  if (dtype != CTM_F64 && dtype != CTM_C128) return fail(nullptr, CTM_EINVAL, "bad dtype");
+  return create(out, Lx, Ly, d, D, D, chi, dtype == CTM_C128, opts, A, bra, false);
+}
+
+ctm_status ctm_init_network(ctm_ctx** out, int Lx, int Ly, const double* const* a, int k, int chi,
+                            const ctm_opts* opts) {
+  return create(out, Lx, Ly, 1, k, 1, chi, false, opts, reinterpret_cast<const void* const*>(a),
+                nullptr, true);
+}
+
+ctm_status ctm_set_env(ctm_ctx* c, const void* C, const void* T) {
+  if (!c || !C || !T) return fail(c, CTM_EINVAL, "NULL argument");
+  Guard gd(c);
+  CTM_CUDA_OK(cudaMemcpyAsync(c->C, C, 4 * c->S * elems_C(c) * c->es, cudaMemcpyHostToDevice, c->stream));
+  CTM_CUDA_OK(cudaMemcpyAsync(c->T, T, 4 * c->S * elems_T(c) * c->es, cudaMemcpyHostToDevice, c->stream));
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  c->spectra_init = false;
+  return CTM_OK;
+}
+
+ctm_status ctm_get_env(ctm_ctx* c, void* C, void* T) {
+  if (!c || !C || !T) return fail(c, CTM_EINVAL, "NULL argument");
+  Guard gd(c);
+  CTM_CUDA_OK(cudaMemcpyAsync(C, c->C, 4 * c->S * elems_C(c) * c->es, cudaMemcpyDeviceToHost, c->stream));
+  CTM_CUDA_OK(cudaMemcpyAsync(T, c->T, 4 * c->S * elems_T(c) * c->es, cudaMemcpyDeviceToHost, c->stream));
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  return CTM_OK;
+}
+
+ctm_status ctm_set_rangefinders(ctm_ctx* c, const void* X, const void* W) {
+  if (!c || !X || !W) return fail(c, CTM_EINVAL, "NULL argument");
+  Guard gd(c);
+  const size_t n = (size_t)4 * c->S * c->N * c->k * c->es;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->X, X, n, cudaMemcpyHostToDevice, c->stream));
+  CTM_CUDA_OK(cudaMemcpyAsync(c->W, W, n, cudaMemcpyHostToDevice, c->stream));
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
+  return CTM_OK;
+}
+
+ctm_status ctm_dims(const ctm_ctx* c, int* N, int* k) {
+  if (!c || !N || !k) return CTM_EINVAL;
+  *N = c->N;
+  *k = c->k;
+  return CTM_OK;
+}
+
+ctm_status ctm_move(ctm_ctx* c, ctm_dir dir) {
+  if (!c) return fail(c, CTM_EINVAL, "ctx is NULL");
+  if (dir < 0 || dir > 3) return fail(c, CTM_EINVAL, "direction must be 0..3");
+  Guard gd(c);
+  const long l0 = c->launches;
+  CTM_CUDA_OK(cudaEventRecord(c->ev0, c->stream));
+  CK(move_impl(c, (int)dir));
+  CTM_CUDA_OK(cudaEventRecord(c->ev1, c->stream));
+  CK(check_err(c));
+  float ms = 0.f;
+  CTM_CUDA_OK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->last_ms = ms;
+  c->last_launches = c->launches - l0;
+  return CTM_OK;
+}
+
+ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, double* delta_out) {
+  if (!c) return fail(c, CTM_EINVAL, "ctx is NULL");
+  if (max_iter < 0) return fail(c, CTM_EINVAL, "max_iter must be >= 0");
+  Guard gd(c);
+  const long l0 = c->launches;
+  CTM_CUDA_OK(cudaEventRecord(c->ev0, c->stream));
+  const int nspec = 4 * c->S * c->chi;
+  if (!c->spectra_init) {
+    CK(corner_spectra(c, c->spec_new));
+    CTM_CUDA_OK(cudaMemsetAsync(c->spec_old, 0, nspec * sizeof(double), c->stream));
+    CTM_CUDA_OK(spectra_delta(c->chi, 4 * c->S, c->spec_new, c->spec_old, c->dscal, c->stream, &c->launches));
+    c->spectra_init = true;
+  }
+  double delta = INFINITY;
+  int it = 0;
+  while (it < max_iter) {
+    for (int r = 0; r < 4; ++r) CK(move_impl(c, r));
+    ++it;
+    CK(corner_spectra(c, c->spec_new));
+    CTM_CUDA_OK(spectra_delta(c->chi, 4 * c->S, c->spec_new, c->spec_old, c->dscal + 1, c->stream, &c->launches));
+    CTM_CUDA_OK(cudaMemcpyAsync(&delta, c->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(check_err(c));
+    if (delta < tol) break;
+  }
+  CTM_CUDA_OK(cudaEventRecord(c->ev1, c->stream));
+  CTM_CUDA_OK(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  CTM_CUDA_OK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->last_ms = ms;
+  c->last_launches = c->launches - l0;
+  if (iters_out) *iters_out = it;
+  if (delta_out) *delta_out = delta;
+  if (!(delta < tol)) {
+    c->msg = "max_iter reached before the corner spectra converged";
+    return CTM_ENOCONV;
+  }
+  return CTM_OK;
+}
+
+ctm_status ctm_spectrum(ctm_ctx* c, int x, int y, int label, double* s_out) {
+  if (!c || !s_out) return fail(c, CTM_EINVAL, "NULL argument");
+  if (!valid_site(c, x, y) || label < 1 || label > 4) return fail(c, CTM_EINVAL, "bad site or label");
+  Guard gd(c);
+  const int site = y * c->Lx + x;
+  CTM_CUDA_OK(jacobi_svd(c->cx, c->chi, Cp(c, label - 1, site), 0, c->sv, nullptr, nullptr, false,
+                         c->jw, 1, 80, c->err, c->stream, &c->launches));
+  CTM_CUDA_OK(normalize(false, c->chi, c->sv, 0, 1, c->dscal, true, c->scratch, c->stream, &c->launches));
+  CTM_CUDA_OK(cudaMemcpyAsync(s_out, c->sv, c->chi * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  return CTM_OK;
+}
+
+ctm_status ctm_rdm2(ctm_ctx* c, int x, int y, int dir, double* rho_out) {
+  if (!c || !rho_out) return fail(c, CTM_EINVAL, "NULL argument");
+  if (!valid_site(c, x, y) || (dir != 0 && dir != 1)) return fail(c, CTM_EINVAL, "bad site or dir");
+  Guard gd(c);
+  const int d2 = c->d * c->d;
+  CK(rho2_device(c, x, y, dir, nullptr, nullptr, c->rho2));
+  std::vector<double> h((size_t)d2 * d2 * (c->cx ? 2 : 1));
+  CTM_CUDA_OK(cudaMemcpyAsync(h.data(), c->rho2, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  double tr_re = 0.0, tr_im = 0.0;
+  for (int i = 0; i < d2; ++i) {
+    if (c->cx) { tr_re += h[2 * (i * d2 + i)]; tr_im += h[2 * (i * d2 + i) + 1]; }
+    else tr_re += h[i * d2 + i];
+  }
+  const double den = tr_re * tr_re + tr_im * tr_im;
+  for (int i = 0; i < d2 * d2; ++i) {
+    double re = c->cx ? h[2 * i] : h[i], im = c->cx ? h[2 * i + 1] : 0.0;
+    rho_out[2 * i] = (re * tr_re + im * tr_im) / den;
+    rho_out[2 * i + 1] = (im * tr_re - re * tr_im) / den;
+  }
+  return CTM_OK;
+}
+
+ctm_status ctm_expect(ctm_ctx* c, const void* op, int x, int y, int dir, double out[2]) {
+  if (!c || !op || !out) return fail(c, CTM_EINVAL, "NULL argument");
+  if (!valid_site(c, x, y) || (dir != 0 && dir != 1)) return fail(c, CTM_EINVAL, "bad site or dir");
+  Guard gd(c);
+  const int d2 = c->d * c->d;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->op, op, (size_t)d2 * d2 * c->es, cudaMemcpyHostToDevice, c->stream));
+  CK(rho2_device(c, x, y, dir, nullptr, nullptr, c->rho2));
+  CTM_CUDA_OK(trace_products(c->cx, d2, c->op, c->rho2, c->dscal + 8, c->stream, &c->launches));
+  double h[4];
+  CTM_CUDA_OK(cudaMemcpyAsync(h, c->dscal + 8, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  const double den = h[2] * h[2] + h[3] * h[3];
+  out[0] = (h[0] * h[2] + h[1] * h[3]) / den;
+  out[1] = (h[1] * h[2] - h[0] * h[3]) / den;
+  return CTM_OK;
+}
+
+ctm_status ctm_expect_bond(ctm_ctx* c, const void* imp1, const void* imp2, int x, int y, int dir,
+                           double out[2]) {
+  if (!c || !imp1 || !imp2 || !out) return fail(c, CTM_EINVAL, "NULL argument");
+  if (!valid_site(c, x, y) || (dir != 0 && dir != 1)) return fail(c, CTM_EINVAL, "bad site or dir");
+  Guard gd(c);
+  const int d2 = c->d * c->d;
+  // identity operator: the traces of the two density matrices
+  std::vector<double> eye((size_t)d2 * d2 * (c->cx ? 2 : 1), 0.0);
+  for (int i = 0; i < d2; ++i) eye[(size_t)(i * d2 + i) * (c->cx ? 2 : 1)] = 1.0;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->op, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(rho2_device(c, x, y, dir, nullptr, nullptr, c->rho2));
+  CTM_CUDA_OK(trace_products(c->cx, d2, c->op, c->rho2, c->dscal + 8, c->stream, &c->launches));
+  CK(rho2_device(c, x, y, dir, imp1, imp2, c->rho2));
+  CTM_CUDA_OK(trace_products(c->cx, d2, c->op, c->rho2, c->dscal + 12, c->stream, &c->launches));
+  double h[8];
+  CTM_CUDA_OK(cudaMemcpyAsync(h, c->dscal + 8, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  const double den = h[2] * h[2] + h[3] * h[3];
+  out[0] = (h[6] * h[2] + h[7] * h[3]) / den;
+  out[1] = (h[7] * h[2] - h[6] * h[3]) / den;
+  return CTM_OK;
+}
+
+ctm_status ctm_expect_site(ctm_ctx* c, const void* imp, int x, int y, double out[2]) {
+  if (!c || !imp || !out) return fail(c, CTM_EINVAL, "NULL argument");
+  if (!valid_site(c, x, y)) return fail(c, CTM_EINVAL, "bad site");
+  Guard gd(c);
+  const size_t nk = elems_ket(c);
+  CTM_CUDA_OK(cudaMemcpyAsync(c->imp[0], imp, nk * c->es, cudaMemcpyHostToDevice, c->stream));
+  const int site = y * c->Lx + x;
+  CK(one_site(c, x, y, KETp(c, 0, site), false, c->dscal + 16));
+  CK(one_site(c, x, y, c->imp[0], false, c->dscal + 20));
+  double h[8];
+  CTM_CUDA_OK(cudaMemcpyAsync(h, c->dscal + 16, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  double z0r = h[0], z0i = c->cx ? h[1] : 0.0, z1r = h[4], z1i = c->cx ? h[5] : 0.0;
+  const double den = z0r * z0r + z0i * z0i;
+  out[0] = (z1r * z0r + z1i * z0i) / den;
+  out[1] = (z1i * z0r - z1r * z0i) / den;
+  return CTM_OK;
+}
+
+ctm_status ctm_free_energy(ctm_ctx* c, double* ln_kappa) {
+  if (!c || !ln_kappa) return fail(c, CTM_EINVAL, "NULL argument");
+  if (c->S != 1) return fail(c, CTM_EINVAL, "free energy per site needs a 1x1 cell");
+  Guard gd(c);
+  const long chi = c->chi, Dk = c->Dk, Db = c->Db;
+  CK(one_site(c, 0, 0, KETp(c, 0, 0), false, c->dscal + 24));
+  auto Ct = [&](int i) { return tn(Cp(c, i, 0), {chi, chi}); };
+  auto Tt = [&](int i) { return tn(Tp(c, i, 0), {chi, chi, Dk, Db}); };
+  void* p0 = c->pipe[0];
+  void* p1 = c->pipe[1];
+  // Z0 = tr(C1 C2 C3 C4)
+  CK(ein(c, "ab,bc->ac", Ct(0), false, Ct(1), false, tn(p0, {chi, chi})));
+  CK(ein(c, "ac,ce->ae", tn(p0, {chi, chi}), false, Ct(2), false, tn(p1, {chi, chi})));
+  CK(ein(c, "ae,ea->", tn(p1, {chi, chi}), false, Ct(3), false, tn(c->dscal + 28, {})));
+  // Z13: T1 and T3 joined
+  CK(ein(c, "ab,bcuU->acuU", Ct(0), false, Tt(0), false, tn(p0, {chi, chi, Dk, Db})));
+  CK(ein(c, "acuU,ce->aeuU", tn(p0, {chi, chi, Dk, Db}), false, Ct(1), false, tn(p1, {chi, chi, Dk, Db})));
+  CK(ein(c, "aeuU,ef->afuU", tn(p1, {chi, chi, Dk, Db}), false, Ct(2), false, tn(p0, {chi, chi, Dk, Db})));
+  CK(ein(c, "afuU,fguU->ag", tn(p0, {chi, chi, Dk, Db}), false, Tt(2), false, tn(p1, {chi, chi})));
+  CK(ein(c, "ag,ga->", tn(p1, {chi, chi}), false, Ct(3), false, tn(c->dscal + 32, {})));
+  // Z24: T2 and T4 joined
+  CK(ein(c, "ab,bc->ac", Ct(0), false, Ct(1), false, tn(p0, {chi, chi})));
+  CK(ein(c, "ac,ceuU->aeuU", tn(p0, {chi, chi}), false, Tt(1), false, tn(p1, {chi, chi, Dk, Db})));
+  CK(ein(c, "aeuU,ef->afuU", tn(p1, {chi, chi, Dk, Db}), false, Ct(2), false, tn(p0, {chi, chi, Dk, Db})));
+  CK(ein(c, "afuU,fg->aguU", tn(p0, {chi, chi, Dk, Db}), false, Ct(3), false, tn(p1, {chi, chi, Dk, Db})));
+  CK(ein(c, "aguU,gauU->", tn(p1, {chi, chi, Dk, Db}), false, Tt(3), false, tn(c->dscal + 36, {})));
+  double h[16];
+  CTM_CUDA_OK(cudaMemcpyAsync(h, c->dscal + 24, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  const double z1 = h[0], z0 = h[4], z13 = h[8], z24 = h[12];
+  const double ratio = z1 * z0 / (z13 * z24);
+  if (!(ratio > 0.0)) return fail(c, CTM_ENUMERIC, "non-positive kappa");
+  *ln_kappa = std::log(ratio);
+  return CTM_OK;
+}
+
+ctm_status ctm_get_projectors(ctm_ctx* c, ctm_dir dir, int x, int y, void* Pl, void* PrH) {
+  if (!c || !Pl || !PrH) return fail(c, CTM_EINVAL, "NULL argument");
+  if ((int)dir != c->last_dir) return fail(c, CTM_EINVAL, "projectors are kept for the last move only");
+  const int r = (int)dir;
+  const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
+  if (x < 0 || y < 0 || x >= Lxf || y >= Lyf) return fail(c, CTM_EINVAL, "bad cut");
+  Guard gd(c);
+  const size_t NC = (size_t)c->N * c->chi;
+  const int cut = y * Lxf + x;
+  CTM_CUDA_OK(cudaMemcpyAsync(Pl, at(c->lastPl, cut * NC, c), NC * c->es, cudaMemcpyDeviceToHost, c->stream));
+  CTM_CUDA_OK(cudaMemcpyAsync(PrH, at(c->lastPrH, cut * NC, c), NC * c->es, cudaMemcpyDeviceToHost, c->stream));
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  return CTM_OK;
+}
+
+ctm_status ctm_last_timing(const ctm_ctx* c, double* ms, long* launches) {
+  if (!c) return CTM_EINVAL;
+  if (ms) *ms = c->last_ms;
+  if (launches) *launches = c->last_launches;
+  return CTM_OK;
+}
+
+void ctm_free(ctm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->split) split_destroy(c->split);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* ctm_last_error(const ctm_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->msg.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Host launchers of the libctm kernels (all asynchronous on the given stream).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace ctm {
+
+// ------------------------------------------------------------- permute.cu
+// out = in with axes reordered: output axis j is input axis perm[j]; both
+// row-major and contiguous. conj conjugates complex elements on the way.
+cudaError_t permute(const void* in, void* out, int rank, const long* in_dims,
+                    const int* perm, bool cx, bool conj, cudaStream_t s,
+                    long* launches);
+
+// ------------------------------------------------------------- gemm64.cu
+enum Op { OP_N = 0, OP_T = 1, OP_C = 2, OP_R = 3 };  // R = conj, no transpose
+
+struct GemmDesc {
+  bool cx = false;
+  int opA = OP_N, opB = OP_N;
+  long M = 0, N = 0, K = 0;
+  const void* A = nullptr; long lda = 0, strideA = 0;
+  const void* B = nullptr; long ldb = 0, strideB = 0;
+  void* C = nullptr; long ldc = 0, strideC = 0;
+  double alpha[2] = {1.0, 0.0};
+  double beta[2] = {0.0, 0.0};
+  int batch = 1;
+};
+// C = alpha op(A) op(B) + beta C in fp64, row-major; op(A) is M x K, op(B)
+// K x N. Split-K partials (deterministic reduction) use work.
+cudaError_t gemm64(const GemmDesc& g, void* work, size_t work_bytes,
+                   cudaStream_t s, long* launches);
+size_t gemm64_work_bytes(const GemmDesc& g);
+
+// out[b] = sum_i conj?(x[b][i]) y[b][i] (n elements, batch b), fp64.
+cudaError_t dot64(bool cx, bool conj_x, long n, const void* x, long sx,
+                  const void* y, long sy, void* out, int batch, void* work,
+                  size_t work_bytes, cudaStream_t s, long* launches);
+
+// ------------------------------------------------------------- linalg.cu
+// Lower Cholesky factor of G (+ shift I) and its inverse, one block per
+// matrix: G is k x k (ld k), overwritten by L; Linv receives L^-1. With
+// shift != 0 the shift is 11 (n k + k (k + 1)) u trace(G) (shifted
+// CholeskyQR, Fukaya et al. 2020); n is the row count of the factored block.
+cudaError_t chol_inv(bool cx, int k, long n, bool shift, void* G, void* Linv,
+                     int batch, int* err, cudaStream_t s, long* launches);
+
+// One-sided Jacobi SVD (Hestenes) of k x k row-major matrices, one block per
+// matrix: A = U diag(s) V^H with s descending; U, V row-major k x k. work
+// holds 2 k^2 elements per matrix. want_uv = false computes s only.
+cudaError_t jacobi_svd(bool cx, int k, const void* A, long strideA,
+                       double* s, void* U, void* V, bool want_uv, void* work,
+                       int batch, int max_sweeps, int* err, cudaStream_t s_,
+                       long* launches);
+
+// Phase of the largest-modulus entry (lowest row on ties) of each of the
+// first ncol columns of an n x ld row-major matrix; ph gets the phase.
+cudaError_t column_phase(bool cx, long n, int ncol, long ld, const void* Z,
+                         void* ph, int batch, long strideZ, cudaStream_t s,
+                         long* launches);
+
+// Multiply column j of each listed row-major matrix by conj(ph[j]).
+cudaError_t scale_columns_conj(bool cx, long rows, int ncol, long ld,
+                               void* Z, const void* ph, cudaStream_t s,
+                               long* launches);
+
+// Vs[i][j] = V[i][j] * s_j^-1/2 (j < c, s_j > cutoff * s_0, else 0) for a
+// k x k matrix V, output k x c.
+cudaError_t scale_by_inv_sqrt(bool cx, int k, int c, const void* V,
+                              const double* s, double cutoff, void* Vs,
+                              cudaStream_t s_, long* launches);
+
+// Frobenius norm of each of batch tensors (n elements) into nrm[b], then
+// x /= nrm (when scale). Deterministic two-level reduction.
+cudaError_t normalize(bool cx, long n, void* x, long stride, int batch,
+                      double* nrm, bool scale, void* work, cudaStream_t s,
+                      long* launches);
+
+// spectra (batch x c, descending) -> unit 2-norm rows; delta[0] = max over
+// rows of ||new - old||_2; old <- new.
+cudaError_t spectra_delta(int c, int batch, double* snew, double* sold,
+                          double* delta, cudaStream_t s, long* launches);
+
+// G += alpha * I for batch k x k matrices
+cudaError_t add_identity(bool cx, int k, void* G, double alpha, int batch,
+                         cudaStream_t s, long* launches);
+
+// y = sum_i O[i] * R[perm(i)] trace product Tr(O R) and Tr(R) for d2 x d2.
+cudaError_t trace_products(bool cx, int d2, const void* O, const void* R,
+                           double* out4, cudaStream_t s, long* launches);
+
+}  // namespace ctm

@@ -1,0 +1,519 @@
+// Small dense FP64 linear algebra of the projector construction, one thread
+// block per matrix (batched over the cuts of a column):
+//   * Cholesky factor and triangular inverse of a k x k Gram matrix, the core
+//     of (shifted) CholeskyQR (Fukaya, Kannan, Nakatsukasa, Yamamoto,
+//     Yanagisawa 2020) that re-orthonormalises the rangefinders;
+//   * one-sided Jacobi SVD (Hestenes 1958; Demmel & Veselic 1992) of the
+//     (chi+p) x (chi+p) matrix rho and of the corners, with round-robin pair
+//     ordering and a bounded number of sweeps;
+//   * the phase fix of singular vectors, s^-1/2 with cutoff, normalisation
+//     and the corner-spectrum convergence measure.
+#include <cfloat>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ctm {
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------ Cholesky
+template <typename T>
+__global__ void __launch_bounds__(256) chol_inv_kernel(int k, long n, int shift,
+                                                       T* G, T* Linv, int* err) {
+  T* g = G + (long)blockIdx.x * k * k;
+  T* L = Linv + (long)blockIdx.x * k * k;
+  __shared__ double sh[32];
+  __shared__ double piv;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  if (shift) {
+    double tr = 0.0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) tr += realv(g[(long)i * k + i]);
+    tr = block_sum(tr, sh);
+    const double sft = 11.0 * ((double)n * k + (double)k * (k + 1)) * DBL_EPSILON * tr;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const double re = realv(g[(long)i * k + i]) + sft;
+      if constexpr (sizeof(T) == 8) g[(long)i * k + i] = re;
+      else g[(long)i * k + i] = make_double2(re, 0.0);
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = realv(g[(long)j * k + j]);
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        piv = 1.0;
+      } else {
+        piv = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double dj = piv, inv = 1.0 / piv;
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
+      g[(long)i * k + j] = scalev(g[(long)i * k + j], inv);
+    if (threadIdx.x == 0) {
+      if constexpr (sizeof(T) == 8) g[(long)j * k + j] = dj;
+      else g[(long)j * k + j] = make_double2(dj, 0.0);
+    }
+    __syncthreads();
+    const int m = k - j - 1;
+    for (long idx = threadIdx.x; idx < (long)m * m; idx += blockDim.x) {
+      const int i = j + 1 + (int)(idx / m), l = j + 1 + (int)(idx % m);
+      if (l > i) continue;
+      // G_il -= L_ij conj(L_lj)
+      T v = g[(long)i * k + l];
+      T lij = g[(long)i * k + j], llj = g[(long)l * k + j];
+      v = subv(v, mulv(lij, conjv(llj)));
+      g[(long)i * k + l] = v;
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(err, DEV_CHOL_PIVOT);
+    // leave an identity inverse so that downstream products stay finite
+    for (long idx = threadIdx.x; idx < (long)k * k; idx += blockDim.x) {
+      const int i = (int)(idx / k), c = (int)(idx % k);
+      T v = zero_of(T());
+      if (i == c) {
+        if constexpr (sizeof(T) == 8) v = 1.0;
+        else v = make_double2(1.0, 0.0);
+      }
+      L[idx] = v;
+    }
+    return;
+  }
+  // forward substitution, one column of L^-1 per thread
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int i = 0; i < k; ++i) {
+      T v = zero_of(T());
+      if (i >= c) {
+        if (i == c) {
+          if constexpr (sizeof(T) == 8) v = 1.0;
+          else v = make_double2(1.0, 0.0);
+        }
+        for (int j = c; j < i; ++j) v = subv(v, mulv(g[(long)i * k + j], L[(long)j * k + c]));
+        v = scalev(v, 1.0 / realv(g[(long)i * k + i]));
+      }
+      L[(long)i * k + c] = v;
+    }
+  }
+}
+
+// --------------------------------------------------------------- Jacobi
+template <typename T>
+__device__ __forceinline__ T phase_of(T g, double mag);
+template <>
+__device__ __forceinline__ double phase_of<double>(double g, double mag) { return g / mag; }
+template <>
+__device__ __forceinline__ cplx phase_of<cplx>(cplx g, double mag) {
+  return make_double2(g.x / mag, -g.y / mag);  // conj(g) / |g|
+}
+
+__device__ __forceinline__ int rr_player(int pos, int t, int m) {
+  // circle method: position 0 fixed, the others rotate
+  return pos == 0 ? 0 : ((pos - 1 + t) % m) + 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) jacobi_kernel(int k, const T* A, long strideA,
+                                                     double* s_out, T* U, T* V,
+                                                     int want_uv, T* work,
+                                                     int max_sweeps, int* err) {
+  const int b = blockIdx.x;
+  T* a = work + (long)b * 2 * k * k;   // column c of A at a[c*k .. c*k+k)
+  T* v = a + (long)k * k;              // column c of V
+  const T* Ab = A + b * strideA;
+  const T one = [] {
+    if constexpr (sizeof(T) == 8) return T(1.0);
+    else return make_double2(1.0, 0.0);
+  }();
+  for (long idx = threadIdx.x; idx < (long)k * k; idx += blockDim.x) {
+    const int r = (int)(idx / k), c = (int)(idx % k);
+    a[(long)c * k + r] = Ab[idx];
+    if (want_uv) v[(long)c * k + r] = (r == c) ? one : zero_of(T());
+  }
+  __shared__ unsigned long long off_bits;
+  __shared__ int done;
+  __syncthreads();
+  const double tol = fmax(1.0, (double)k) * DBL_EPSILON;
+  const int kk = k + (k & 1), m = kk - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  int sweep = 0;
+  if (threadIdx.x == 0) done = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) off_bits = 0ull;
+    __syncthreads();
+    for (int t = 0; t < m; ++t) {
+      for (int pr = warp; pr < kk / 2; pr += nwarps) {
+        int p = rr_player(pr, t, m), q = rr_player(kk - 1 - pr, t, m);
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        if (q >= k) continue;
+        T* ap = a + (long)p * k;
+        T* aq = a + (long)q * k;
+        double al = 0.0, be = 0.0;
+        T ga = zero_of(T());
+        for (int r = lane; r < k; r += 32) {
+          const T x = ap[r], y = aq[r];
+          al += absq(x);
+          be += absq(y);
+          fmacv(ga, x, y);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        const double g = sqrt(absq(ga));
+        const double nrm = sqrt(al) * sqrt(be);
+        if (!(g > tol * nrm) || g == 0.0) continue;
+        if (lane == 0) atomicMax(&off_bits, (unsigned long long)__double_as_longlong(g / nrm));
+        const double zeta = (be - al) / (2.0 * g);
+        const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+        const double c = 1.0 / hypot(1.0, tt), s = c * tt;
+        const T eph = phase_of<T>(ga, g);
+        for (int r = lane; r < k; r += 32) {
+          const T x = ap[r], y = mulv(eph, aq[r]);
+          ap[r] = subv(scalev(x, c), scalev(y, s));
+          aq[r] = addv(scalev(x, s), scalev(y, c));
+        }
+        if (want_uv) {
+          T* vp = v + (long)p * k;
+          T* vq = v + (long)q * k;
+          for (int r = lane; r < k; r += 32) {
+            const T x = vp[r], y = mulv(eph, vq[r]);
+            vp[r] = subv(scalev(x, c), scalev(y, s));
+            vq[r] = addv(scalev(x, s), scalev(y, c));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const double off = __longlong_as_double((long long)off_bits);
+    __syncthreads();
+    if (off <= tol) break;
+  }
+  if (sweep == max_sweeps && threadIdx.x == 0) atomicOr(err, DEV_JACOBI_NOCONV);
+  // singular values and their descending order (ties: lower index first)
+  extern __shared__ double sv[];        // k values
+  int* rk = reinterpret_cast<int*>(sv + k);
+  for (int c = warp; c < k; c += nwarps) {
+    double acc = 0.0;
+    for (int r = lane; r < k; r += 32) acc += absq(a[(long)c * k + r]);
+    acc = warp_sum(acc);
+    if (lane == 0) sv[c] = sqrt(acc);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    int r = 0;
+    const double x = sv[c];
+    for (int j = 0; j < k; ++j) r += (sv[j] > x) || (sv[j] == x && j < c);
+    rk[c] = r;
+    if (!isfinite(x)) atomicOr(err, DEV_NONFINITE);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) s_out[(long)b * k + rk[c]] = sv[c];
+  if (!want_uv) return;
+  T* Ub = U + (long)b * k * k;
+  T* Vb = V + (long)b * k * k;
+  for (long idx = threadIdx.x; idx < (long)k * k; idx += blockDim.x) {
+    const int c = (int)(idx / k), r = (int)(idx % k);
+    const double sc = sv[c];
+    const T x = a[idx];
+    Ub[(long)r * k + rk[c]] = sc > 0.0 ? scalev(x, 1.0 / sc) : zero_of(T());
+    Vb[(long)r * k + rk[c]] = v[idx];
+  }
+  __syncthreads();
+  // exactly-zero singular values leave zero columns of U: complete U to a
+  // unitary by Gram-Schmidt against unit vectors (warp 0, rare path)
+  if (warp != 0) return;
+  int nzero = 0;
+  for (int c = 0; c < k; ++c) nzero += (sv[c] == 0.0);
+  if (nzero == 0) return;
+  int cand = 0;
+  for (int col = k - nzero; col < k; ++col) {
+    T* tmp = a;   // reuse the work area as a length-k scratch vector
+    for (; cand < k; ++cand) {
+      for (int r = lane; r < k; r += 32) tmp[r] = (r == cand) ? one : zero_of(T());
+      __syncwarp();
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int j = 0; j < col; ++j) {
+          T d = zero_of(T());
+          for (int r = lane; r < k; r += 32) fmacv(d, Ub[(long)r * k + j], tmp[r]);
+          d = warp_sum(d);
+          __syncwarp();
+          for (int r = lane; r < k; r += 32) tmp[r] = subv(tmp[r], mulv(Ub[(long)r * k + j], d));
+          __syncwarp();
+        }
+      }
+      double nn = 0.0;
+      for (int r = lane; r < k; r += 32) nn += absq(tmp[r]);
+      nn = warp_sum(nn);
+      if (nn > 0.25) {
+        const double inv = 1.0 / sqrt(nn);
+        for (int r = lane; r < k; r += 32) Ub[(long)r * k + col] = scalev(tmp[r], inv);
+        __syncwarp();
+        ++cand;
+        break;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------- phase fixing
+template <typename T>
+__global__ void colphase_kernel(long n, int ncol, long ld, const T* Z, long strideZ,
+                                T* ph) {
+  const int c = blockIdx.x, b = blockIdx.y;
+  const T* z = Z + b * strideZ;
+  double best = -1.0;
+  long bi = 0;
+  for (long r = threadIdx.x; r < n; r += blockDim.x) {
+    const double m = absq(z[r * ld + c]);
+    if (m > best) { best = m; bi = r; }
+  }
+  __shared__ double sb[256];
+  __shared__ long si[256];
+  sb[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double m2 = sb[threadIdx.x + o];
+      const long i2 = si[threadIdx.x + o];
+      if (m2 > sb[threadIdx.x] || (m2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sb[threadIdx.x] = m2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const T piv = z[si[0] * ld + c];
+    const double mag = sqrt(absq(piv));
+    T out;
+    if constexpr (sizeof(T) == 8) out = mag > 0.0 ? piv / mag : 1.0;
+    else out = mag > 0.0 ? make_double2(piv.x / mag, piv.y / mag) : make_double2(1.0, 0.0);
+    ph[(long)b * ncol + c] = out;
+  }
+}
+
+template <typename T>
+__global__ void scale_cols_kernel(long rows, int ncol, long ld, T* Z, const T* ph) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < rows * ncol;
+       idx += (long)gridDim.x * blockDim.x) {
+    const long r = idx / ncol;
+    const int c = (int)(idx % ncol);
+    Z[r * ld + c] = mulv(Z[r * ld + c], conjv(ph[c]));
+  }
+}
+
+template <typename T>
+__global__ void inv_sqrt_kernel(int k, int c, const T* V, const double* s, double cutoff,
+                                T* Vs) {
+  const double s0 = s[0];
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)k * c;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / c), j = (int)(idx % c);
+    const double sj = s[j];
+    const double f = (s0 > 0.0 && sj > cutoff * s0) ? 1.0 / sqrt(sj) : 0.0;
+    Vs[idx] = scalev(V[(long)i * k + j], f);
+  }
+}
+
+// ------------------------------------------------------------ normalise
+template <typename T>
+__global__ void sumsq_partial(long n, const T* x, long stride, double* part, int nblk) {
+  const int b = blockIdx.y;
+  const T* xb = x + b * stride;
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    acc += absq(xb[i]);
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[b * nblk + blockIdx.x] = acc;
+}
+
+__global__ void sumsq_final(const double* part, int nblk, double* nrm) {
+  const int b = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[b * nblk + i];
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) nrm[b] = sqrt(acc);
+}
+
+template <typename T>
+__global__ void scale_kernel(long n, T* x, long stride, const double* nrm) {
+  const int b = blockIdx.y;
+  const double inv = 1.0 / nrm[b];
+  T* xb = x + b * stride;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    xb[i] = scalev(xb[i], inv);
+}
+
+__global__ void spectra_delta_kernel(int c, int batch, double* snew, double* sold,
+                                     double* delta) {
+  __shared__ double sh[32];
+  double dmax = 0.0;
+  for (int b = 0; b < batch; ++b) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < c; i += blockDim.x) acc += snew[(long)b * c + i] * snew[(long)b * c + i];
+    acc = block_sum(acc, sh);
+    const double inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+    double d = 0.0;
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+      const double x = snew[(long)b * c + i] * inv;
+      const double e = x - sold[(long)b * c + i];
+      d += e * e;
+      snew[(long)b * c + i] = x;
+      sold[(long)b * c + i] = x;
+    }
+    d = block_sum(d, sh);
+    dmax = fmax(dmax, sqrt(d));
+  }
+  if (threadIdx.x == 0) delta[0] = dmax;
+}
+
+template <typename T>
+__global__ void add_identity_kernel(int k, T* G, double alpha, int batch) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)k * batch;
+       idx += (long)gridDim.x * blockDim.x) {
+    const long b = idx / k, i = idx % k;
+    T* g = G + b * k * k + i * k + i;
+    if constexpr (sizeof(T) == 8) *g += alpha;
+    else g->x += alpha;
+  }
+}
+
+template <typename T>
+__global__ void trace_products_kernel(int d2, const T* O, const T* R, double* out4) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  T tor = zero_of(T()), tr = zero_of(T());
+  for (int i = 0; i < d2; ++i) {
+    tr = addv(tr, R[(long)i * d2 + i]);
+    for (int j = 0; j < d2; ++j) fmav(tor, O[(long)i * d2 + j], R[(long)j * d2 + i]);
+  }
+  if constexpr (sizeof(T) == 8) {
+    out4[0] = tor; out4[1] = 0.0; out4[2] = tr; out4[3] = 0.0;
+  } else {
+    out4[0] = tor.x; out4[1] = tor.y; out4[2] = tr.x; out4[3] = tr.y;
+  }
+}
+
+unsigned grid_for(long n, int per = 256, long cap = 152L * 8) {
+  long g = (n + per - 1) / per;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+cudaError_t chol_inv(bool cx, int k, long n, bool shift, void* G, void* Linv,
+                     int batch, int* err, cudaStream_t s, long* launches) {
+  if (cx)
+    chol_inv_kernel<cplx><<<batch, 256, 0, s>>>(k, n, shift, (cplx*)G, (cplx*)Linv, err);
+  else
+    chol_inv_kernel<double><<<batch, 256, 0, s>>>(k, n, shift, (double*)G, (double*)Linv, err);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t jacobi_svd(bool cx, int k, const void* A, long strideA, double* sv,
+                       void* U, void* V, bool want_uv, void* work, int batch,
+                       int max_sweeps, int* err, cudaStream_t s, long* launches) {
+  const size_t shm = (size_t)k * (sizeof(double) + sizeof(int));
+  if (cx)
+    jacobi_kernel<cplx><<<batch, 512, shm, s>>>(k, (const cplx*)A, strideA, sv, (cplx*)U,
+                                                (cplx*)V, want_uv, (cplx*)work, max_sweeps, err);
+  else
+    jacobi_kernel<double><<<batch, 512, shm, s>>>(k, (const double*)A, strideA, sv,
+                                                  (double*)U, (double*)V, want_uv,
+                                                  (double*)work, max_sweeps, err);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t column_phase(bool cx, long n, int ncol, long ld, const void* Z, void* ph,
+                         int batch, long strideZ, cudaStream_t s, long* launches) {
+  dim3 grid(ncol, batch);
+  if (cx) colphase_kernel<cplx><<<grid, 256, 0, s>>>(n, ncol, ld, (const cplx*)Z, strideZ, (cplx*)ph);
+  else colphase_kernel<double><<<grid, 256, 0, s>>>(n, ncol, ld, (const double*)Z, strideZ, (double*)ph);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t scale_columns_conj(bool cx, long rows, int ncol, long ld, void* Z,
+                               const void* ph, cudaStream_t s, long* launches) {
+  if (cx) scale_cols_kernel<cplx><<<grid_for(rows * ncol), 256, 0, s>>>(rows, ncol, ld, (cplx*)Z, (const cplx*)ph);
+  else scale_cols_kernel<double><<<grid_for(rows * ncol), 256, 0, s>>>(rows, ncol, ld, (double*)Z, (const double*)ph);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t scale_by_inv_sqrt(bool cx, int k, int c, const void* V, const double* sv,
+                              double cutoff, void* Vs, cudaStream_t s, long* launches) {
+  if (cx) inv_sqrt_kernel<cplx><<<grid_for((long)k * c), 256, 0, s>>>(k, c, (const cplx*)V, sv, cutoff, (cplx*)Vs);
+  else inv_sqrt_kernel<double><<<grid_for((long)k * c), 256, 0, s>>>(k, c, (const double*)V, sv, cutoff, (double*)Vs);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t normalize(bool cx, long n, void* x, long stride, int batch, double* nrm,
+                      bool scale, void* work, cudaStream_t s, long* launches) {
+  int nblk = (int)((n + 255) / 256);
+  if (nblk > 152) nblk = 152;
+  if (nblk < 1) nblk = 1;
+  dim3 g(nblk, batch);
+  if (cx) sumsq_partial<cplx><<<g, 256, 0, s>>>(n, (const cplx*)x, stride, (double*)work, nblk);
+  else sumsq_partial<double><<<g, 256, 0, s>>>(n, (const double*)x, stride, (double*)work, nblk);
+  sumsq_final<<<batch, 256, 0, s>>>((const double*)work, nblk, nrm);
+  if (launches) *launches += 2;
+  if (scale) {
+    if (cx) scale_kernel<cplx><<<g, 256, 0, s>>>(n, (cplx*)x, stride, nrm);
+    else scale_kernel<double><<<g, 256, 0, s>>>(n, (double*)x, stride, nrm);
+    if (launches) ++*launches;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t spectra_delta(int c, int batch, double* snew, double* sold, double* delta,
+                          cudaStream_t s, long* launches) {
+  spectra_delta_kernel<<<1, 256, 0, s>>>(c, batch, snew, sold, delta);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t add_identity(bool cx, int k, void* G, double alpha, int batch, cudaStream_t s,
+                         long* launches) {
+  if (cx) add_identity_kernel<cplx><<<grid_for((long)k * batch), 256, 0, s>>>(k, (cplx*)G, alpha, batch);
+  else add_identity_kernel<double><<<grid_for((long)k * batch), 256, 0, s>>>(k, (double*)G, alpha, batch);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t trace_products(bool cx, int d2, const void* O, const void* R, double* out4,
+                           cudaStream_t s, long* launches) {
+  if (cx) trace_products_kernel<cplx><<<1, 32, 0, s>>>(d2, (const cplx*)O, (const cplx*)R, out4);
+  else trace_products_kernel<double><<<1, 32, 0, s>>>(d2, (const double*)O, (const double*)R, out4);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace ctm

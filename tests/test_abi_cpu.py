@@ -1,0 +1,51 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/ctm.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2607_15158_gb300 as pkg
+from paper_2607_15158_gb300 import build as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "ctm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(pkg.LIB_PATH):
+        B.build()
+    return ctypes.CDLL(pkg.LIB_PATH)
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ctm_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("ctm_init", "ctm_move", "ctm_converge", "ctm_expect", "ctm_free"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_opts_without_gpu(lib):
+    o = pkg.ctm_default_opts()
+    assert (o.p, o.si_rounds, o.method, o.prec, o.normalize, o.sign_fix) == (5, 1, 0, 0, 1, 1)
+    assert o.svd_rel_cutoff == 1e-14
+
+
+def test_argument_errors_are_reported_before_device_work(lib):
+    pkg.load()
+    ptr = ctypes.c_void_p()
+    st = pkg._lib.ctm_init(ctypes.byref(ptr), 0, 1, None, None, 0, 2, 2, 4, None)
+    assert st == pkg.CTM_EINVAL
+    assert b"must be >= 1" in pkg._lib.ctm_last_error(None)

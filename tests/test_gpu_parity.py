@@ -1,0 +1,194 @@
+"""GPU (C ABI, FP64 path) vs the CPU oracle on the same seeded inputs.
+
+Compared quantities are gauge invariant: unit-normalised corner spectra, bond
+energies, the oblique projector P_l P_r of every cut of the last move, Ising
+free energy / magnetisation / correlations. Tolerance 1e-10 (relative to the
+largest entry for matrices), the FP64 bar.
+"""
+import numpy as np
+import pytest
+
+import ctm_synth as S
+import paper_2607_15158_gb300 as pkg
+from oracle import ctmrg, ising
+
+pytestmark = pytest.mark.gpu
+HEIS = S.heisenberg_bond()
+TOL = 1e-10
+
+
+def _pair(Lx, Ly, d, D, chi, p, cplx, rounds, seed=0, diag=0.0):
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, seed=seed, diag_weight=diag)
+    Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx, seed=1)
+    N = chi * D * D
+    k = min(chi + p, N)
+    X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx, seed=2)
+    ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx,
+                       opts=pkg.ctm_default_opts(p=p, si_rounds=rounds))
+    ctx.ctm_set_env(Cs, Ts)
+    ctx.ctm_set_rangefinders(X0, W0)
+    ref = ctmrg.CTM(Lx, Ly, A, [a.conj() for a in A], Cs, Ts, chi, method="si", p=p,
+                    si_rounds=rounds, X0=X0, W0=W0)
+    return ctx, ref
+
+
+def _compare(ctx, ref, energies=True):
+    Lx, Ly = ref.Lx, ref.Ly
+    spec = ref.spectra()
+    for lab in range(4):
+        for y in range(Ly):
+            for x in range(Lx):
+                s = ctx.ctm_spectrum(x, y, lab + 1)
+                assert np.abs(s - spec[lab][y * Lx + x]).max() < TOL, (lab, x, y)
+    # oblique projectors of every cut of the last move (direction 3)
+    f = ctmrg.Frame(Lx, Ly, 3)
+    for y in range(f.Ly):
+        for x in range(f.Lx):
+            Pl, PrH = ctx.ctm_get_projectors(3, x, y)
+            Pi = Pl @ PrH.conj().T
+            d = ref.last[(3, x, y)]
+            Pi_ref = d["Pl"] @ d["Pr"]
+            assert np.abs(Pi - Pi_ref).max() / np.abs(Pi_ref).max() < TOL
+            eye = PrH.conj().T @ Pl
+            assert np.abs(eye - np.eye(eye.shape[0])).max() < 1e-9
+    if energies:
+        for y in range(Ly):
+            for x in range(Lx):
+                for direction in (0, 1):
+                    e = ctx.ctm_expect(HEIS, x, y, direction)
+                    e_ref = ref.expect2(HEIS, x, y, direction)
+                    assert abs(e - e_ref) < TOL, (x, y, direction, e, e_ref)
+
+
+@pytest.mark.parametrize("case", [
+    # Lx, Ly, d, D, chi, p, complex, rounds, iterations
+    (1, 1, 2, 2, 8, 5, False, 2, 3),
+    (2, 1, 2, 2, 10, 5, True, 1, 2),
+    (2, 2, 2, 3, 12, 5, False, 1, 2),      # N = 108: two GEMM tiles, ragged tail
+    (1, 1, 2, 3, 20, 5, True, 1, 2),       # N = 180, k = 25
+    (3, 3, 2, 2, 9, 5, True, 1, 1),        # the 3x3 cell of the large workloads
+    (1, 2, 3, 2, 1, 2, True, 1, 2),        # chi = 1, d = 3
+])
+def test_si_moves_match_oracle(case):
+    Lx, Ly, d, D, chi, p, cplx, rounds, iters = case
+    ctx, ref = _pair(Lx, Ly, d, D, chi, p, cplx, rounds)
+    for _ in range(iters):
+        for r in range(4):
+            ctx.ctm_move(r)
+        ref.iteration()
+    _compare(ctx, ref)
+    ctx.ctm_free()
+
+
+def test_single_moves_each_direction():
+    ctx, ref = _pair(2, 3, 2, 2, 6, 4, True, 1)
+    for r in (2, 0, 3, 1, 1):
+        ctx.ctm_move(r)
+        ref.left_move(r)
+    spec = ref.spectra()
+    for lab in range(4):
+        for i in range(6):
+            s = ctx.ctm_spectrum(i % 2, i // 2, lab + 1)
+            assert np.abs(s - spec[lab][i]).max() < TOL
+    ctx.ctm_free()
+
+
+def test_cfg1_workload_converges_like_the_oracle():
+    """1x1 cell, real A[2,3,3,3,3], chi = 27, p = 5, 2 SI rounds, to
+    Delta < 1e-10 (the small workload of the benchmark suite)."""
+    w = S.WORKLOADS["cfg1_1x1_D3_chi27"]
+    ctx, ref = _pair(1, 1, 2, 3, 27, 5, False, 2)
+    it, delta, ok = ctx.ctm_converge(1e-10, 200)
+    assert ok and delta < 1e-10
+    it_ref, d_ref = ref.converge(1e-10, 200)
+    assert it == it_ref
+    _compare(ctx, ref)
+    ctx.ctm_free()
+
+
+def _ising_ctx(beta, chi, rounds=2):
+    a = S.ising_tensor(beta)
+    ket, bra = S.classical_as_ket(a)
+    Cs, Ts = S.initial_env(1, 1, chi, 2, 1, seed=1)
+    N, k = 2 * chi, min(chi + 5, 2 * chi)
+    X0, W0 = S.initial_rangefinders(1, 1, N, k, seed=2)
+    ctx = pkg.ctm_init_network(1, 1, [a], chi, opts=pkg.ctm_default_opts(si_rounds=rounds))
+    ctx.ctm_set_env(Cs, Ts)
+    ctx.ctm_set_rangefinders(X0, W0)
+    ref = ctmrg.CTM(1, 1, [ket], [bra], Cs, Ts, chi, method="si", p=5, si_rounds=rounds,
+                    X0=X0, W0=W0)
+    return ctx, ref
+
+
+def test_ising_onsager_on_gpu():
+    beta = 0.40
+    ctx, ref = _ising_ctx(beta, 27)
+    it, delta, ok = ctx.ctm_converge(1e-11, 300)
+    ref.converge(1e-11, 300)
+    f = ctx.ctm_free_energy()
+    assert abs(f - ising.onsager_lnz(beta)) < 1e-11
+    assert abs(f - ref.free_energy()) < 1e-12
+    imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)
+    for direction in (0, 1):
+        ss = ctx.ctm_expect_bond(imp, imp, 0, 0, direction).real
+        assert abs(ss - ising.nn_correlation(beta)) < 1e-9
+    ctx.ctm_free()
+
+
+def test_ising_yang_on_gpu():
+    beta = 0.50
+    ctx, ref = _ising_ctx(beta, 27)
+    ctx.ctm_converge(1e-11, 300)
+    ref.converge(1e-11, 300)
+    imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)
+    m = ctx.ctm_expect_site(imp, 0, 0).real
+    assert abs(abs(m) - ising.yang_m(beta)) < 1e-10
+    assert abs(m - ref.site_ratio(0, 0, imp)) < 1e-10
+    ctx.ctm_free()
+
+
+def test_product_states_on_gpu():
+    """D = 1: rho has exactly-zero singular values (cutoff and the unitary
+    completion of u in the Jacobi SVD); bond energies are <S>_i . <S>_j."""
+    Lx, Ly, chi = 3, 2, 4
+    A = S.product_state_tensors(Lx, Ly, seed=4)
+    Cs, Ts = S.initial_env(Lx, Ly, chi, 1, 1, complex_=True, seed=1)
+    X0, W0 = S.initial_rangefinders(Lx, Ly, chi, chi, complex_=True, seed=2)
+    ctx = pkg.ctm_init(Lx, Ly, A, 2, 1, chi, cplx=True)
+    ctx.ctm_set_env(Cs, Ts)
+    ctx.ctm_set_rangefinders(X0, W0)
+    for _ in range(3):
+        for r in range(4):
+            ctx.ctm_move(r)
+    ops = S.spin_ops()
+    phis = [a.reshape(2) for a in A]
+    sv = [np.array([np.vdot(p, o @ p).real for o in ops]) for p in phis]
+    for y in range(Ly):
+        for x in range(Lx):
+            i = y * Lx + x
+            for direction, j in ((0, y * Lx + (x + 1) % Lx), (1, ((y + 1) % Ly) * Lx + x)):
+                e = ctx.ctm_expect(HEIS, x, y, direction)
+                assert abs(e - sv[i] @ sv[j]) < 1e-12
+    ctx.ctm_free()
+
+
+def test_rdm2_matches_oracle():
+    ctx, ref = _pair(2, 2, 2, 2, 8, 5, True, 1)
+    for r in range(4):
+        ctx.ctm_move(r)
+    ref.iteration()
+    for direction in (0, 1):
+        R = ctx.ctm_rdm2(1, 0, direction)
+        assert np.abs(R - ref.rdm2(1, 0, direction)).max() < TOL
+    ctx.ctm_free()
+
+
+def test_errors_are_status_codes():
+    A = S.ipeps_tensors(1, 1, 2, 2, seed=0)
+    ctx = pkg.ctm_init(1, 1, A, 2, 2, 4)
+    with pytest.raises(pkg.CTMError) as e:
+        ctx.ctm_move(7)
+    assert e.value.status == pkg.CTM_EINVAL
+    with pytest.raises(pkg.CTMError):
+        ctx.ctm_free_energy() if False else ctx.ctm_get_projectors(0, 0, 0)
+    ctx.ctm_free()
