@@ -26,11 +26,19 @@ Readings where the paper is silent (each listed in the design notes):
   so the paper's half-systems are H_R = Q1 Q2 (its C2~ C3~) and
   H_L = Q3 Q4 (its C4~ C1~), and M = H_L H_R;
 * complex tensors: M^T -> M^dagger; Y is stored as W = Y^dagger (N x k);
-* sign fix: for every column i of the left singular vectors (U_i for the
-  standard SVD, (W u)_i for SI) the entry of largest modulus (lowest row on a
-  tie) is made real positive; the same phase multiplies v_i;
-* s^-1/2 is set to 0 for s_i <= cutoff * s_1 (default cutoff 1e-14);
-* C and T are divided by their Frobenius norm after each move;
+* sign fix: for every column i of the left singular vectors (U_i of M for
+  the standard SVD, u_i of the small SVD of rho for SI) the entry of largest
+  modulus (lowest row on a tie) is made real positive; v_i takes the same
+  phase. For SI this anchors the gauge of the new bond in the recycled bases
+  (u ~ I near the fixed point), which is what lets X, W be recycled;
+* QR: Z = Q R with R normalised to a real positive diagonal (unique Q);
+* the rangefinder update applies a QR after each application of M or M^H
+  (same span as qr(M^H M X), without squaring cond(M) first);
+* s^-1/2 is set to 0 for s_i <= cutoff * s_1 (default cutoff 1e-12: the
+  singular values of M, a product of four corners, have an fp64 noise floor
+  near 1e-14 s_1 that s^-1/2 would amplify);
+* C and T are divided by their Frobenius norm after each move and their
+  largest-modulus entry (lowest flat index on a tie) is made real positive;
 * moves up / right / down are left moves of the cell rotated by 1 / 2 / 3
   counter-clockwise quarter turns;
 * convergence: Delta = max over corners and sites of ||s_new - s_old||_2 of
@@ -96,8 +104,15 @@ def enlarged_corner(C, Tb, Ta, A, B):
 
 
 def qr_q(Z):
-    """Orthonormal basis of span(Z) (Householder QR, reduced)."""
-    return np.linalg.qr(Z)[0]
+    """Q of the reduced QR Z = Q R normalised to a real positive diagonal of
+    R (Householder QR, then column phases); for a full-rank Z this Q is
+    unique."""
+    Q, R = np.linalg.qr(Z)
+    d = np.diagonal(R).copy()
+    ph = np.ones_like(d)
+    nz = np.abs(d) > 0
+    ph[nz] = d[nz] / np.abs(d[nz])
+    return Q * ph[None, :]
 
 
 def inv_sqrt(s, cutoff):
@@ -121,7 +136,7 @@ def sign_fix_phases(U):
     return ph
 
 
-def projectors_svd(Q1, Q2, Q3, Q4, chi, cutoff=1e-14, sign_fix=True):
+def projectors_svd(Q1, Q2, Q3, Q4, chi, cutoff=1e-12, sign_fix=True):
     """Standard truncated-SVD projectors (Eq. svd_projectors_diag).
 
     M = H_L H_R with H_L = Q3 Q4, H_R = Q1 Q2; M ~ U S V^dagger truncated to
@@ -156,13 +171,14 @@ def apply_Mh(Q1, Q2, Q3, Q4, Z):
     return h(Q2) @ (h(Q1) @ (h(Q4) @ (h(Q3) @ Z)))
 
 
-def projectors_si(Q1, Q2, Q3, Q4, X, W, chi, rounds=1, cutoff=1e-14,
+def projectors_si(Q1, Q2, Q3, Q4, X, W, chi, rounds=1, cutoff=1e-12,
                   sign_fix=True):
     """SI-CTMRG projectors with recycling (QR-based projector, steps 1-4).
 
     X (N x k, columns in M's column space) and W = Y^dagger (N x k, M's row
     space) are orthonormal on entry. Each round: X <- qr(M^H M X),
-    W <- qr(M M^H W) (Eq. xy_iter). Then Z_R = H_R X, Z_L = H_L^H W,
+    W <- qr(M M^H W) (Eq. xy_iter), with a QR after each application of M
+    or M^H (the span is the same; M^H M would square cond(M) before the QR). Then Z_R = H_R X, Z_L = H_L^H W,
     rho = Z_L^H Z_R = Y M X (Eq. rho_hat_diag), rho = u s v^H, truncated to
     chi; P_l = Z_R v_chi s^-1/2, P_r = s^-1/2 u_chi^H Z_L^H (Eq.
     projectors_diag); recycle X <- X v, W <- W u (Eq. xy_recycle).
@@ -170,21 +186,24 @@ def projectors_si(Q1, Q2, Q3, Q4, X, W, chi, rounds=1, cutoff=1e-14,
     Pinned by: P_r P_l = I (P5), span invariance (P6), SI -> SVD (P7),
     exact growth with k = N (P3)."""
     for _ in range(rounds):
-        X = qr_q(apply_Mh(Q1, Q2, Q3, Q4, apply_M(Q1, Q2, Q3, Q4, X)))
-        W = qr_q(apply_M(Q1, Q2, Q3, Q4, apply_Mh(Q1, Q2, Q3, Q4, W)))
+        # span(M^H M X) taken as qr(M^H qr(M X)): the same span, without
+        # squaring the condition number of M before the QR
+        X = qr_q(apply_Mh(Q1, Q2, Q3, Q4, qr_q(apply_M(Q1, Q2, Q3, Q4, X))))
+        W = qr_q(apply_M(Q1, Q2, Q3, Q4, qr_q(apply_Mh(Q1, Q2, Q3, Q4, W))))
     ZR = Q1 @ (Q2 @ X)
     ZL = Q4.conj().T @ (Q3.conj().T @ W)
     rho = ZL.conj().T @ ZR
     u, s_all, vh = np.linalg.svd(rho)
     v = vh.conj().T
-    Wn = W @ u
-    Xn = X @ v
     if sign_fix:
-        ph = sign_fix_phases(Wn).conj()
+        # sign fix of the small SVD (step 4): the largest-modulus entry of
+        # each column of u becomes real positive, v_i takes the same phase;
+        # near the fixed point u ~ I, so the recycled bases keep their gauge
+        ph = sign_fix_phases(u).conj()
         u = u * ph[None, :]
         v = v * ph[None, :]
-        Wn = Wn * ph[None, :]
-        Xn = Xn * ph[None, :]
+    Wn = W @ u
+    Xn = X @ v
     c = min(chi, s_all.size)
     s = s_all[:c]
     si = inv_sqrt(s, cutoff)
@@ -202,13 +221,16 @@ class CTM:
     [s, u, l, d, r]; the network tensor at a site is ket (x) bra summed over s.
     C[label][site] (chi x chi), T[label][site] (chi x chi x Dk x Db).
     method: "si" (SI-CTMRG) or "svd" (standard CTMRG).
+    warmup_iters, warmup_rounds: the first warmup_iters moves of each
+    direction use warmup_rounds subspace-iteration rounds (warm-up steps
+    before the recycled bases settle), later moves si_rounds.
     X0, W0: raw Gaussian N x k blocks per [direction][cut]; they are
     orthonormalised on first use (QR of a Gaussian matrix, step 1).
     """
 
     def __init__(self, Lx, Ly, kets, bras, C, T, chi, method="si", p=5,
-                 si_rounds=1, X0=None, W0=None, cutoff=1e-14, normalize=True,
-                 sign_fix=True):
+                 si_rounds=1, X0=None, W0=None, cutoff=1e-12, normalize=True,
+                 sign_fix=True, warmup_iters=0, warmup_rounds=8):
         self.Lx, self.Ly = Lx, Ly
         self.kets = [np.asarray(a) for a in kets]
         self.bras = [np.asarray(b) for b in bras]
@@ -225,6 +247,9 @@ class CTM:
         self.rf = {}          # (r, cut) -> (X, W), orthonormal
         self.last = {}        # (r, x, y) -> dict of diagnostics of the last cut
         self.log_norms = []   # log Frobenius norms divided out (normalize)
+        self.warmup_iters = warmup_iters
+        self.warmup_rounds = warmup_rounds
+        self.moves_done = [0, 0, 0, 0]   # moves per direction
 
     # -- frame accessors
     def _get(self, f, kind, i, x, y):
@@ -286,8 +311,10 @@ class CTM:
         dtype = np.result_type(Q1, Q2, Q3, Q4)
         cut = (y % f.Ly) * f.Lx + (x % f.Lx)
         X, W = self._rangefinder(f.r, cut, Nc, Nr, k, dtype)
+        rounds = (self.warmup_rounds if self.moves_done[f.r] < self.warmup_iters
+                  else self.si_rounds)
         Pl, Pr, s, Xn, Wn, s_all = projectors_si(
-            Q1, Q2, Q3, Q4, X, W, self.chi, self.si_rounds, self.cutoff,
+            Q1, Q2, Q3, Q4, X, W, self.chi, rounds, self.cutoff,
             self.sign_fix)
         # principal angles between the old and new leading chi-subspaces
         c = min(self.chi, k)
@@ -298,11 +325,17 @@ class CTM:
         return Pl, Pr
 
     def _norm(self, t):
+        """Unit Frobenius norm and a real positive largest-modulus entry
+        (lowest flat index on a tie): fixes the free scale and phase of
+        each new tensor so that C and T can converge element-wise."""
         if not self.normalize:
             return t
         n = np.linalg.norm(t)
         self.log_norms.append(np.log(n))
-        return t / n
+        flat = t.reshape(-1)
+        piv = flat[np.argmax(np.abs(flat))]
+        ph = piv / abs(piv) if abs(piv) > 0 else 1.0
+        return t * (np.conj(ph) / n)
 
     def left_move(self, r):
         """Left move of the frame turned by r quarter turns (End Matter):
@@ -345,6 +378,7 @@ class CTM:
                 self._set(f, "C", 0, x + 1, y, self._norm(C1n))
                 self._set(f, "T", 3, x + 1, y, self._norm(T4n))
                 self._set(f, "C", 3, x + 1, y, self._norm(C4n))
+        self.moves_done[f.r] += 1
 
     def move(self, direction):
         r = MOVES[direction] if isinstance(direction, str) else int(direction)
