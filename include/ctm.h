@@ -75,17 +75,20 @@ typedef enum { CTM_PROJ_SI = 0, CTM_PROJ_SVD = 1 } ctm_method;
 typedef struct {
   int p;                  /* oversampling, k = chi + p (paper: p = 5) */
   int si_rounds;          /* subspace-iteration rounds per projector */
+  int warmup_iters;       /* first moves per direction that use ... */
+  int warmup_rounds;      /* ... this many rounds (warm-up, paper step 4) */
   ctm_method method;      /* CTM_PROJ_SI or CTM_PROJ_SVD */
   ctm_prec prec;          /* arithmetic of the large contractions */
   double svd_rel_cutoff;  /* s^-1/2 := 0 for s_i <= cutoff * s_1 */
-  int normalize;          /* divide C, T by their Frobenius norm per move */
-  int sign_fix;           /* fix the phase of every singular vector */
+  int normalize;          /* new C, T: unit Frobenius norm, largest entry
+                             real positive */
+  int sign_fix;           /* phase fix of the small SVD of rho */
   uint64_t seed;          /* seed of the default random C, T, X, W */
   void* stream;           /* cudaStream_t to run on, NULL = a private stream */
 } ctm_opts;
 
-/* Defaults: p = 5, si_rounds = 1, SI, FP64, cutoff 1e-14, normalize = 1,
- * sign_fix = 1, seed = 0, stream = NULL. */
+/* Defaults: p = 5, si_rounds = 1, warmup_iters = 5, warmup_rounds = 8, SI,
+ * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0, stream = NULL. */
 void ctm_default_opts(ctm_opts* opts);
 
 /* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz

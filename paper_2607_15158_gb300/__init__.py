@@ -27,7 +27,8 @@ CTM_PROJ_SI, CTM_PROJ_SVD = 0, 1
 
 
 class ctm_opts(C.Structure):
-    _fields_ = [("p", C.c_int), ("si_rounds", C.c_int), ("method", C.c_int),
+    _fields_ = [("p", C.c_int), ("si_rounds", C.c_int), ("warmup_iters", C.c_int),
+                ("warmup_rounds", C.c_int), ("method", C.c_int),
                 ("prec", C.c_int), ("svd_rel_cutoff", C.c_double),
                 ("normalize", C.c_int), ("sign_fix", C.c_int),
                 ("seed", C.c_uint64), ("stream", C.c_void_p)]

@@ -105,6 +105,10 @@ struct ctm_ctx {
   void* rho2 = nullptr;        // d^4 two-site density matrix
   void* imp[2] = {nullptr};    // impurity kets
   int* err = nullptr;
+  int* dead = nullptr;         // k flags of the CholeskyQR repair
+  void* fac = nullptr;         // per-tensor normalisation factors
+  uint64_t qr_calls = 0;       // counter of the repair directions
+  int moves_done[4] = {0, 0, 0, 0};
   bool spectra_init = false;
   // split-precision state
   SplitCtx* split = nullptr;
@@ -395,6 +399,11 @@ ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, 
 // by two CholeskyQR passes (CholeskyQR3, Fukaya et al. 2020). Only the span
 // enters the projectors (paper step 1), so R is not kept.
 ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp) {
+  // the first two passes also find columns that are numerically in the span
+  // of the previous ones (rank-deficient block: D = 1 states, fast decaying
+  // spectra) and refill them with pseudo-random directions, so that the last
+  // plain pass always sees a full-rank block
+  ++c->qr_calls;
   for (int pass = 0; pass < 3; ++pass) {
     GemmDesc g;
     g.opA = c->cx ? OP_C : OP_T;
@@ -404,8 +413,8 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp) {
     g.B = Zm; g.ldb = c->k;
     g.C = c->G; g.ldc = c->k;
     CK(gemm(c, g));
-    CTM_CUDA_OK(chol_inv(c->cx, c->k, c->N, pass == 0, c->G, c->Linv, 1, c->err, c->stream,
-                         &c->launches));
+    CTM_CUDA_OK(chol_inv(c->cx, c->k, c->N, pass == 0, c->G, c->Linv, 1,
+                         pass < 2 ? c->dead : nullptr, c->err, c->stream, &c->launches));
     GemmDesc h;
     h.opA = OP_N;
     h.opB = c->cx ? OP_C : OP_T;
@@ -414,6 +423,10 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp) {
     h.B = c->Linv; h.ldb = c->k;
     h.C = tmp; h.ldc = c->k;
     CK(gemm(c, h));
+    if (pass < 2)
+      CTM_CUDA_OK(repair_dead_columns(c->cx, c->N, c->k, tmp, c->dead,
+                                      (c->opts.seed * 1000003ull + c->qr_calls) * 4 + pass,
+                                      c->stream, &c->launches));
     CTM_CUDA_OK(cudaMemcpyAsync(Zm, tmp, (size_t)c->N * c->k * c->es, cudaMemcpyDeviceToDevice,
                                 c->stream));
   }
@@ -448,23 +461,29 @@ ctm_status si_projectors(ctm_ctx* c, int r, int cut, void* Pl, void* PrH) {
     CK(qr_inplace(c, W, Z[0]));
     ready = 1;
   }
-  for (int round = 0; round < c->opts.si_rounds; ++round) {
+  const int rounds =
+      c->moves_done[r] < c->opts.warmup_iters ? c->opts.warmup_rounds : c->opts.si_rounds;
+  for (int round = 0; round < rounds; ++round) {
+    // X <- qr(M^H qr(M X)): the span of M^H M X without squaring cond(M)
     CK(apply_corner(c, Q[1], false, X, Z[0]));
     CK(apply_corner(c, Q[0], false, Z[0], Z[1]));
     CK(apply_corner(c, Q[3], false, Z[1], Z[0]));
     CK(apply_corner(c, Q[2], false, Z[0], Z[1]));
+    CK(qr_inplace(c, Z[1], Z[0]));
     CK(apply_corner(c, Q[2], true, Z[1], Z[0]));
-    CK(apply_corner(c, Q[3], true, Z[0], Z[1]));
-    CK(apply_corner(c, Q[0], true, Z[1], Z[0]));
+    CK(apply_corner(c, Q[3], true, Z[0], Z[2]));
+    CK(apply_corner(c, Q[0], true, Z[2], Z[0]));
     CK(apply_corner(c, Q[1], true, Z[0], X));
     CK(qr_inplace(c, X, Z[0]));
+    // W <- qr(M qr(M^H W))
     CK(apply_corner(c, Q[2], true, W, Z[0]));
     CK(apply_corner(c, Q[3], true, Z[0], Z[1]));
     CK(apply_corner(c, Q[0], true, Z[1], Z[0]));
     CK(apply_corner(c, Q[1], true, Z[0], Z[1]));
+    CK(qr_inplace(c, Z[1], Z[0]));
     CK(apply_corner(c, Q[1], false, Z[1], Z[0]));
-    CK(apply_corner(c, Q[0], false, Z[0], Z[1]));
-    CK(apply_corner(c, Q[3], false, Z[1], Z[0]));
+    CK(apply_corner(c, Q[0], false, Z[0], Z[2]));
+    CK(apply_corner(c, Q[3], false, Z[2], Z[0]));
     CK(apply_corner(c, Q[2], false, Z[0], W));
     CK(qr_inplace(c, W, Z[0]));
   }
@@ -478,15 +497,15 @@ ctm_status si_projectors(ctm_ctx* c, int r, int cut, void* Pl, void* PrH) {
   CK(mm_small(c, opH, OP_N, k, k, c->N, Z[3], k, Z[2], k, c->rho, k));
   CTM_CUDA_OK(jacobi_svd(c->cx, k, c->rho, 0, c->sv, c->u, c->v, true, c->jw, 1, 80, c->err,
                          c->stream, &c->launches));
-  CK(mm_small(c, OP_N, OP_N, c->N, k, k, X, k, c->v, k, c->Xn, k));
-  CK(mm_small(c, OP_N, OP_N, c->N, k, k, W, k, c->u, k, c->Wn, k));
   if (c->opts.sign_fix) {
-    CTM_CUDA_OK(column_phase(c->cx, c->N, k, k, c->Wn, c->ph, 1, 0, c->stream, &c->launches));
-    CTM_CUDA_OK(scale_columns_conj(c->cx, c->N, k, k, c->Wn, c->ph, c->stream, &c->launches));
-    CTM_CUDA_OK(scale_columns_conj(c->cx, c->N, k, k, c->Xn, c->ph, c->stream, &c->launches));
+    // sign fix of the small SVD (step 4): largest-modulus entry of each
+    // column of u real positive, v_i takes the same phase
+    CTM_CUDA_OK(column_phase(c->cx, k, k, k, c->u, c->ph, 1, 0, c->stream, &c->launches));
     CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, c->u, c->ph, c->stream, &c->launches));
     CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, c->v, c->ph, c->stream, &c->launches));
   }
+  CK(mm_small(c, OP_N, OP_N, c->N, k, k, X, k, c->v, k, c->Xn, k));
+  CK(mm_small(c, OP_N, OP_N, c->N, k, k, W, k, c->u, k, c->Wn, k));
   CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, c->v, c->sv, c->opts.svd_rel_cutoff, c->Vs,
                                 c->stream, &c->launches));
   CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, c->u, c->sv, c->opts.svd_rel_cutoff, c->Us,
@@ -578,27 +597,28 @@ ctm_status move_impl(ctm_ctx* c, int r) {
                                   NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
     }
     for (int y = 0; y < Lyf; ++y) CK(absorb_site(c, r, x, y, Lyf));
+    if (c->opts.normalize) {
+      const size_t mark = c->scratch_off;
+      void* w = scratch_alloc(c, (size_t)3 * 152 * Lyf * sizeof(double));
+      if (!w) return fail(c, CTM_ENOMEM, "scratch arena too small for the norms");
+      CTM_CUDA_OK(normalize_phase(c->cx, elems_C(c), c->stC1, elems_C(c), Lyf, c->fac, w,
+                                  c->stream, &c->launches));
+      CTM_CUDA_OK(normalize_phase(c->cx, elems_C(c), c->stC4, elems_C(c), Lyf, c->fac, w,
+                                  c->stream, &c->launches));
+      CTM_CUDA_OK(normalize_phase(c->cx, elems_T(c), c->stT4, elems_T(c), Lyf, c->fac, w,
+                                  c->stream, &c->launches));
+      c->scratch_off = mark;
+    }
     for (int y = 0; y < Lyf; ++y) {
-      void* dC1 = fC(c, r, 0, x + 1, y);
-      void* dT4 = fT(c, r, 3, x + 1, y);
-      void* dC4 = fC(c, r, 3, x + 1, y);
-      CTM_CUDA_OK(cudaMemcpyAsync(dC1, at(c->stC1, y * elems_C(c), c), elems_C(c) * c->es,
-                                  cudaMemcpyDeviceToDevice, c->stream));
-      CTM_CUDA_OK(cudaMemcpyAsync(dT4, at(c->stT4, y * elems_T(c), c), elems_T(c) * c->es,
-                                  cudaMemcpyDeviceToDevice, c->stream));
-      CTM_CUDA_OK(cudaMemcpyAsync(dC4, at(c->stC4, y * elems_C(c), c), elems_C(c) * c->es,
-                                  cudaMemcpyDeviceToDevice, c->stream));
-      if (c->opts.normalize) {
-        const size_t mark = c->scratch_off;
-        void* w = scratch_alloc(c, 152 * sizeof(double));
-        if (!w) return fail(c, CTM_ENOMEM, "scratch arena too small for the norms");
-        CTM_CUDA_OK(normalize(c->cx, elems_C(c), dC1, 0, 1, c->dscal, true, w, c->stream, &c->launches));
-        CTM_CUDA_OK(normalize(c->cx, elems_T(c), dT4, 0, 1, c->dscal, true, w, c->stream, &c->launches));
-        CTM_CUDA_OK(normalize(c->cx, elems_C(c), dC4, 0, 1, c->dscal, true, w, c->stream, &c->launches));
-        c->scratch_off = mark;
-      }
+      CTM_CUDA_OK(cudaMemcpyAsync(fC(c, r, 0, x + 1, y), at(c->stC1, y * elems_C(c), c),
+                                  elems_C(c) * c->es, cudaMemcpyDeviceToDevice, c->stream));
+      CTM_CUDA_OK(cudaMemcpyAsync(fT(c, r, 3, x + 1, y), at(c->stT4, y * elems_T(c), c),
+                                  elems_T(c) * c->es, cudaMemcpyDeviceToDevice, c->stream));
+      CTM_CUDA_OK(cudaMemcpyAsync(fC(c, r, 3, x + 1, y), at(c->stC4, y * elems_C(c), c),
+                                  elems_C(c) * c->es, cudaMemcpyDeviceToDevice, c->stream));
     }
   }
+  c->moves_done[r] += 1;
   c->last_dir = r;
   return CTM_OK;
 }
@@ -654,6 +674,7 @@ ctm_status upload_default_state(ctm_ctx* c) {
   CTM_CUDA_OK(cudaMemcpy(c->W, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
   c->spectra_init = false;
+  for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
   return CTM_OK;
 }
 
@@ -674,7 +695,8 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   c->es = cx ? 16 : 8;
   if (opts) c->opts = *opts;
   else ctm_default_opts(&c->opts);
-  if (c->opts.p < 0 || c->opts.si_rounds < 0) {
+  if (c->opts.p < 0 || c->opts.si_rounds < 0 || c->opts.warmup_iters < 0 ||
+      c->opts.warmup_rounds < 0) {
     delete c;
     g_cur = nullptr;
     return fail(nullptr, CTM_EINVAL, "p and si_rounds must be >= 0");
@@ -752,6 +774,8 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->imp[0], nk * es);
   AL(c->imp[1], nk * es);
   AL(c->err, sizeof(int));
+  AL(c->dead, k * sizeof(int));
+  AL(c->fac, Lmax * es);
 #undef AL
   if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess)
     return bail(fail(c, CTM_ECUDA, "cudaMemset failed"));
@@ -935,9 +959,11 @@ void ctm_default_opts(ctm_opts* o) {
   if (!o) return;
   o->p = 5;
   o->si_rounds = 1;
+  o->warmup_iters = 5;
+  o->warmup_rounds = 8;
   o->method = CTM_PROJ_SI;
   o->prec = CTM_PREC_FP64;
-  o->svd_rel_cutoff = 1e-14;
+  o->svd_rel_cutoff = 1e-12;
   o->normalize = 1;
   o->sign_fix = 1;
   o->seed = 0;
@@ -983,6 +1009,7 @@ ctm_status ctm_set_rangefinders(ctm_ctx* c, const void* X, const void* W) {
   CTM_CUDA_OK(cudaMemcpyAsync(c->W, W, n, cudaMemcpyHostToDevice, c->stream));
   CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
+  for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
   return CTM_OK;
 }
 

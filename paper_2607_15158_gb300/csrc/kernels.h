@@ -45,8 +45,23 @@ cudaError_t dot64(bool cx, bool conj_x, long n, const void* x, long sx,
 // matrix: G is k x k (ld k), overwritten by L; Linv receives L^-1. With
 // shift != 0 the shift is 11 (n k + k (k + 1)) u trace(G) (shifted
 // CholeskyQR, Fukaya et al. 2020); n is the row count of the factored block.
+// With dead != NULL a column that lies numerically in the span of the
+// previous ones (shifted pass: residual below 1e-9 of the shift; plain pass:
+// pivot below 1e-10 of its squared norm) is marked dead[j] = 1 and excluded
+// (unit column of L); repair_dead_columns then refills it.
 cudaError_t chol_inv(bool cx, int k, long n, bool shift, void* G, void* Linv,
-                     int batch, int* err, cudaStream_t s, long* launches);
+                     int batch, int* dead, int* err, cudaStream_t s, long* launches);
+
+// Overwrite the dead columns of a rows x k matrix with deterministic
+// pseudo-random entries (a counter-based hash of seed, column, row).
+cudaError_t repair_dead_columns(bool cx, long rows, int k, void* Q, const int* dead,
+                                uint64_t seed, cudaStream_t s, long* launches);
+
+// Per tensor (batch, stride): x <- x * conj(phase of its largest-modulus
+// entry, lowest index on ties) / ||x||_F. work: 3 * 152 * batch doubles;
+// fac: batch elements.
+cudaError_t normalize_phase(bool cx, long n, void* x, long stride, int batch, void* fac,
+                            void* work, cudaStream_t s, long* launches);
 
 // One-sided Jacobi SVD (Hestenes) of k x k row-major matrices, one block per
 // matrix: A = U diag(s) V^H with s descending; U, V row-major k x k. work

@@ -32,18 +32,25 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // ------------------------------------------------------------ Cholesky
 template <typename T>
 __global__ void __launch_bounds__(256) chol_inv_kernel(int k, long n, int shift,
-                                                       T* G, T* Linv, int* err) {
+                                                       T* G, T* Linv, int* dead,
+                                                       int* err) {
   T* g = G + (long)blockIdx.x * k * k;
   T* L = Linv + (long)blockIdx.x * k * k;
   __shared__ double sh[32];
   __shared__ double piv;
-  __shared__ int bad;
+  __shared__ int bad, isdead;
+  extern __shared__ double orig[];      // k original diagonal entries
   if (threadIdx.x == 0) bad = 0;
+  double sft = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    orig[i] = realv(g[(long)i * k + i]);
+    if (dead) dead[(long)blockIdx.x * k + i] = 0;
+  }
   if (shift) {
     double tr = 0.0;
     for (int i = threadIdx.x; i < k; i += blockDim.x) tr += realv(g[(long)i * k + i]);
     tr = block_sum(tr, sh);
-    const double sft = 11.0 * ((double)n * k + (double)k * (k + 1)) * DBL_EPSILON * tr;
+    sft = 11.0 * ((double)n * k + (double)k * (k + 1)) * DBL_EPSILON * tr;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
       const double re = realv(g[(long)i * k + i]) + sft;
       if constexpr (sizeof(T) == 8) g[(long)i * k + i] = re;
@@ -54,7 +61,19 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int k, long n, int shift,
   for (int j = 0; j < k; ++j) {
     if (threadIdx.x == 0) {
       const double d = realv(g[(long)j * k + j]);
-      if (!(d > 0.0) || !isfinite(d)) {
+      isdead = 0;
+      // dead-column detection. Shifted pass: a column whose residual (pivot
+      // minus the shift) is below 1e-9 of the shift leaves the pass with a
+      // norm below ~3e-5 made of rounding noise; plain pass: a pivot below
+      // 1e-10 of the column's own squared norm. Either column lies
+      // numerically in the span of the previous ones.
+      const bool is_dead =
+          dead && (shift ? !(d - sft > fmax(1e-9 * sft, 8.0 * k * DBL_EPSILON * (orig[j] + sft)))
+                         : !(d > 1e-10 * orig[j]));
+      if (is_dead) {
+        isdead = 1;
+        piv = 1.0;
+      } else if (!(d > 0.0) || !isfinite(d)) {
         bad = 1;
         piv = 1.0;
       } else {
@@ -63,6 +82,18 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int k, long n, int shift,
     }
     __syncthreads();
     if (bad) break;
+    if (isdead) {
+      // unit column of L: the column is excluded from the elimination and
+      // replaced by a fresh direction after the product with L^-H
+      for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) g[(long)i * k + j] = zero_of(T());
+      if (threadIdx.x == 0) {
+        if constexpr (sizeof(T) == 8) g[(long)j * k + j] = 1.0;
+        else g[(long)j * k + j] = make_double2(1.0, 0.0);
+        dead[(long)blockIdx.x * k + j] = 1;
+      }
+      __syncthreads();
+      continue;
+    }
     const double dj = piv, inv = 1.0 / piv;
     for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
       g[(long)i * k + j] = scalev(g[(long)i * k + j], inv);
@@ -416,6 +447,102 @@ __global__ void trace_products_kernel(int d2, const T* O, const T* R, double* ou
   }
 }
 
+__device__ __forceinline__ double hash_uniform(uint64_t a, uint64_t b, uint64_t c) {
+  // splitmix64 finaliser of a counter: uniform in [-1, 1)
+  uint64_t z = a * 0x9E3779B97F4A7C15ull ^ (b + 0x632BE59BD9B4E019ull) * 0xBF58476D1CE4E5B9ull ^
+               (c + 0x8CB92BA72F3D8DD7ull) * 0x94D049BB133111EBull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+template <typename T>
+__global__ void repair_kernel(long rows, int k, T* Q, const int* dead, uint64_t seed) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < rows * k;
+       idx += (long)gridDim.x * blockDim.x) {
+    const long r = idx / k;
+    const int c = (int)(idx % k);
+    if (!dead[c]) continue;
+    const double x = hash_uniform(seed, (uint64_t)c, (uint64_t)r);
+    if constexpr (sizeof(T) == 8) Q[idx] = x;
+    else Q[idx] = make_double2(x, hash_uniform(seed ^ 0x5bd1e995ull, (uint64_t)c, (uint64_t)r));
+  }
+}
+
+// per tensor: sum of |x|^2 and the first index of the largest |x|
+template <typename T>
+__global__ void normph_partial(long n, const T* x, long stride, double* ps, double* pm,
+                               long* pi, int nblk) {
+  const int b = blockIdx.y;
+  const T* xb = x + b * stride;
+  double acc = 0.0, best = -1.0;
+  long bi = 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const double m = absq(xb[i]);
+    acc += m;
+    if (m > best) { best = m; bi = i; }
+  }
+  __shared__ double sm[256];
+  __shared__ long si[256];
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  sm[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double m2 = sm[threadIdx.x + o];
+      const long i2 = si[threadIdx.x + o];
+      if (m2 > sm[threadIdx.x] || (m2 == sm[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sm[threadIdx.x] = m2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ps[b * nblk + blockIdx.x] = acc;
+    pm[b * nblk + blockIdx.x] = sm[0];
+    pi[b * nblk + blockIdx.x] = si[0];
+  }
+}
+
+template <typename T>
+__global__ void normph_final(const T* x, long stride, const double* ps, const double* pm,
+                             const long* pi, int nblk, T* fac) {
+  const int b = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  double acc = 0.0, best = -1.0;
+  long bi = 0;
+  for (int i = 0; i < nblk; ++i) {
+    acc += ps[b * nblk + i];
+    const double m = pm[b * nblk + i];
+    const long j = pi[b * nblk + i];
+    if (m > best || (m == best && j < bi)) { best = m; bi = j; }
+  }
+  const double nrm = sqrt(acc);
+  const T piv = x[b * stride + bi];
+  const double mag = sqrt(absq(piv));
+  if constexpr (sizeof(T) == 8) {
+    fac[b] = (mag > 0.0 ? (piv > 0.0 ? 1.0 : -1.0) : 1.0) / nrm;
+  } else {
+    fac[b] = mag > 0.0 ? make_double2(piv.x / (mag * nrm), -piv.y / (mag * nrm))
+                       : make_double2(1.0 / nrm, 0.0);
+  }
+}
+
+template <typename T>
+__global__ void scale_by_kernel(long n, T* x, long stride, const T* fac) {
+  const int b = blockIdx.y;
+  const T f = fac[b];
+  T* xb = x + b * stride;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    xb[i] = mulv(xb[i], f);
+}
+
 unsigned grid_for(long n, int per = 256, long cap = 152L * 8) {
   long g = (n + per - 1) / per;
   if (g < 1) g = 1;
@@ -426,12 +553,44 @@ unsigned grid_for(long n, int per = 256, long cap = 152L * 8) {
 }  // namespace
 
 cudaError_t chol_inv(bool cx, int k, long n, bool shift, void* G, void* Linv,
-                     int batch, int* err, cudaStream_t s, long* launches) {
+                     int batch, int* dead, int* err, cudaStream_t s, long* launches) {
+  const size_t shm = (size_t)k * sizeof(double);
   if (cx)
-    chol_inv_kernel<cplx><<<batch, 256, 0, s>>>(k, n, shift, (cplx*)G, (cplx*)Linv, err);
+    chol_inv_kernel<cplx><<<batch, 256, shm, s>>>(k, n, shift, (cplx*)G, (cplx*)Linv, dead, err);
   else
-    chol_inv_kernel<double><<<batch, 256, 0, s>>>(k, n, shift, (double*)G, (double*)Linv, err);
+    chol_inv_kernel<double><<<batch, 256, shm, s>>>(k, n, shift, (double*)G, (double*)Linv,
+                                                     dead, err);
   if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t repair_dead_columns(bool cx, long rows, int k, void* Q, const int* dead,
+                                uint64_t seed, cudaStream_t s, long* launches) {
+  if (cx) repair_kernel<cplx><<<grid_for(rows * k), 256, 0, s>>>(rows, k, (cplx*)Q, dead, seed);
+  else repair_kernel<double><<<grid_for(rows * k), 256, 0, s>>>(rows, k, (double*)Q, dead, seed);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t normalize_phase(bool cx, long n, void* x, long stride, int batch, void* fac,
+                            void* work, cudaStream_t s, long* launches) {
+  int nblk = (int)((n + 255) / 256);
+  if (nblk > 152) nblk = 152;
+  if (nblk < 1) nblk = 1;
+  double* ps = static_cast<double*>(work);
+  double* pm = ps + (size_t)nblk * batch;
+  long* pi = reinterpret_cast<long*>(pm + (size_t)nblk * batch);
+  dim3 g(nblk, batch);
+  if (cx) {
+    normph_partial<cplx><<<g, 256, 0, s>>>(n, (const cplx*)x, stride, ps, pm, pi, nblk);
+    normph_final<cplx><<<batch, 32, 0, s>>>((const cplx*)x, stride, ps, pm, pi, nblk, (cplx*)fac);
+    scale_by_kernel<cplx><<<g, 256, 0, s>>>(n, (cplx*)x, stride, (const cplx*)fac);
+  } else {
+    normph_partial<double><<<g, 256, 0, s>>>(n, (const double*)x, stride, ps, pm, pi, nblk);
+    normph_final<double><<<batch, 32, 0, s>>>((const double*)x, stride, ps, pm, pi, nblk, (double*)fac);
+    scale_by_kernel<double><<<g, 256, 0, s>>>(n, (double*)x, stride, (const double*)fac);
+  }
+  if (launches) *launches += 3;
   return cudaGetLastError();
 }
 

@@ -39,8 +39,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_default_opts_without_gpu(lib):
     o = pkg.ctm_default_opts()
-    assert (o.p, o.si_rounds, o.method, o.prec, o.normalize, o.sign_fix) == (5, 1, 0, 0, 1, 1)
-    assert o.svd_rel_cutoff == 1e-14
+    assert (o.p, o.si_rounds, o.warmup_iters, o.warmup_rounds, o.method, o.prec,
+            o.normalize, o.sign_fix) == (5, 1, 5, 8, 0, 0, 1, 1)
+    assert o.svd_rel_cutoff == 1e-12
 
 
 def test_argument_errors_are_reported_before_device_work(lib):
