@@ -364,14 +364,15 @@ class CTM:
                 E4 = np.einsum("tmdD,mn->tndD", T3, C4)
                 E4 = E4.reshape(T3.shape[0], -1)
                 C4n = E4 @ Pl_dn
-                # T4' = P_r (T4 A B) P_l
-                G = np.einsum("tqlw,sulde,svwDE->tdDquveE", T4, A, B,
-                              optimize=True)
-                sh = G.shape
-                G = G.reshape(sh[0] * sh[1] * sh[2], sh[3] * sh[4] * sh[5],
-                              sh[6], sh[7])
-                T4n = np.einsum("ci,ijeE,jk->ckeE", Pr_dn, G, Pl_up,
-                                optimize=True)
+                # T4' = P_r (T4 A B) P_l, contracted as ((T4 P_l) A) B then P_r
+                # so that no intermediate exceeds chi^2 d D^4
+                Dk, Db = A.shape[1], B.shape[1]
+                Pl4 = Pl_up.reshape(T4.shape[1], Dk, Db, -1)       # [q,u,v,c]
+                Pr4 = Pr_dn.reshape(-1, T4.shape[0], Dk, Db)       # [c',t,d,D]
+                Y = np.einsum("tqlw,quvc->tlwuvc", T4, Pl4, optimize=True)
+                Y = np.einsum("tlwuvc,sulde->twvcsde", Y, A, optimize=True)
+                Y = np.einsum("twvcsde,svwDE->tdDceE", Y, B, optimize=True)
+                T4n = np.einsum("atdD,tdDceE->aceE", Pr4, Y, optimize=True)
                 new.append((C1n, T4n, C4n))
             for y in range(f.Ly):
                 C1n, T4n, C4n = new[y]

@@ -163,7 +163,7 @@ def test_ising_onsager_on_gpu():
 
 def test_ising_yang_on_gpu():
     beta = 0.50
-    ctx, ref = _ising_ctx(beta, 27)
+    ctx, ref = _ising_ctx(beta, 12)
     ctx.ctm_converge(1e-11, 300)
     ref.converge(1e-11, 300)
     imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)

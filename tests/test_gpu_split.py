@@ -1,0 +1,83 @@
+"""Split-precision path (bf16 slices on the tcgen05 tensor cores, fp32
+accumulation, fp64 reduction; QR, small SVD and s^-1/2 in fp64) against the
+fp64 path on the GPU and against the CPU oracle.
+
+Three bf16 slices keep 24 significant bits of every operand and fp32
+accumulation rounds each partial sum to 24 bits, so one product has a
+relative error of ~1e-7 of its terms; the tolerances below state what the
+converged environment inherits from that.
+"""
+import numpy as np
+import pytest
+
+import ctm_synth as S
+import paper_2607_15158_gb300 as pkg
+from oracle import ctmrg
+
+pytestmark = pytest.mark.gpu
+HEIS = S.heisenberg_bond()
+TOL_SPLIT = 1e-6     # converged spectra and energies, split vs fp64
+
+
+def _ctx(case, prec):
+    Lx, Ly, d, D, chi, p, cplx, rounds = case
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, seed=0)
+    Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx, seed=1)
+    N = chi * D * D
+    k = min(chi + p, N)
+    X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx, seed=2)
+    ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx,
+                       opts=pkg.ctm_default_opts(p=p, si_rounds=rounds, prec=prec))
+    ctx.ctm_set_env(Cs, Ts)
+    ctx.ctm_set_rangefinders(X0, W0)
+    return ctx, (A, Cs, Ts, X0, W0)
+
+
+def _spectra(ctx):
+    return np.array([[ctx.ctm_spectrum(x, y, lab + 1) for y in range(ctx.Ly) for x in range(ctx.Lx)]
+                     for lab in range(4)])
+
+
+@pytest.mark.parametrize("case", [
+    (1, 1, 2, 2, 8, 5, False, 1),
+    (2, 1, 2, 3, 10, 5, True, 1),        # N = 90 complex: ragged tiles
+    (1, 1, 2, 4, 12, 5, True, 1),        # N = 192: two 128-row tiles
+])
+def test_one_move_split_matches_fp64(case):
+    a, _ = _ctx(case, pkg.CTM_PREC_FP64)
+    b, _ = _ctx(case, pkg.CTM_PREC_SPLIT_BF16)
+    a.ctm_move(0)
+    b.ctm_move(0)
+    sa, sb = _spectra(a), _spectra(b)
+    assert np.abs(sa - sb).max() < 1e-5
+    Pl, PrH = b.ctm_get_projectors(0, 0, 0)
+    assert np.abs(PrH.conj().T @ Pl - np.eye(Pl.shape[1])).max() < 1e-9
+    a.ctm_free()
+    b.ctm_free()
+
+
+@pytest.mark.parametrize("case", [
+    (1, 1, 2, 2, 8, 5, False, 2),
+    (2, 2, 2, 2, 8, 5, True, 2),
+])
+def test_converged_split_matches_fp64_and_oracle(case):
+    a, inputs = _ctx(case, pkg.CTM_PREC_FP64)
+    b, _ = _ctx(case, pkg.CTM_PREC_SPLIT_BF16)
+    ita, da, oka = a.ctm_converge(1e-11, 200)
+    itb, db, okb = b.ctm_converge(1e-9, 200)
+    assert oka and okb
+    sa, sb = _spectra(a), _spectra(b)
+    assert np.abs(sa - sb).max() < TOL_SPLIT
+    Lx, Ly = case[0], case[1]
+    A, Cs, Ts, X0, W0 = inputs
+    ref = ctmrg.CTM(Lx, Ly, A, [x.conj() for x in A], Cs, Ts, case[4], method="si", p=case[5],
+                    si_rounds=case[7], X0=X0, W0=W0, warmup_iters=5, warmup_rounds=8)
+    ref.converge(1e-11, 200)
+    for y in range(Ly):
+        for x in range(Lx):
+            for direction in (0, 1):
+                e_ref = ref.expect2(HEIS, x, y, direction)
+                assert abs(a.ctm_expect(HEIS, x, y, direction) - e_ref) < 1e-10
+                assert abs(b.ctm_expect(HEIS, x, y, direction) - e_ref) < TOL_SPLIT
+    a.ctm_free()
+    b.ctm_free()

@@ -85,9 +85,11 @@ def test_ctm_onsager_beta040(method):
 
 @pytest.mark.parametrize("method", ["svd", "si"])
 def test_ctm_yang_beta050(method):
-    """P2: spontaneous magnetisation (Yang) at beta = 0.50, chi = 27."""
+    """P2: spontaneous magnetisation (Yang) at beta = 0.50. The corner
+    spectrum is effectively of rank ~10 here, so chi = 12 keeps it above the
+    fp64 noise floor (a much larger chi keeps zero directions)."""
     beta = 0.50
-    ctm = _ising_ctm(beta, 27, method)
+    ctm = _ising_ctm(beta, 12, method)
     ctm.converge(1e-11, 300)
     imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)
     assert abs(abs(ctm.site_ratio(0, 0, imp)) - ising.yang_m(beta)) < 1e-10
@@ -149,8 +151,10 @@ def _growth(method, kets, bras, chi0, Dk, Db, niter, cplx):
     C, T = S.initial_env(1, 1, chi0, Dk, Db, complex_=cplx, seed=3)
     C0 = [c[0].copy() for c in C]
     T0 = [t[0].copy() for t in T]
+    # no truncation beyond the exactly-zero directions of M (rank-deficient
+    # finite boundaries): those carry no weight, so dropping them is exact
     ctm = ctmrg.CTM(1, 1, kets, bras, C, T, chi=10 ** 6, method=method, p=5,
-                    cutoff=0.0, normalize=False)
+                    cutoff=1e-12, normalize=False)
     for _ in range(niter):
         ctm.iteration()
     return ctm, C0, T0
@@ -177,10 +181,10 @@ def test_exact_growth_quantum(method):
 
 @pytest.mark.parametrize("method", ["svd", "si"])
 def test_exact_growth_classical_two_iterations(method):
-    """P3: a positive random classical network grown for two iterations
+    """P3: a generic (Gaussian) classical network grown for two iterations
     from a chi = 1 boundary equals the exact 5x5 patch."""
     rng = np.random.default_rng(5)
-    ket, bra = S.classical_as_ket(np.abs(rng.standard_normal((2, 2, 2, 2))) + 0.1)
+    ket, bra = S.classical_as_ket(rng.standard_normal((2, 2, 2, 2)))
     ctm, C0, T0 = _growth(method, [ket], [bra], 1, 2, 1, 2, False)
     z_ex = exact.finite_patch(C0, T0, ket, bra, 5, 5)
     assert abs(ctm.z_one_site() / z_ex - 1) < 1e-8
