@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""SI-CTMRG throughput on GB300: CTMRG moves/s on the 3x3-cell, complex
+D = 6, chi = 144 workload (half-system 5184 x 5184), split-precision tensor-core
+products, through the C ABI of libctm.
+
+One step = one CTMRG iteration: the four directional moves over the 3x3 cell
+(9 cuts each: enlarged corners, one subspace-iteration round with QR, small
+SVD, projectors, absorption) plus the corner-spectrum convergence scalar.
+Inputs are seeded synthetic tensors (ctm_synth); the working set (four
+0.43 GB corners per cut plus their bf16 slices) is far larger than L2, so no
+explicit flush is needed between timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the path has no exchange step); value = moves of all ranks / max time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "cfg3_3x3_D6_chi144_c128"
+METRIC = "CTMRG moves/s (3x3 cell, complex D=6, chi=144, split BF16x3 tensor-core products)"
+UNIT = "moves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["split", "fp64"], default="split")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
+                   samples=len(rows))
+        return out
+
+
+# ------------------------------------------------------------- oracle timing
+def oracle_sample_seconds(w):
+    """Time one cut of the workload in the CPU oracle: the four enlarged
+    corners, one subspace-iteration round (rangefinder updates with QR),
+    the small SVD and projectors, and the absorption of one site. A move is
+    Lx*Ly such cuts. Returns (seconds per move, seconds measured, sample)."""
+    import numpy as np
+    import ctm_synth as S
+    from oracle import ctmrg
+
+    Lx, Ly, d, D, chi, p = w["Lx"], w["Ly"], w["d"], w["D"], w["chi"], w["p"]
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=w["complex_"], diag_weight=w["diag_weight"])
+    Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=w["complex_"])
+    N = chi * D * D
+    k = min(chi + p, N)
+    X0, W0 = S.initial_rangefinders(1, 1, N, k, complex_=w["complex_"])
+    ref = ctmrg.CTM(Lx, Ly, A, [a.conj() for a in A], Cs, Ts, chi, method="si", p=p,
+                    si_rounds=w["si_rounds"])
+    f = ctmrg.Frame(Lx, Ly, 0)
+    t0 = time.perf_counter()
+    Q = ref.cut_corners(f, 0, 0)
+    X = ctmrg.qr_q(X0[0][0])
+    W = ctmrg.qr_q(W0[0][0])
+    Pl, Pr, s, Xn, Wn, s_all = ctmrg.projectors_si(*Q, X, W, chi, w["si_rounds"])
+    # absorption of one site with this cut's projectors on both sides
+    C1, T1, T4 = ref.C[0][0], ref.T[0][0], ref.T[3][0]
+    E1 = np.einsum("pm,mnuv->puvn", C1, T1).reshape(-1, chi)
+    C1n = Pr @ E1
+    Pl4 = Pl.reshape(chi, D, D, chi)
+    Pr4 = Pr.reshape(chi, chi, D, D)
+    Y = np.einsum("tqlw,quvc->tlwuvc", T4, Pl4, optimize=True)
+    Y = np.einsum("tlwuvc,sulde->twvcsde", Y, A[0], optimize=True)
+    Y = np.einsum("twvcsde,svwDE->tdDceE", Y, A[0].conj(), optimize=True)
+    T4n = np.einsum("atdD,tdDceE->aceE", Pr4, Y, optimize=True)
+    dt = time.perf_counter() - t0
+    del C1n, T4n
+    per_move = dt * Lx * Ly
+    sample = (f"one cut of the {Lx}x{Ly} D={D} chi={chi} workload (4 enlarged corners, "
+              f"{w['si_rounds']} SI round, small SVD, projectors, absorption of one site) "
+              f"x {Lx * Ly} cuts per move")
+    return per_move, dt, sample
+
+
+def cpu_cores():
+    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS")
+    return int(threads) if threads else os.cpu_count()
+
+
+# -------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    import ctm_synth as S
+
+    if rank != 0:
+        return
+    w = S.WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample_seconds(w)
+    per = []
+    for _ in range(args.steps):
+        pm, dt, sample = oracle_sample_seconds(w)
+        per.append(pm)
+    ms_per_move = 1000.0 * sum(per) / len(per)
+    value = 1000.0 / ms_per_move
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 4 * ms_per_move, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": args.workload, "cell": "3x3", "D": w["D"], "chi": w["chi"],
+                   "p": w["p"], "si_rounds": w["si_rounds"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import ctm_synth as S
+    import paper_2607_15158_gb300 as pkg
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    w = S.WORKLOADS[args.workload]
+    Lx, Ly, d, D, chi, p = w["Lx"], w["Ly"], w["d"], w["D"], w["chi"], w["p"]
+    cplx = w["complex_"]
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, diag_weight=w["diag_weight"])
+    Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx)
+    N = chi * D * D
+    k = min(chi + p, N)
+    X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx)
+    stream = torch.cuda.current_stream()
+    prec = pkg.CTM_PREC_SPLIT_BF16 if args.prec == "split" else pkg.CTM_PREC_FP64
+    # steady-state SI moves: one subspace-iteration round per move from the
+    # first move on (the warm-up schedule is a convergence aid, not part of
+    # the per-move work being measured)
+    opts = pkg.ctm_default_opts(p=p, si_rounds=w["si_rounds"], warmup_iters=0, prec=prec,
+                                stream=stream.cuda_stream)
+    ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx, opts=opts)
+    ctx.ctm_set_env(Cs, Ts)
+    ctx.ctm_set_rangefinders(X0, W0)
+
+    def step():
+        it, delta, _ = ctx.ctm_converge(0.0, 1)
+        _, launches = ctx.ctm_last_timing()
+        return launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if prec == pkg.CTM_PREC_SPLIT_BF16:
+        ctx.ctm_profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        launches += step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.ctm_profile_read() if prec == pkg.CTM_PREC_SPLIT_BF16 else None
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    moves = 4 * args.steps * world
+    value = moves / (ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: per step the
+    # environment is copied in from host memory, the iteration runs, and the
+    # corner spectra (the step's result) are read back
+    Ch = np.ascontiguousarray(np.asarray(Cs), dtype=np.complex128 if cplx else np.float64)
+    Th = np.ascontiguousarray(np.asarray(Ts), dtype=np.complex128 if cplx else np.float64)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.ctm_set_env(Ch, Th)
+        step()
+        for lab in range(4):
+            for y in range(Ly):
+                for x in range(Lx):
+                    ctx.ctm_spectrum(x, y, lab + 1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = moves / e2e_s
+    h2d = Ch.nbytes + Th.nbytes
+    d2h = 4 * Lx * Ly * chi * 8
+
+    if rank != 0:
+        ctx.ctm_free()
+        return
+    peaks, src = load_peaks()
+    roofline = None
+    if prof is not None and prof[1] > 0:
+        mma_ms, mma_n, mma_flops, mma_bytes = prof
+        achieved = mma_flops / (mma_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        roofline = {"bound": "tensor", "kernel": "split_mma_kernel (tcgen05 bf16, fp32 accum)",
+                    "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": f"{src} bf16 sustained",
+                    "launches": mma_n, "kernel_ms": round(mma_ms, 3),
+                    "kernel_share_of_step": round(mma_ms / ms, 4)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        per_move, dt, sample = oracle_sample_seconds(w)
+        cpu = {"value": 1.0 / per_move, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": sample, "seconds_measured": round(dt, 2)}
+    algo_flops_move = move_flops(w)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if cplx else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cell": f"{Lx}x{Ly}", "d": d, "D": D, "chi": chi,
+                   "p": p, "N": N, "k": k, "si_rounds": w["si_rounds"],
+                   "precision": "split-bf16x3 (6 slice products), fp32 accum, fp64 QR/SVD"
+                   if args.prec == "split" else "fp64",
+                   "step": "1 iteration = 4 moves + corner-spectrum scalar",
+                   "l2": "working set >> L2 (no flush)", "replicas": world},
+        "algorithmic_tflops": round(algo_flops_move * value / 1e12, 3),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"]},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.ctm_free()
+
+
+def move_flops(w):
+    """Algorithmic real flops of one move (complex MAC = 8 real flops): per
+    cut 4 enlarged corners (chi^3 D^2 + chi^3 D^4 + 2 chi^2 d D^6 MAC each),
+    SI round(s) (16 N^2 k), Z_R and Z_L (4 N^2 k), rho (N k^2), the
+    absorption (chi^3 D^2 + 2 chi^3 D^4 + 2 chi^2 d D^6)."""
+    chi, D, d, p = w["chi"], w["D"], w["d"], w["p"]
+    N = chi * D * D
+    k = min(chi + p, N)
+    r = w["si_rounds"]
+    mac = 4 * (chi ** 3 * D ** 2 + chi ** 3 * D ** 4 + 2 * chi ** 2 * d * D ** 6)
+    mac += (16 * r + 4) * N * N * k + N * k * k
+    mac += chi ** 3 * D ** 2 + 2 * chi ** 3 * D ** 4 + 2 * chi ** 2 * d * D ** 6
+    per_mac = 8 if w["complex_"] else 2
+    return per_mac * mac * w["Lx"] * w["Ly"]
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

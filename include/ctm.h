@@ -177,6 +177,17 @@ ctm_status ctm_get_projectors(ctm_ctx* ctx, ctm_dir dir, int x, int y,
  * number of kernels it launched. */
 ctm_status ctm_last_timing(const ctm_ctx* ctx, double* ms, long* launches);
 
+/* Per-launch timing of the split-precision tensor-core GEMM kernel (the
+ * dominant kernel of CTM_PREC_SPLIT_BF16): ctm_profile_enable(ctx, 1) starts
+ * recording CUDA events around each launch on the context's stream and clears
+ * the totals; ctm_profile_read returns the summed device time, the launch
+ * count, the tensor-pipe flops (six bf16 slice products of the real-embedded,
+ * unpadded problem) and the bf16 operand bytes the launches consumed.
+ * CTM_EUNSUPPORTED for an FP64 context. */
+ctm_status ctm_profile_enable(ctm_ctx* ctx, int on);
+ctm_status ctm_profile_read(ctm_ctx* ctx, double* ms, long* launches, double* flops,
+                            double* bytes);
+
 void ctm_free(ctm_ctx* ctx);
 
 /* Message of the last failed call on ctx (or of the last failed creation when

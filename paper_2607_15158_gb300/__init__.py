@@ -72,6 +72,8 @@ def load():
         "ctm_free_energy": (I, [ctx_p, P(D)]),
         "ctm_get_projectors": (I, [ctx_p, I, I, I, VP, VP]),
         "ctm_last_timing": (I, [ctx_p, P(D), P(C.c_long)]),
+        "ctm_profile_enable": (I, [ctx_p, I]),
+        "ctm_profile_read": (I, [ctx_p, P(D), P(C.c_long), P(D), P(D)]),
         "ctm_free": (None, [ctx_p]),
         "ctm_last_error": (C.c_char_p, [ctx_p]),
     }
@@ -216,6 +218,15 @@ class Context:
         _check(self.lib, self.ptr, self.lib.ctm_get_projectors(
             self.ptr, int(direction), x, y, Pl.ctypes.data, PrH.ctypes.data))
         return Pl, PrH
+
+    def ctm_profile_enable(self, on=True):
+        _check(self.lib, self.ptr, self.lib.ctm_profile_enable(self.ptr, 1 if on else 0))
+
+    def ctm_profile_read(self):
+        ms, n, fl, by = C.c_double(), C.c_long(), C.c_double(), C.c_double()
+        _check(self.lib, self.ptr, self.lib.ctm_profile_read(
+            self.ptr, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by)))
+        return ms.value, n.value, fl.value, by.value
 
     def ctm_last_timing(self):
         ms, n = C.c_double(), C.c_long()

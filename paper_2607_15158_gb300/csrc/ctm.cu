@@ -224,6 +224,10 @@ ctm_status gemm(ctm_ctx* c, GemmDesc& g) {
   return CTM_OK;
 }
 
+// contractions with at least this many multiply-adds go to the split-precision
+// tensor-core GEMM when the context runs in CTM_PREC_SPLIT_BF16
+constexpr double SPLIT_MIN_MNK = 1 << 22;
+
 // ------------------------------------------------ pairwise contractions
 // out[lo] = sum over shared labels of A[la] B[lb] (conj on request): at most
 // one permute of each operand into a matrix view, one fp64 GEMM (or a dot
@@ -328,14 +332,24 @@ ctm_status ein(ctm_ctx* c, const char* spec, const Tn& A, bool cA, const Tn& B, 
     if (!w) return fail(c, CTM_ENOMEM, "scratch arena too small for a dot product");
     CTM_CUDA_OK(dot64(c->cx, false, K, Am, 0, Bm, 0, Cm, 1, w, wb, c->stream, &c->launches));
   } else {
-    GemmDesc g;
-    g.opA = p.opA;
-    g.opB = p.opB;
-    g.M = M; g.N = Nn; g.K = K;
-    g.A = Am; g.lda = (p.opA == OP_N || p.opA == OP_R) ? K : M;
-    g.B = Bm; g.ldb = (p.opB == OP_N || p.opB == OP_R) ? Nn : K;
-    g.C = Cm; g.ldc = Nn;
-    CK(gemm(c, g));
+    const long lda = (p.opA == OP_N || p.opA == OP_R) ? K : M;
+    const long ldb = (p.opB == OP_N || p.opB == OP_R) ? Nn : K;
+    if (c->split && (double)M * Nn * K >= SPLIT_MIN_MNK) {
+      // large contraction (enlarged corners, absorption): split precision on
+      // the tensor cores
+      const ctm_status st = split_gemm(c->split, p.opA, Am, lda, p.opB, Bm, ldb, (int)M, (int)Nn,
+                                       (int)K, Cm, Nn, c->stream, &c->launches);
+      if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+    } else {
+      GemmDesc g;
+      g.opA = p.opA;
+      g.opB = p.opB;
+      g.M = M; g.N = Nn; g.K = K;
+      g.A = Am; g.lda = lda;
+      g.B = Bm; g.ldb = ldb;
+      g.C = Cm; g.ldc = Nn;
+      CK(gemm(c, g));
+    }
   }
   if (final_perm) {
     Tn tmp;
@@ -813,7 +827,7 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   }
   if ((st = upload_default_state(c)) != CTM_OK) return bail(st);
   if (c->opts.prec == CTM_PREC_SPLIT_BF16) {
-    st = split_create(&c->split, cx, (int)N, (int)k, c->stream);
+    st = split_create(&c->split, cx, (int)N, (int)k, c->err, c->stream);
     if (st != CTM_OK) {
       c->msg = "split-precision setup failed";
       return bail(st);
@@ -1225,6 +1239,25 @@ ctm_status ctm_last_timing(const ctm_ctx* c, double* ms, long* launches) {
   if (!c) return CTM_EINVAL;
   if (ms) *ms = c->last_ms;
   if (launches) *launches = c->last_launches;
+  return CTM_OK;
+}
+
+ctm_status ctm_profile_enable(ctm_ctx* c, int on) {
+  if (!c) return CTM_EINVAL;
+  if (!c->split) return fail(c, CTM_EUNSUPPORTED, "profiling covers the split-precision kernel");
+  Guard gd(c);
+  const ctm_status st = split_profile(c->split, on ? 1 : 0, nullptr, nullptr, nullptr, nullptr);
+  if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+  return CTM_OK;
+}
+
+ctm_status ctm_profile_read(ctm_ctx* c, double* ms, long* launches, double* flops,
+                            double* bytes) {
+  if (!c) return CTM_EINVAL;
+  if (!c->split) return fail(c, CTM_EUNSUPPORTED, "profiling covers the split-precision kernel");
+  Guard gd(c);
+  const ctm_status st = split_profile(c->split, -1, ms, launches, flops, bytes);
+  if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
   return CTM_OK;
 }
 

@@ -1,24 +1,714 @@
-// Placeholder: split-precision products are not available in this build.
+// Split-precision GEMM on the sm_103a tensor cores (tcgen05 + TMA + TMEM).
+//
+// C = op(A) op(B) for fp64 (or complex fp64) operands, computed as sums of
+// bf16 x bf16 products with fp32 accumulation:
+//   * every fp64 value x is split into three bf16 slices x = s0 + s1 + s2 + e
+//     (each slice the bf16 rounding of the remainder; |e| <~ 2^-24 |x|);
+//   * a product keeps the six slice products of order >= 2^-16
+//     (s0 t0, s0 t1, s1 t0, s0 t2, s1 t1, s2 t0), all accumulated into one
+//     fp32 accumulator in tensor memory;
+//   * complex data uses the real embedding A_emb = [A_r | A_i] (M x 2K),
+//     B_emb = [[B_r, B_i], [-B_i, B_r]] (2K x 2N), C_emb = [C_r | C_i];
+//   * K is split over CTAs; fp32 partials are reduced in fp64.
+//
+// Kernel: one CTA = 128 output rows x BNc (<= 160) output columns; A and B
+// slices are K-major, staged by TMA in 64-element (128-byte, 128B-swizzled)
+// K blocks through a two-stage mbarrier pipeline; one thread issues the
+// tcgen05.mma instructions, four warps drain the accumulator with
+// tcgen05.ld. Every mbarrier wait is bounded (2 s of %globaltimer), after
+// which the CTA records DEV_MBAR_TIMEOUT, skips its work, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
 #include "split_gemm.h"
 
 namespace ctm {
 
-struct SplitCtx {
-  int dummy;
+namespace {
+
+constexpr int BM = 128;          // rows per CTA (tcgen05 M)
+constexpr int BK = 64;           // K elements per stage (128 bytes of bf16)
+constexpr int STAGES = 2;
+constexpr int MAX_BNC = 160;     // columns per CTA
+constexpr int A_SLICE_BYTES = BM * BK * 2;   // 16 KB
+constexpr uint64_t WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
+
+// ---------------------------------------------------------------- PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the completion of the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (globaltimer() - t0 > WAIT_NS) {
+      atomicOr(err, DEV_MBAR_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (sm_100 descriptor version 1)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+  return d;
+}
+// instruction descriptor of kind::f16: bf16 x bf16 -> f32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct MmaParams {
+  int M;          // output rows
+  int Np;         // padded output columns (row length of the partials)
+  int BNc;        // columns per CTA, multiple of 16, <= MAX_BNC
+  int kb_total;   // K blocks of 64
+  int kb_split;   // K blocks per split
+  float* part;    // [nks][M][Np] fp32 partial sums
+  int* err;
 };
 
-ctm_status split_create(SplitCtx** out, bool, int, int, cudaStream_t) {
+__global__ void __launch_bounds__(128, 1)
+    split_mma_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB, MmaParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int BNc = p.BNc;
+  const uint32_t b_slice_bytes = (uint32_t)BNc * BK * 2;
+  const uint32_t stage_bytes = 3 * A_SLICE_BYTES + 3 * b_slice_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 done = smem_u32(bars + 2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m_tile = blockIdx.x, chunk = blockIdx.y, ks = blockIdx.z;
+  const int kb0 = ks * p.kb_split;
+  const int nkb = min(p.kb_split, p.kb_total - kb0);
+  uint32_t ncols = 32;
+  while ((int)ncols < BNc) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  __shared__ int failed;
+  if (threadIdx.x == 0) failed = 0;
+  __syncthreads();
+
+  if (nkb > 0 && warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ((kb / STAGES) - 1) & 1, p.err)) {
+        failed = 1;
+        break;
+      }
+      const uint32_t full = full0 + 8 * s;
+      mbar_expect_tx(full, stage_bytes);
+      uint8_t* st = smem + s * stage_bytes;
+      const int kx = (kb0 + kb) * BK;
+      for (int sl = 0; sl < 3; ++sl)
+        tma_load_3d(smem_u32(st + sl * A_SLICE_BYTES), &tmA, kx, m_tile * BM, sl, full);
+      for (int sl = 0; sl < 3; ++sl)
+        tma_load_3d(smem_u32(st + 3 * A_SLICE_BYTES + sl * b_slice_bytes), &tmB, kx,
+                    chunk * BNc, sl, full);
+    }
+  } else if (nkb > 0 && warp == 1 && lane == 0) {
+    // MMA issuer: six slice products per K block, four K=16 steps each
+    const uint32_t idesc = idesc_bf16(BM, BNc);
+    const int pa[6] = {0, 0, 1, 0, 1, 2};
+    const int pb[6] = {0, 1, 0, 2, 1, 0};
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, p.err)) {
+        ok = false;
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(smem + s * stage_bytes);
+      for (int pr = 0; pr < 6; ++pr) {
+        const uint32_t a0 = st + pa[pr] * A_SLICE_BYTES;
+        const uint32_t b0 = st + 3 * A_SLICE_BYTES + pb[pr] * b_slice_bytes;
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          mma_bf16(tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                   (kb > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    if (ok) mma_commit(done);
+  }
+  // epilogue: all four warps, TMEM lanes 32w .. 32w+31 = rows of this warp
+  __syncwarp();
+  bool have = nkb > 0;
+  if (have && !mbar_wait(done, 0, p.err)) have = false;
+  __syncthreads();
+  if (failed) have = false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have) {
+    const int row = m_tile * BM + warp * 32 + lane;
+    float* out = p.part + ((size_t)ks * p.M + row) * p.Np + (size_t)chunk * BNc;
+    for (int c0 = 0; c0 < BNc; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (row < p.M) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) out[c0 + i] = __uint_as_float(r[i]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
+}
+
+// ------------------------------------------------------------ slicing
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat16& s1,
+                                       __nv_bfloat16& s2) {
+  s0 = __double2bfloat16(x);
+  const double r1 = x - (double)__bfloat162float(s0);
+  s1 = __double2bfloat16(r1);
+  const double r2 = r1 - (double)__bfloat162float(s1);
+  s2 = __double2bfloat16(r2);
+}
+
+// element (m, kk) of op(A) for a row-major fp64 / complex matrix A
+template <typename T>
+__device__ __forceinline__ T op_elem(const T* A, long lda, int op, long m, long kk) {
+  T v = (op == OP_N || op == OP_R) ? A[m * lda + kk] : A[kk * lda + m];
+  if (op == OP_C || op == OP_R) v = conjv(v);
+  return v;
+}
+
+// A slices: out[s][m][kr], kr < K: Re op(A)(m, kr); K <= kr < 2K: Im
+// (complex); zero up to Kp. One thread per output element along kr; a 32 x 32
+// shared tile transposes the transposed operands.
+template <typename T>
+__global__ void prep_a_kernel(const T* A, long lda, int op, int M, int K, int Kp,
+                               __nv_bfloat16* out) {
+  __shared__ T tile[32][33];
+  const bool cx = sizeof(T) == 16;
+  const int Kr = cx ? 2 * K : K;
+  const long slice = (long)M * Kp;
+  const int tiles_k = (Kp + 31) / 32, tiles_m = (M + 31) / 32;
+  const bool trans = (op == OP_T || op == OP_C);
+  for (int t = blockIdx.x; t < tiles_k * tiles_m; t += gridDim.x) {
+    const int tk = t % tiles_k, tm = t / tiles_k;
+    const int m0 = tm * 32, kr0 = tk * 32;
+    if (trans) {
+      // stage op(A)(m0.., kk..) for the kk range this tile needs (per part)
+      // rows of A are kk, contiguous along m
+      for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int kr = kr0 + yy;
+        const int kk = (cx && kr >= K) ? kr - K : kr;
+        const int m = m0 + threadIdx.x;
+        T v = zero_of(T());
+        if (kr < Kr && m < M) v = op_elem(A, lda, op, m, kk);
+        tile[yy][threadIdx.x] = v;
+      }
+      __syncthreads();
+      for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int m = m0 + yy, kr = kr0 + threadIdx.x;
+        if (m >= M) continue;
+        double x = 0.0;
+        if (kr < Kr) {
+          const T v = tile[threadIdx.x][yy];
+          if constexpr (sizeof(T) == 16) x = (kr < K) ? v.x : v.y;
+          else x = v;
+        }
+        __nv_bfloat16 s0, s1, s2;
+        split3(x, s0, s1, s2);
+        const long o = (long)m * Kp + kr;
+        out[o] = s0;
+        out[slice + o] = s1;
+        out[2 * slice + o] = s2;
+      }
+      __syncthreads();
+    } else {
+      for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int m = m0 + yy, kr = kr0 + threadIdx.x;
+        if (m >= M) continue;
+        double x = 0.0;
+        if (kr < Kr) {
+          const int kk = (cx && kr >= K) ? kr - K : kr;
+          const T v = op_elem(A, lda, op, m, kk);
+          if constexpr (sizeof(T) == 16) x = (kr < K) ? v.x : v.y;
+          else x = v;
+        }
+        __nv_bfloat16 s0, s1, s2;
+        split3(x, s0, s1, s2);
+        const long o = (long)m * Kp + kr;
+        out[o] = s0;
+        out[slice + o] = s1;
+        out[2 * slice + o] = s2;
+      }
+    }
+  }
+}
+
+// B slices (K-major rows = output real columns): out[s][j][kr] = B_emb[kr][j]
+// with B_emb = [[B_r, B_i], [-B_i, B_r]] for complex, B for real.
+template <typename T>
+__global__ void prep_b_kernel(const T* B, long ldb, int op, int K, int N, int Kp, int Np,
+                              __nv_bfloat16* out) {
+  const bool cx = sizeof(T) == 16;
+  const int Kr = cx ? 2 * K : K;
+  const int Nr = cx ? 2 * N : N;
+  const long slice = (long)Np * Kp;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)Np * Kp;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / Kp), kr = (int)(idx % Kp);
+    double x = 0.0;
+    if (j < Nr && kr < Kr) {
+      const int part_k = (cx && kr >= K) ? 1 : 0, kk = part_k ? kr - K : kr;
+      const int part_n = (cx && j >= N) ? 1 : 0, jj = part_n ? j - N : j;
+      // op(B)(kk, jj)
+      const T v = (op == OP_N || op == OP_R) ? B[(long)kk * ldb + jj] : B[(long)jj * ldb + kk];
+      if constexpr (sizeof(T) == 16) {
+        const bool cj = (op == OP_C || op == OP_R);
+        const double re = v.x, im = cj ? -v.y : v.y;
+        // [[re, im], [-im, re]]
+        if (part_k == 0) x = part_n == 0 ? re : im;
+        else x = part_n == 0 ? -im : re;
+      } else {
+        x = v;
+      }
+    }
+    __nv_bfloat16 s0, s1, s2;
+    split3(x, s0, s1, s2);
+    out[idx] = s0;
+    out[slice + idx] = s1;
+    out[2 * slice + idx] = s2;
+  }
+}
+
+// C[m][j] = sum over splits of the partials (fp64), complex from [C_r | C_i]
+template <typename T>
+__global__ void reduce_kernel(const float* part, int nks, int M, int N, int Np, T* C, long ldc) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)M * N;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int m = (int)(idx / N), j = (int)(idx % N);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < nks; ++s) {
+      const float* row = part + ((size_t)s * M + m) * Np;
+      re += (double)row[j];
+      if constexpr (sizeof(T) == 16) im += (double)row[N + j];
+    }
+    if constexpr (sizeof(T) == 16) C[(long)m * ldc + j] = make_double2(re, im);
+    else C[(long)m * ldc + j] = re;
+  }
+}
+
+unsigned grid_cap(long n, long cap = 152L * 8) {
+  long g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3-D map over [3][rows][Kp] bf16 with a (64, box_rows, 1) box, 128B swizzle
+bool make_map(CUtensorMap* map, const void* base, int rows, int Kp, int box_rows) {
+  EncodeTiledFn enc = get_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ context
+struct SplitCtx {
+  bool cx = false;
+  int N = 0, k = 0;
+  std::string msg;
+  // cached corner operands: [corner][op N / op H] slices, and their sources
+  void* corner_src[4] = {nullptr};
+  __nv_bfloat16* cslices[4][2] = {{nullptr}};
+  int corner_Kp = 0;
+  // generic operand buffers (grown on demand)
+  __nv_bfloat16* abuf = nullptr;
+  size_t abuf_bytes = 0;
+  __nv_bfloat16* bbuf = nullptr;
+  size_t bbuf_bytes = 0;
+  float* part = nullptr;
+  size_t part_bytes = 0;
+  int* err = nullptr;       // device error flag of the owning context
+  // per-launch CUDA events around the tensor-core kernel (profiling)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  long prof_launches = 0;
+  double prof_flops = 0.0, prof_bytes = 0.0, prof_ms = 0.0;
+};
+
+namespace {
+
+ctm_status sfail(SplitCtx* sc, ctm_status st, const char* m) {
+  sc->msg = m;
+  return st;
+}
+
+ctm_status grow(SplitCtx* sc, void** p, size_t* have, size_t need) {
+  if (*have >= need) return CTM_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    return sfail(sc, CTM_ENOMEM, "split-precision buffer allocation failed");
+  }
+  *have = need;
+  return CTM_OK;
+}
+
+int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+// column chunking of Nr real output columns into CTAs of <= MAX_BNC columns
+void chunking(int Nr, int* nchunks, int* BNc) {
+  int nc = (Nr + MAX_BNC - 1) / MAX_BNC;
+  if (nc < 1) nc = 1;
+  int b = pad_to((Nr + nc - 1) / nc, 16);
+  if (b < 16) b = 16;
+  *nchunks = nc;
+  *BNc = b;
+}
+
+int choose_splits(int tiles, int kb_total) {
+  int best = 1;
+  double best_t = 1e30;
+  const int smax = std::max(1, std::min(32, kb_total / 4));
+  for (int s = 1; s <= smax; ++s) {
+    const int per = (kb_total + s - 1) / s;
+    const int used = (kb_total + per - 1) / per;
+    const long ctas = (long)tiles * used;
+    const long waves = (ctas + 151) / 152;
+    const double t = (double)waves * (per + 2);
+    if (t < best_t - 1e-9) { best_t = t; best = used; }
+  }
+  return best;
+}
+
+// real K of the current problem (set by the caller before run_mma)
+thread_local int g_kr_real = 0;
+inline double Kr_used(int Kp, const SplitCtx*) { return g_kr_real > 0 ? g_kr_real : Kp; }
+
+// run the tensor-core kernel on prepared slices: A [3][M][Kp], B [3][Np][Kp]
+ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* Bs, int M, int Kp,
+                   int Nr, int nchunks, int BNc, void* C, long ldc, int Nout, cudaStream_t s,
+                   long* launches) {
+  const int Np = nchunks * BNc;
+  const int kb_total = Kp / BK;
+  const int mt = (M + BM - 1) / BM;
+  const int nks = choose_splits(mt * nchunks, kb_total);
+  const int kb_split = (kb_total + nks - 1) / nks;
+  {
+    ctm_status st = grow(sc, (void**)&sc->part, &sc->part_bytes, (size_t)nks * M * Np * 4);
+    if (st != CTM_OK) return st;
+  }
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, As, M, Kp, BM) || !make_map(&tb, Bs, Np, Kp, BNc))
+    return sfail(sc, CTM_ECUDA, "cuTensorMapEncodeTiled failed");
+  MmaParams p;
+  p.M = M;
+  p.Np = Np;
+  p.BNc = BNc;
+  p.kb_total = kb_total;
+  p.kb_split = kb_split;
+  p.part = sc->part;
+  p.err = sc->err;
+  const size_t smem = 1024 + (size_t)STAGES * (3 * A_SLICE_BYTES + 3 * (size_t)BNc * BK * 2) +
+                      (2 * STAGES + 1) * 8 + 16;
+  static size_t configured = 0;
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(split_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return sfail(sc, CTM_ECUDA, "cannot reserve shared memory for the tensor-core kernel");
+    configured = smem;
+  }
+  dim3 grid(mt, nchunks, nks);
+  const bool timed = sc->prof && sc->ev_used + 2 <= sc->ev.size();
+  if (timed) cudaEventRecord(sc->ev[sc->ev_used], s);
+  split_mma_kernel<<<grid, 128, smem, s>>>(ta, tb, p);
+  if (timed) {
+    cudaEventRecord(sc->ev[sc->ev_used + 1], s);
+    sc->ev_used += 2;
+    // tensor-pipe work: six bf16 slice products of the real-embedded
+    // (unpadded) problem; bytes: the three slices of both operands once
+    sc->prof_launches += 1;
+    sc->prof_flops += 6.0 * 2.0 * (double)M * (double)Nr * (double)Kr_used(Kp, sc);
+    sc->prof_bytes += 6.0 * ((double)M * Kp + (double)nchunks * BNc * Kp) +
+                      4.0 * (double)nks * M * Np;
+  }
+  if (launches) ++*launches;
+  if (sc->cx)
+    reduce_kernel<cplx><<<grid_cap((long)M * Nout), 256, 0, s>>>(sc->part, nks, M, Nout, Np,
+                                                                 (cplx*)C, ldc);
+  else
+    reduce_kernel<double><<<grid_cap((long)M * Nout), 256, 0, s>>>(sc->part, nks, M, Nout, Np,
+                                                                   (double*)C, ldc);
+  if (launches) ++*launches;
+  if (cudaGetLastError() != cudaSuccess) return sfail(sc, CTM_ECUDA, "split GEMM launch failed");
+  (void)Nr;
+  return CTM_OK;
+}
+
+ctm_status prep_a(SplitCtx* sc, const void* A, long lda, int op, int M, int K, int Kp,
+                  __nv_bfloat16* out, cudaStream_t s, long* launches) {
+  const long tiles = (long)((Kp + 31) / 32) * ((M + 31) / 32);
+  const unsigned g = (unsigned)std::min<long>(tiles, 152L * 16);
+  if (sc->cx) prep_a_kernel<cplx><<<g, dim3(32, 8), 0, s>>>((const cplx*)A, lda, op, M, K, Kp, out);
+  else prep_a_kernel<double><<<g, dim3(32, 8), 0, s>>>((const double*)A, lda, op, M, K, Kp, out);
+  if (launches) ++*launches;
+  return cudaGetLastError() == cudaSuccess ? CTM_OK : sfail(sc, CTM_ECUDA, "slice launch failed");
+}
+
+ctm_status prep_b(SplitCtx* sc, const void* B, long ldb, int op, int K, int N, int Kp, int Np,
+                  __nv_bfloat16* out, cudaStream_t s, long* launches) {
+  const unsigned g = grid_cap((long)Np * Kp);
+  if (sc->cx) prep_b_kernel<cplx><<<g, 256, 0, s>>>((const cplx*)B, ldb, op, K, N, Kp, Np, out);
+  else prep_b_kernel<double><<<g, 256, 0, s>>>((const double*)B, ldb, op, K, N, Kp, Np, out);
+  if (launches) ++*launches;
+  return cudaGetLastError() == cudaSuccess ? CTM_OK : sfail(sc, CTM_ECUDA, "slice launch failed");
+}
+
+}  // namespace
+
+ctm_status split_create(SplitCtx** out, bool cx, int N, int k, int* err, cudaStream_t s) {
+  (void)s;
   *out = nullptr;
-  return CTM_EUNSUPPORTED;
+  if (!get_encoder()) return CTM_EUNSUPPORTED;
+  SplitCtx* sc = new SplitCtx();
+  sc->cx = cx;
+  sc->N = N;
+  sc->k = k;
+  sc->err = err;
+  *out = sc;
+  return CTM_OK;
 }
-void split_destroy(SplitCtx*) {}
-ctm_status split_prepare_corners(SplitCtx*, void* const*, int, cudaStream_t, long*) {
-  return CTM_EUNSUPPORTED;
+
+ctm_status split_profile(SplitCtx* sc, int on, double* ms, long* launches, double* flops,
+                         double* bytes) {
+  if (on >= 0) {
+    if (on && sc->ev.empty()) {
+      sc->ev.resize(8192);
+      for (auto& e : sc->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return sfail(sc, CTM_ECUDA, "event creation failed");
+    }
+    sc->prof = on != 0;
+    sc->ev_used = 0;
+    sc->prof_launches = 0;
+    sc->prof_flops = sc->prof_bytes = sc->prof_ms = 0.0;
+    return CTM_OK;
+  }
+  // read: fold the recorded pairs into the totals
+  for (size_t i = 0; i + 1 < sc->ev_used; i += 2) {
+    if (cudaEventSynchronize(sc->ev[i + 1]) != cudaSuccess)
+      return sfail(sc, CTM_ECUDA, "event synchronisation failed");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, sc->ev[i], sc->ev[i + 1]);
+    sc->prof_ms += t;
+  }
+  sc->ev_used = 0;
+  if (ms) *ms = sc->prof_ms;
+  if (launches) *launches = sc->prof_launches;
+  if (flops) *flops = sc->prof_flops;
+  if (bytes) *bytes = sc->prof_bytes;
+  return CTM_OK;
 }
-ctm_status split_apply(SplitCtx*, const void*, bool, const void*, void*, int, int, cudaStream_t,
-                       long*) {
-  return CTM_EUNSUPPORTED;
+
+void split_destroy(SplitCtx* sc) {
+  if (!sc) return;
+  for (auto& e : sc->ev) cudaEventDestroy(e);
+  for (int i = 0; i < 4; ++i)
+    for (int o = 0; o < 2; ++o)
+      if (sc->cslices[i][o]) cudaFree(sc->cslices[i][o]);
+  if (sc->abuf) cudaFree(sc->abuf);
+  if (sc->bbuf) cudaFree(sc->bbuf);
+  if (sc->part) cudaFree(sc->part);
+  delete sc;
 }
-const char* split_last_error(const SplitCtx*) { return "split precision not built"; }
+
+ctm_status split_prepare_corners(SplitCtx* sc, void* const* Q, int N, cudaStream_t s,
+                                 long* launches) {
+  const int Kr = sc->cx ? 2 * N : N;
+  const int Kp = pad_to(Kr, BK);
+  sc->corner_Kp = Kp;
+  for (int i = 0; i < 4; ++i) {
+    sc->corner_src[i] = Q[i];
+    for (int o = 0; o < 2; ++o) {
+      if (!sc->cslices[i][o]) {
+        if (cudaMalloc(&sc->cslices[i][o], (size_t)3 * N * Kp * 2) != cudaSuccess) {
+          cudaGetLastError();
+          return sfail(sc, CTM_ENOMEM, "corner slice allocation failed");
+        }
+      }
+      const int op = o == 0 ? OP_N : (sc->cx ? OP_C : OP_T);
+      ctm_status st = prep_a(sc, Q[i], N, op, N, N, Kp, sc->cslices[i][o], s, launches);
+      if (st != CTM_OK) return st;
+    }
+  }
+  return CTM_OK;
+}
+
+ctm_status split_apply(SplitCtx* sc, const void* Q, bool herm, const void* Zin, void* Zout, int N,
+                       int k, cudaStream_t s, long* launches) {
+  int ci = -1;
+  for (int i = 0; i < 4; ++i)
+    if (sc->corner_src[i] == Q) ci = i;
+  if (ci < 0) return sfail(sc, CTM_EINVAL, "corner was not prepared");
+  const int Kp = sc->corner_Kp;
+  const int Nr = sc->cx ? 2 * k : k;
+  g_kr_real = sc->cx ? 2 * N : N;
+  int nchunks, BNc;
+  chunking(Nr, &nchunks, &BNc);
+  const int Np = nchunks * BNc;
+  ctm_status st = grow(sc, (void**)&sc->bbuf, &sc->bbuf_bytes, (size_t)3 * Np * Kp * 2);
+  if (st != CTM_OK) return st;
+  st = prep_b(sc, Zin, k, OP_N, N, k, Kp, Np, sc->bbuf, s, launches);
+  if (st != CTM_OK) return st;
+  return run_mma(sc, sc->cslices[ci][herm ? 1 : 0], sc->bbuf, N, Kp, Nr, nchunks, BNc, Zout, k, k,
+                 s, launches);
+}
+
+ctm_status split_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, const void* B,
+                      long ldb, int M, int N, int K, void* C, long ldc, cudaStream_t s,
+                      long* launches) {
+  const int Kr = sc->cx ? 2 * K : K;
+  const int Kp = pad_to(Kr, BK);
+  const int Nr = sc->cx ? 2 * N : N;
+  g_kr_real = Kr;
+  int nchunks, BNc;
+  chunking(Nr, &nchunks, &BNc);
+  const int Np = nchunks * BNc;
+  ctm_status st = grow(sc, (void**)&sc->abuf, &sc->abuf_bytes, (size_t)3 * M * Kp * 2);
+  if (st != CTM_OK) return st;
+  st = grow(sc, (void**)&sc->bbuf, &sc->bbuf_bytes, (size_t)3 * Np * Kp * 2);
+  if (st != CTM_OK) return st;
+  st = prep_a(sc, A, lda, opA, M, K, Kp, sc->abuf, s, launches);
+  if (st != CTM_OK) return st;
+  st = prep_b(sc, B, ldb, opB, K, N, Kp, Np, sc->bbuf, s, launches);
+  if (st != CTM_OK) return st;
+  return run_mma(sc, sc->abuf, sc->bbuf, M, Kp, Nr, nchunks, BNc, C, ldc, N, s, launches);
+}
+
+const char* split_last_error(const SplitCtx* sc) {
+  return sc ? sc->msg.c_str() : "split precision not initialised";
+}
 
 }  // namespace ctm

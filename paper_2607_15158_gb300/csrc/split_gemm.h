@@ -11,8 +11,9 @@ namespace ctm {
 struct SplitCtx;
 
 // State for N x N corners and N x k blocks of real (cx = false) or complex
-// data; allocates the bf16 slice buffers of four corners.
-ctm_status split_create(SplitCtx** out, bool cx, int N, int k, cudaStream_t s);
+// data; err is the owner's device error flag (bounded waits report there).
+// Buffers are allocated on first use.
+ctm_status split_create(SplitCtx** out, bool cx, int N, int k, int* err, cudaStream_t s);
 void split_destroy(SplitCtx* sc);
 
 // Slice the four fp64 corners Q[0..3] (N x N) into bf16 operands, in both
@@ -24,6 +25,18 @@ ctm_status split_prepare_corners(SplitCtx* sc, void* const* Q, int N, cudaStream
 // Zin, Zout fp64 N x k row-major.
 ctm_status split_apply(SplitCtx* sc, const void* Q, bool herm, const void* Zin, void* Zout,
                        int N, int k, cudaStream_t s, long* launches);
+
+// General C = op(A) op(B) (M x N, inner K; ops as in GemmDesc) in split
+// precision: both operands are sliced on the fly.
+ctm_status split_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, const void* B,
+                      long ldb, int M, int N, int K, void* C, long ldc, cudaStream_t s,
+                      long* launches);
+
+// Profiling of the tensor-core kernel: on = 1 / 0 starts / stops recording
+// CUDA events around every launch (and clears the totals); on = -1 reads the
+// accumulated device time, launches, tensor-pipe flops and operand bytes.
+ctm_status split_profile(SplitCtx* sc, int on, double* ms, long* launches, double* flops,
+                         double* bytes);
 
 const char* split_last_error(const SplitCtx* sc);
 
