@@ -31,6 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "cfg3_3x3_D6_chi144_c128"
+WARM_ITERS, WARM_ROUNDS = 2, 4
 METRIC = "CTMRG moves/s (3x3 cell, complex D=6, chi=144, split BF16x3 tensor-core products)"
 UNIT = "moves/s"
 
@@ -214,11 +215,12 @@ def run_ours(args, rank, world, local_rank):
     X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx)
     stream = torch.cuda.current_stream()
     prec = pkg.CTM_PREC_SPLIT_BF16 if args.prec == "split" else pkg.CTM_PREC_FP64
-    # steady-state SI moves: one subspace-iteration round per move from the
-    # first move on (the warm-up schedule is a convergence aid, not part of
-    # the per-move work being measured)
-    opts = pkg.ctm_default_opts(p=p, si_rounds=w["si_rounds"], warmup_iters=0, prec=prec,
-                                stream=stream.cuda_stream)
+    # the algorithm's own warm-up (first WARM_ITERS iterations with
+    # WARM_ROUNDS subspace-iteration rounds and the fp64 QR schedule) runs in
+    # the untimed warm-up steps; timed steps are steady-state SI moves with
+    # one round per move
+    opts = pkg.ctm_default_opts(p=p, si_rounds=w["si_rounds"], warmup_iters=WARM_ITERS,
+                                warmup_rounds=WARM_ROUNDS, prec=prec, stream=stream.cuda_stream)
     ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx, opts=opts)
     ctx.ctm_set_env(Cs, Ts)
     ctx.ctm_set_rangefinders(X0, W0)
@@ -235,8 +237,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clocks = Clocks(local_rank)
     clocks.start()
-    if prec == pkg.CTM_PREC_SPLIT_BF16:
-        ctx.ctm_profile_enable(True)
+    ctx.ctm_profile_enable(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -251,6 +252,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     prof = ctx.ctm_profile_read() if prec == pkg.CTM_PREC_SPLIT_BF16 else None
+    phases = {k_: round(v / args.steps, 2) for k_, v in ctx.ctm_profile_phases().items()}
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -322,6 +324,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "phase_ms_per_step": phases,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"]},
     }
@@ -347,6 +350,8 @@ def move_flops(w):
 
 def main():
     args = parse()
+    if args.impl == "ours" and args.warmup < WARM_ITERS:
+        args.warmup = WARM_ITERS
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

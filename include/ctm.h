@@ -183,10 +183,18 @@ ctm_status ctm_last_timing(const ctm_ctx* ctx, double* ms, long* launches);
  * the totals; ctm_profile_read returns the summed device time, the launch
  * count, the tensor-pipe flops (six bf16 slice products of the real-embedded,
  * unpadded problem) and the bf16 operand bytes the launches consumed.
- * CTM_EUNSUPPORTED for an FP64 context. */
+ * Kernel statistics are CTM_EUNSUPPORTED for an FP64 context; phase timing
+ * (ctm_profile_phases) works for both. */
 ctm_status ctm_profile_enable(ctm_ctx* ctx, int on);
 ctm_status ctm_profile_read(ctm_ctx* ctx, double* ms, long* launches, double* flops,
                             double* bytes);
+
+/* Device milliseconds spent since ctm_profile_enable in each phase of the
+ * move, in this order: enlarged corners, bf16 slicing of the corners,
+ * corner x block products, QR, small problem (rho, small SVD, recycling,
+ * projectors), absorption, normalisation, corner spectra. */
+#define CTM_NPHASES 8
+ctm_status ctm_profile_phases(ctm_ctx* ctx, double ms[CTM_NPHASES]);
 
 void ctm_free(ctm_ctx* ctx);
 

@@ -74,6 +74,7 @@ def load():
         "ctm_last_timing": (I, [ctx_p, P(D), P(C.c_long)]),
         "ctm_profile_enable": (I, [ctx_p, I]),
         "ctm_profile_read": (I, [ctx_p, P(D), P(C.c_long), P(D), P(D)]),
+        "ctm_profile_phases": (I, [ctx_p, P(D)]),
         "ctm_free": (None, [ctx_p]),
         "ctm_last_error": (C.c_char_p, [ctx_p]),
     }
@@ -227,6 +228,14 @@ class Context:
         _check(self.lib, self.ptr, self.lib.ctm_profile_read(
             self.ptr, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by)))
         return ms.value, n.value, fl.value, by.value
+
+    PHASES = ("corners", "slicing", "products", "qr", "small_problem", "absorption",
+              "normalisation", "spectra")
+
+    def ctm_profile_phases(self):
+        ms = (C.c_double * len(self.PHASES))()
+        _check(self.lib, self.ptr, self.lib.ctm_profile_phases(self.ptr, ms))
+        return dict(zip(self.PHASES, list(ms)))
 
     def ctm_last_timing(self):
         ms, n = C.c_double(), C.c_long()

@@ -106,12 +106,20 @@ struct ctm_ctx {
   void* imp[2] = {nullptr};    // impurity kets
   int* err = nullptr;
   int* dead = nullptr;         // k flags of the CholeskyQR repair
+  void* chol_work = nullptr;   // cooperative Cholesky scratch
   void* fac = nullptr;         // per-tensor normalisation factors
   uint64_t qr_calls = 0;       // counter of the repair directions
   int moves_done[4] = {0, 0, 0, 0};
+  int num_sms = 1;
   bool spectra_init = false;
   // split-precision state
   SplitCtx* split = nullptr;
+  // phase timing (profiling)
+  bool prof = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pph;
+  size_t pev_used = 0;
+  double phase_ms[CTM_NPHASES] = {0};
   // bookkeeping
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_ms = 0.0;
@@ -153,6 +161,38 @@ ctm_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line
   } while (0)
 
 namespace {
+
+enum Phase { PH_CORNER = 0, PH_SLICE, PH_PROD, PH_QR, PH_SMALL, PH_ABSORB, PH_NORM, PH_SPECTRA };
+
+// non-overlapping timed intervals of the move (only while profiling)
+struct PhaseScope {
+  ctm_ctx* c;
+  int ph;
+  bool on;
+  PhaseScope(ctm_ctx* c_, int ph_) : c(c_), ph(ph_) {
+    on = c->prof && c->pev_used + 2 <= c->pev.size();
+    if (on) {
+      cudaEventRecord(c->pev[c->pev_used], c->stream);
+    }
+  }
+  ~PhaseScope() {
+    if (on) {
+      cudaEventRecord(c->pev[c->pev_used + 1], c->stream);
+      c->pph[c->pev_used / 2] = ph;
+      c->pev_used += 2;
+    }
+  }
+};
+
+void phases_fold(ctm_ctx* c) {
+  for (size_t i = 0; i + 1 < c->pev_used; i += 2) {
+    cudaEventSynchronize(c->pev[i + 1]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, c->pev[i], c->pev[i + 1]);
+    c->phase_ms[c->pph[i / 2]] += t;
+  }
+  c->pev_used = 0;
+}
 
 // ------------------------------------------------------------ helpers
 size_t elems_C(const ctm_ctx* c) { return (size_t)c->chi * c->chi; }
@@ -393,6 +433,7 @@ ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
 // ------------------------------------------------- subspace iteration
 // Y = op(Q) Z for an N x N corner and an N x k block.
 ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, void* Zout) {
+  PhaseScope ps(c, PH_PROD);
   if (c->opts.prec == CTM_PREC_SPLIT_BF16 && c->split) {
     const ctm_status st = split_apply(c->split, Qm, herm, Zin, Zout, c->N, c->k, c->stream,
                                       &c->launches);
@@ -412,31 +453,55 @@ ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, 
 // Orthonormal basis of span(Z) in place (N x k): shifted CholeskyQR followed
 // by two CholeskyQR passes (CholeskyQR3, Fukaya et al. 2020). Only the span
 // enters the projectors (paper step 1), so R is not kept.
-ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp) {
+ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
+  PhaseScope ps(c, PH_QR);
   // the first two passes also find columns that are numerically in the span
   // of the previous ones (rank-deficient block: D = 1 states, fast decaying
   // spectra) and refill them with pseudo-random directions, so that the last
-  // plain pass always sees a full-rank block
+  // pass always sees a full-rank block.
+  // fp64 contexts: three passes (shifted CholeskyQR3) with fp64 Gram and
+  // product. Split mode (split contexts after the warm-up moves): two passes
+  // on the Jacobi-scaled Gram (columns of unit norm: once the rangefinders
+  // have settled, the ill-conditioning of M^H M X is column scaling) with
+  // the Gram and the product on the tensor cores; the Cholesky factorisation
+  // stays fp64. From a random start the columns are nearly parallel and
+  // need the fp64 schedule.
   ++c->qr_calls;
-  for (int pass = 0; pass < 3; ++pass) {
-    GemmDesc g;
-    g.opA = c->cx ? OP_C : OP_T;
-    g.opB = OP_N;
-    g.M = c->k; g.N = c->k; g.K = c->N;
-    g.A = Zm; g.lda = c->k;
-    g.B = Zm; g.ldb = c->k;
-    g.C = c->G; g.ldc = c->k;
-    CK(gemm(c, g));
-    CTM_CUDA_OK(chol_inv(c->cx, c->k, c->N, pass == 0, c->G, c->Linv, 1,
-                         pass < 2 ? c->dead : nullptr, c->err, c->stream, &c->launches));
-    GemmDesc h;
-    h.opA = OP_N;
-    h.opB = c->cx ? OP_C : OP_T;
-    h.M = c->N; h.N = c->k; h.K = c->k;
-    h.A = Zm; h.lda = c->k;
-    h.B = c->Linv; h.ldb = c->k;
-    h.C = tmp; h.ldc = c->k;
-    CK(gemm(c, h));
+  const bool split = split_mode && c->split != nullptr;
+  const int passes = split ? 2 : 3;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int opH = c->cx ? OP_C : OP_T;
+    if (split) {
+      const ctm_status st = split_gemm(c->split, opH, Zm, c->k, OP_N, Zm, c->k, c->k, c->k, c->N,
+                                       c->G, c->k, c->stream, &c->launches);
+      if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+    } else {
+      GemmDesc g;
+      g.opA = opH;
+      g.opB = OP_N;
+      g.M = c->k; g.N = c->k; g.K = c->N;
+      g.A = Zm; g.lda = c->k;
+      g.B = Zm; g.ldb = c->k;
+      g.C = c->G; g.ldc = c->k;
+      CK(gemm(c, g));
+    }
+    CTM_CUDA_OK(chol_inv_coop(c->cx, c->k, c->N, pass == 0, split, c->G, c->Linv, 1,
+                              pass < 2 ? c->dead : nullptr, c->chol_work, c->err, c->num_sms,
+                              c->stream, &c->launches));
+    if (split) {
+      const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, opH, c->Linv, c->k, c->N, c->k,
+                                       c->k, tmp, c->k, c->stream, &c->launches);
+      if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+    } else {
+      GemmDesc h;
+      h.opA = OP_N;
+      h.opB = opH;
+      h.M = c->N; h.N = c->k; h.K = c->k;
+      h.A = Zm; h.lda = c->k;
+      h.B = c->Linv; h.ldb = c->k;
+      h.C = tmp; h.ldc = c->k;
+      CK(gemm(c, h));
+    }
     if (pass < 2)
       CTM_CUDA_OK(repair_dead_columns(c->cx, c->N, c->k, tmp, c->dead,
                                       (c->opts.seed * 1000003ull + c->qr_calls) * 4 + pass,
@@ -471,35 +536,41 @@ ctm_status si_projectors(ctm_ctx* c, int r, int cut, void* Pl, void* PrH) {
   void** Z = c->Z;
   char& ready = c->rf_ready[r * c->S + cut];
   if (!ready) {
-    CK(qr_inplace(c, X, Z[0]));
-    CK(qr_inplace(c, W, Z[0]));
+    CK(qr_inplace(c, X, Z[0], false));
+    CK(qr_inplace(c, W, Z[0], false));
     ready = 1;
   }
-  const int rounds =
-      c->moves_done[r] < c->opts.warmup_iters ? c->opts.warmup_rounds : c->opts.si_rounds;
+  const bool warm = c->moves_done[r] < c->opts.warmup_iters;
+  const int rounds = warm ? c->opts.warmup_rounds : c->opts.si_rounds;
+  // fp64 QR schedule in fp64 contexts and during warm-up, split afterwards
+  const bool split_qr = c->split != nullptr && !warm;
+  // fp64: a QR after each application of M or M^H (the span of M^H M X
+  // without squaring cond(M)); split: one QR per update on the Jacobi-scaled
+  // block (the products themselves carry ~1e-7 errors)
+  const bool qr_each = !split_qr;
   for (int round = 0; round < rounds; ++round) {
-    // X <- qr(M^H qr(M X)): the span of M^H M X without squaring cond(M)
+    // X <- qr(M^H M X)
     CK(apply_corner(c, Q[1], false, X, Z[0]));
     CK(apply_corner(c, Q[0], false, Z[0], Z[1]));
     CK(apply_corner(c, Q[3], false, Z[1], Z[0]));
     CK(apply_corner(c, Q[2], false, Z[0], Z[1]));
-    CK(qr_inplace(c, Z[1], Z[0]));
+    if (qr_each) CK(qr_inplace(c, Z[1], Z[0], false));
     CK(apply_corner(c, Q[2], true, Z[1], Z[0]));
     CK(apply_corner(c, Q[3], true, Z[0], Z[2]));
     CK(apply_corner(c, Q[0], true, Z[2], Z[0]));
     CK(apply_corner(c, Q[1], true, Z[0], X));
-    CK(qr_inplace(c, X, Z[0]));
+    CK(qr_inplace(c, X, Z[0], split_qr));
     // W <- qr(M qr(M^H W))
     CK(apply_corner(c, Q[2], true, W, Z[0]));
     CK(apply_corner(c, Q[3], true, Z[0], Z[1]));
     CK(apply_corner(c, Q[0], true, Z[1], Z[0]));
     CK(apply_corner(c, Q[1], true, Z[0], Z[1]));
-    CK(qr_inplace(c, Z[1], Z[0]));
+    if (qr_each) CK(qr_inplace(c, Z[1], Z[0], false));
     CK(apply_corner(c, Q[1], false, Z[1], Z[0]));
     CK(apply_corner(c, Q[0], false, Z[0], Z[2]));
     CK(apply_corner(c, Q[3], false, Z[2], Z[0]));
     CK(apply_corner(c, Q[2], false, Z[0], W));
-    CK(qr_inplace(c, W, Z[0]));
+    CK(qr_inplace(c, W, Z[0], split_qr));
   }
   // Z_R = Q1 (Q2 X) in Z[2], Z_L = Q4^H (Q3^H W) in Z[3]
   CK(apply_corner(c, Q[1], false, X, Z[0]));
@@ -508,9 +579,10 @@ ctm_status si_projectors(ctm_ctx* c, int r, int cut, void* Pl, void* PrH) {
   CK(apply_corner(c, Q[3], true, Z[0], Z[3]));
   const int k = c->k, chi = c->chi;
   const int opH = c->cx ? OP_C : OP_T;
+  PhaseScope ps(c, PH_SMALL);
   CK(mm_small(c, opH, OP_N, k, k, c->N, Z[3], k, Z[2], k, c->rho, k));
-  CTM_CUDA_OK(jacobi_svd(c->cx, k, c->rho, 0, c->sv, c->u, c->v, true, c->jw, 1, 80, c->err,
-                         c->stream, &c->launches));
+  CTM_CUDA_OK(jacobi_svd_coop(c->cx, k, c->rho, 0, c->sv, c->u, c->v, true, c->jw, 1, 80,
+                              c->err, c->num_sms, c->stream, &c->launches));
   if (c->opts.sign_fix) {
     // sign fix of the small SVD (step 4): largest-modulus entry of each
     // column of u real positive, v_i takes the same phase
@@ -598,8 +670,12 @@ ctm_status move_impl(ctm_ctx* c, int r) {
     return fail(c, CTM_EUNSUPPORTED, "standard-SVD projectors are not built on the device");
   for (int x = 0; x < Lxf; ++x) {
     for (int y = 0; y < Lyf; ++y) {
-      for (int i = 0; i < 4; ++i) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
+      {
+        PhaseScope ps(c, PH_CORNER);
+        for (int i = 0; i < 4; ++i) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
+      }
       if (c->split) {
+        PhaseScope ps(c, PH_SLICE);
         const ctm_status st = split_prepare_corners(c->split, c->Q, c->N, c->stream, &c->launches);
         if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
       }
@@ -610,7 +686,11 @@ ctm_status move_impl(ctm_ctx* c, int r) {
       CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPrH, cut * NC, c), at(c->PrH, y * NC, c),
                                   NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
     }
-    for (int y = 0; y < Lyf; ++y) CK(absorb_site(c, r, x, y, Lyf));
+    {
+      PhaseScope ps(c, PH_ABSORB);
+      for (int y = 0; y < Lyf; ++y) CK(absorb_site(c, r, x, y, Lyf));
+    }
+    PhaseScope psn(c, PH_NORM);
     if (c->opts.normalize) {
       const size_t mark = c->scratch_off;
       void* w = scratch_alloc(c, (size_t)3 * 152 * Lyf * sizeof(double));
@@ -638,9 +718,11 @@ ctm_status move_impl(ctm_ctx* c, int r) {
 }
 
 ctm_status corner_spectra(ctm_ctx* c, double* out) {
+  PhaseScope ps(c, PH_SPECTRA);
   // unnormalised singular values of all 4 S corners, [label][site][chi]
-  CTM_CUDA_OK(jacobi_svd(c->cx, c->chi, c->C, (long)elems_C(c), out, nullptr, nullptr, false,
-                         c->jw, 4 * c->S, 80, c->err, c->stream, &c->launches));
+  CTM_CUDA_OK(jacobi_svd_coop(c->cx, c->chi, c->C, (long)elems_C(c), out, nullptr, nullptr,
+                              false, c->jw, 4 * c->S, 80, c->err, c->num_sms, c->stream,
+                              &c->launches));
   return CTM_OK;
 }
 
@@ -738,6 +820,12 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   }
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
     return bail(fail(c, CTM_ECUDA, "cudaEventCreate failed"));
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return bail(fail(c, CTM_ECUDA, "cannot query the SM count"));
+  }
   const size_t S = c->S, N = c->N, k = c->k, es = c->es;
   const size_t nk = elems_ket(c), nb = elems_bra(c);
   const size_t NN = N * N;
@@ -772,7 +860,8 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->rho, k * k * es);
   AL(c->u, k * k * es);
   AL(c->v, k * k * es);
-  AL(c->jw, std::max(2 * k * k, 8 * S * (size_t)chi * chi) * es);
+  AL(c->jw, std::max(jacobi_coop_work_bytes(cx, (int)k, 1),
+                     jacobi_coop_work_bytes(cx, chi, 4 * (int)S)));
   AL(c->ph, std::max(k, (size_t)chi) * es);
   AL(c->Vs, k * chi * es);
   AL(c->Us, k * chi * es);
@@ -789,6 +878,7 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->imp[1], nk * es);
   AL(c->err, sizeof(int));
   AL(c->dead, k * sizeof(int));
+  AL(c->chol_work, chol_coop_work_bytes((int)k, 1));
   AL(c->fac, Lmax * es);
 #undef AL
   if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess)
@@ -1094,8 +1184,9 @@ ctm_status ctm_spectrum(ctm_ctx* c, int x, int y, int label, double* s_out) {
   if (!valid_site(c, x, y) || label < 1 || label > 4) return fail(c, CTM_EINVAL, "bad site or label");
   Guard gd(c);
   const int site = y * c->Lx + x;
-  CTM_CUDA_OK(jacobi_svd(c->cx, c->chi, Cp(c, label - 1, site), 0, c->sv, nullptr, nullptr, false,
-                         c->jw, 1, 80, c->err, c->stream, &c->launches));
+  CTM_CUDA_OK(jacobi_svd_coop(c->cx, c->chi, Cp(c, label - 1, site), 0, c->sv, nullptr,
+                              nullptr, false, c->jw, 1, 80, c->err, c->num_sms, c->stream,
+                              &c->launches));
   CTM_CUDA_OK(normalize(false, c->chi, c->sv, 0, 1, c->dscal, true, c->scratch, c->stream, &c->launches));
   CTM_CUDA_OK(cudaMemcpyAsync(s_out, c->sv, c->chi * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(check_err(c));
@@ -1244,8 +1335,17 @@ ctm_status ctm_last_timing(const ctm_ctx* c, double* ms, long* launches) {
 
 ctm_status ctm_profile_enable(ctm_ctx* c, int on) {
   if (!c) return CTM_EINVAL;
-  if (!c->split) return fail(c, CTM_EUNSUPPORTED, "profiling covers the split-precision kernel");
   Guard gd(c);
+  if (on && c->pev.empty()) {
+    c->pev.resize(32768);
+    c->pph.resize(c->pev.size() / 2);
+    for (auto& e : c->pev)
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(c, CTM_ECUDA, "event creation failed");
+  }
+  c->prof = on != 0;
+  c->pev_used = 0;
+  for (double& v : c->phase_ms) v = 0.0;
+  if (!c->split) return CTM_OK;
   const ctm_status st = split_profile(c->split, on ? 1 : 0, nullptr, nullptr, nullptr, nullptr);
   if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
   return CTM_OK;
@@ -1261,8 +1361,18 @@ ctm_status ctm_profile_read(ctm_ctx* c, double* ms, long* launches, double* flop
   return CTM_OK;
 }
 
+ctm_status ctm_profile_phases(ctm_ctx* c, double ms[CTM_NPHASES]) {
+  if (!c || !ms) return CTM_EINVAL;
+  Guard gd(c);
+  phases_fold(c);
+  for (int i = 0; i < CTM_NPHASES; ++i) ms[i] = c->phase_ms[i];
+  return CTM_OK;
+}
+
 void ctm_free(ctm_ctx* c) {
   if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& e : c->pev) cudaEventDestroy(e);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->split) split_destroy(c->split);
   for (void* p : c->allocs) cudaFree(p);

@@ -71,6 +71,23 @@ cudaError_t jacobi_svd(bool cx, int k, const void* A, long strideA,
                        int batch, int max_sweeps, int* err, cudaStream_t s_,
                        long* launches);
 
+// The same SVD with each matrix spread over several blocks of one
+// cooperative grid (jacobi.cu); max_blocks caps the grid (SM count). work:
+// jacobi_coop_work_bytes(cx, k, batch).
+cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double* s, void* U,
+                            void* V, bool want_uv, void* work, int batch, int max_sweeps,
+                            int* err, int max_blocks, cudaStream_t s_, long* launches);
+size_t jacobi_coop_work_bytes(bool cx, int k, int batch);
+
+// chol_inv on a cooperative grid (blocked, jacobi.cu); with scale the Gram
+// is first scaled to unit diagonal (D^-1 G D^-1) and Linv returns
+// L_s^-1 D^-1, so that Z Linv^H is still the orthonormalised block. work:
+// chol_coop_work_bytes(k, batch).
+cudaError_t chol_inv_coop(bool cx, int k, long n, bool shift, bool scale, void* G, void* Linv,
+                          int batch, int* dead, void* work, int* err, int max_blocks,
+                          cudaStream_t s, long* launches);
+size_t chol_coop_work_bytes(int k, int batch);
+
 // Phase of the largest-modulus entry (lowest row on ties) of each of the
 // first ncol columns of an n x ld row-major matrix; ph gets the phase.
 cudaError_t column_phase(bool cx, long n, int ncol, long ld, const void* Z,
