@@ -107,6 +107,7 @@ struct ctm_ctx {
   int* err = nullptr;
   int* dead = nullptr;         // k flags of the CholeskyQR repair
   void* chol_work = nullptr;   // cooperative Cholesky scratch
+  double* dsc = nullptr;       // column scales of the Jacobi-scaled Gram
   void* fac = nullptr;         // per-tensor normalisation factors
   uint64_t qr_calls = 0;       // counter of the repair directions
   int moves_done[4] = {0, 0, 0, 0};
@@ -455,27 +456,23 @@ ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, 
 // enters the projectors (paper step 1), so R is not kept.
 ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
   PhaseScope ps(c, PH_QR);
-  // the first two passes also find columns that are numerically in the span
-  // of the previous ones (rank-deficient block: D = 1 states, fast decaying
-  // spectra) and refill them with pseudo-random directions, so that the last
-  // pass always sees a full-rank block.
-  // fp64 contexts: three passes (shifted CholeskyQR3) with fp64 Gram and
-  // product. Split mode (split contexts after the warm-up moves): two passes
-  // on the Jacobi-scaled Gram (columns of unit norm: once the rangefinders
-  // have settled, the ill-conditioning of M^H M X is column scaling) with
-  // the Gram and the product on the tensor cores; the Cholesky factorisation
-  // stays fp64. From a random start the columns are nearly parallel and
-  // need the fp64 schedule.
+  // every pass also finds columns that are numerically in the span of the
+  // previous ones (rank-deficient block: D = 1 states, fast decaying
+  // spectra) and refills them with pseudo-random directions; such columns
+  // carry no information of the block, and the next QR orthonormalises them.
+  // Three passes (shifted CholeskyQR3) on the Jacobi-scaled Gram (columns of
+  // unit norm; much of the ill-conditioning of M^H M X is column scaling):
+  // fp64 Gram (lower triangle), Cholesky factor in shared memory, and Q by a
+  // row-parallel triangular solve.
   ++c->qr_calls;
   const bool split = split_mode && c->split != nullptr;
-  const int passes = split ? 2 : 3;
+  const int passes = 3;
+  const bool smem_chol = chol_smem_bytes(c->cx, c->k) <= (size_t)(226 * 1024);
   for (int pass = 0; pass < passes; ++pass) {
     const int opH = c->cx ? OP_C : OP_T;
-    if (split) {
-      const ctm_status st = split_gemm(c->split, opH, Zm, c->k, OP_N, Zm, c->k, c->k, c->k, c->N,
-                                       c->G, c->k, c->stream, &c->launches);
-      if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
-    } else {
+    {
+      // the Gram stays fp64: from unsettled rangefinders its columns are
+      // nearly parallel and a ~1e-7-accurate Gram would lose the subspace
       GemmDesc g;
       g.opA = opH;
       g.opB = OP_N;
@@ -483,29 +480,35 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
       g.A = Zm; g.lda = c->k;
       g.B = Zm; g.ldb = c->k;
       g.C = c->G; g.ldc = c->k;
+      g.lower_only = smem_chol;
       CK(gemm(c, g));
     }
-    CTM_CUDA_OK(chol_inv_coop(c->cx, c->k, c->N, pass == 0, split, c->G, c->Linv, 1,
-                              pass < 2 ? c->dead : nullptr, c->chol_work, c->err, c->num_sms,
-                              c->stream, &c->launches));
-    if (split) {
-      const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, opH, c->Linv, c->k, c->N, c->k,
-                                       c->k, tmp, c->k, c->stream, &c->launches);
-      if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+    int* dead = c->dead;   // every pass finds and refills dependent columns
+    if (smem_chol) {
+      // L = chol(D^-1 G D^-1) in shared memory, Q = Z D^-1 L^-H row by row
+      CTM_CUDA_OK(chol_qr_pass(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
+                               Zm, tmp, c->err, c->num_sms, c->stream, &c->launches));
     } else {
-      GemmDesc h;
-      h.opA = OP_N;
-      h.opB = opH;
-      h.M = c->N; h.N = c->k; h.K = c->k;
-      h.A = Zm; h.lda = c->k;
-      h.B = c->Linv; h.ldb = c->k;
-      h.C = tmp; h.ldc = c->k;
-      CK(gemm(c, h));
+      CTM_CUDA_OK(chol_inv_coop(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, 1, dead,
+                                c->chol_work, c->err, c->num_sms, c->stream, &c->launches));
+      if (split) {
+        const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, opH, c->Linv, c->k, c->N, c->k,
+                                         c->k, tmp, c->k, c->stream, &c->launches);
+        if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+      } else {
+        GemmDesc h;
+        h.opA = OP_N;
+        h.opB = opH;
+        h.M = c->N; h.N = c->k; h.K = c->k;
+        h.A = Zm; h.lda = c->k;
+        h.B = c->Linv; h.ldb = c->k;
+        h.C = tmp; h.ldc = c->k;
+        CK(gemm(c, h));
+      }
     }
-    if (pass < 2)
-      CTM_CUDA_OK(repair_dead_columns(c->cx, c->N, c->k, tmp, c->dead,
-                                      (c->opts.seed * 1000003ull + c->qr_calls) * 4 + pass,
-                                      c->stream, &c->launches));
+    CTM_CUDA_OK(repair_dead_columns(c->cx, c->N, c->k, tmp, c->dead,
+                                    (c->opts.seed * 1000003ull + c->qr_calls) * 4 + pass,
+                                    c->stream, &c->launches));
     CTM_CUDA_OK(cudaMemcpyAsync(Zm, tmp, (size_t)c->N * c->k * c->es, cudaMemcpyDeviceToDevice,
                                 c->stream));
   }
@@ -879,6 +882,7 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->err, sizeof(int));
   AL(c->dead, k * sizeof(int));
   AL(c->chol_work, chol_coop_work_bytes((int)k, 1));
+  AL(c->dsc, k * sizeof(double));
   AL(c->fac, Lmax * es);
 #undef AL
   if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess)

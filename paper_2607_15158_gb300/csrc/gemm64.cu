@@ -20,6 +20,7 @@ struct GemmP {
   double2 alpha, beta;
   int splits;
   void* work;
+  int lower_only;
 };
 
 template <typename T> __device__ __forceinline__ T from2(double2 v);
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmP p) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const long m0 = (long)blockIdx.y * BM, n0 = (long)blockIdx.x * BN;
+  if (p.lower_only && n0 > m0 + BM - 1) return;   // tile strictly above the diagonal
   const int z = blockIdx.z;
   const int b = z / p.splits, sp = z % p.splits;
   const long kbeg = sp * p.kchunk;
@@ -249,6 +251,7 @@ cudaError_t gemm64(const GemmDesc& g, void* work, size_t work_bytes,
   p.C = g.C; p.ldc = g.ldc; p.sC = g.strideC;
   p.alpha = make_double2(g.alpha[0], g.alpha[1]);
   p.beta = make_double2(g.beta[0], g.beta[1]);
+  p.lower_only = g.lower_only ? 1 : 0;
   p.splits = choose_splits(g);
   if (p.splits > 1 && work_bytes < gemm64_work_bytes(g)) p.splits = 1;
   p.work = work;

@@ -108,19 +108,23 @@ __device__ __forceinline__ int player(int pos, int t, int m) {
   return pos == 0 ? 0 : ((pos - 1 + t) % m) + 1;
 }
 
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
+  // R: elements of a column held per lane (k <= 32 R); the pair's columns
+  // stay in registers between the dot product and the rotation, and the
+  // squared column norms are kept in nsq (exact at the start of each sweep,
+  // updated by alpha' = alpha - t |gamma|, beta' = beta + t |gamma|)
   const int k = a.k, G = a.G;
   const int b = blockIdx.x / G, g = blockIdx.x % G;
   const unsigned nblocks = gridDim.x;
   T* wa = static_cast<T*>(a.work) + (size_t)b * 2 * k * k;   // column c at wa[c*k]
   T* wv = wa + (size_t)k * k;
+  double* nsq = a.norms + (size_t)b * k;
   const T* Ab = static_cast<const T*>(a.A) + (size_t)b * a.strideA;
   const T one = [] {
     if constexpr (sizeof(T) == 8) return T(1.0);
     else return make_double2(1.0, 0.0);
   }();
-  // load A (row-major) into column-major work, V = I
   for (long idx = (long)g * JT + threadIdx.x; idx < (long)k * k; idx += (long)G * JT) {
     const int r = (int)(idx / k), c = (int)(idx % k);
     stcg(wa + (size_t)c * k + r, Ab[idx]);
@@ -138,6 +142,14 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
   int sweep = 0;
   bool converged = false;
   for (; sweep < a.max_sweeps; ++sweep) {
+    // exact squared norms at the start of the sweep (one warp per column)
+    for (int c = gw; c < k; c += nw) {
+      double acc = 0.0;
+      for (int r = lane; r < k; r += 32) acc += absq(ldcg(wa + (size_t)c * k + r));
+      acc = warp_sum(acc);
+      if (lane == 0) __stcg(nsq + c, acc);
+    }
+    if (!grid_barrier(a.bar, nblocks, a.err)) return;
     unsigned long long* offb = reinterpret_cast<unsigned long long*>(a.off + 2 * b + (sweep & 1));
     for (int t = 0; t < m; ++t) {
       for (int pr = gw; pr < npairs; pr += nw) {
@@ -146,17 +158,19 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
         if (q >= k) continue;
         T* ap = wa + (size_t)p * k;
         T* aq = wa + (size_t)q * k;
-        double al = 0.0, be = 0.0;
+        T xr[R], yr[R];
         T ga = zero_of(T());
-        for (int r = lane; r < k; r += 32) {
-          const T x = ldcg(ap + r), y = ldcg(aq + r);
-          al += absq(x);
-          be += absq(y);
-          fmacv(ga, x, y);
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const int r = lane + 32 * e;
+          if (r < k) {
+            xr[e] = ldcg(ap + r);
+            yr[e] = ldcg(aq + r);
+            fmacv(ga, xr[e], yr[e]);
+          }
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
         ga = warp_sum(ga);
+        const double al = __ldcg(nsq + p), be = __ldcg(nsq + q);
         const double gm = sqrt(absq(ga));
         const double nrm = sqrt(al) * sqrt(be);
         if (!(gm > tol * nrm) || gm == 0.0) continue;
@@ -165,18 +179,30 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
         const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
         const double c = 1.0 / hypot(1.0, tt), s = c * tt;
         const T eph = phase_conj<T>(ga, gm);
-        for (int r = lane; r < k; r += 32) {
-          const T x = ldcg(ap + r), y = mulv(eph, ldcg(aq + r));
-          stcg(ap + r, subv(scalev(x, c), scalev(y, s)));
-          stcg(aq + r, addv(scalev(x, s), scalev(y, c)));
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const int r = lane + 32 * e;
+          if (r < k) {
+            const T x = xr[e], y = mulv(eph, yr[e]);
+            stcg(ap + r, subv(scalev(x, c), scalev(y, s)));
+            stcg(aq + r, addv(scalev(x, s), scalev(y, c)));
+          }
+        }
+        if (lane == 0) {
+          __stcg(nsq + p, al - tt * gm);
+          __stcg(nsq + q, be + tt * gm);
         }
         if (a.want_uv) {
           T* vp = wv + (size_t)p * k;
           T* vq = wv + (size_t)q * k;
-          for (int r = lane; r < k; r += 32) {
-            const T x = ldcg(vp + r), y = mulv(eph, ldcg(vq + r));
-            stcg(vp + r, subv(scalev(x, c), scalev(y, s)));
-            stcg(vq + r, addv(scalev(x, s), scalev(y, c)));
+#pragma unroll
+          for (int e = 0; e < R; ++e) {
+            const int r = lane + 32 * e;
+            if (r < k) {
+              const T x = ldcg(vp + r), y = mulv(eph, ldcg(vq + r));
+              stcg(vp + r, subv(scalev(x, c), scalev(y, s)));
+              stcg(vq + r, addv(scalev(x, s), scalev(y, c)));
+            }
           }
         }
       }
@@ -521,7 +547,15 @@ cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double*
   cudaError_t e = cudaMemsetAsync(a.bar, 0, 3 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
-  const void* fn = cx ? (const void*)jacobi_coop<cplx> : (const void*)jacobi_coop<double>;
+  const void* fn;
+  if (k <= 32 * 5)
+    fn = cx ? (const void*)jacobi_coop<cplx, 5> : (const void*)jacobi_coop<double, 5>;
+  else if (k <= 32 * 9)
+    fn = cx ? (const void*)jacobi_coop<cplx, 9> : (const void*)jacobi_coop<double, 9>;
+  else if (k <= 32 * 16)
+    fn = cx ? (const void*)jacobi_coop<cplx, 16> : (const void*)jacobi_coop<double, 16>;
+  else
+    return cudaErrorInvalidValue;
   e = cudaLaunchCooperativeKernel(fn, dim3(batch * G), dim3(JT), args, 0, s);
   if (launches) ++*launches;
   return e;

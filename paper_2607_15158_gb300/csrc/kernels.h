@@ -28,6 +28,7 @@ struct GemmDesc {
   double alpha[2] = {1.0, 0.0};
   double beta[2] = {0.0, 0.0};
   int batch = 1;
+  bool lower_only = false;   // compute only output tiles on or below the diagonal
 };
 // C = alpha op(A) op(B) + beta C in fp64, row-major; op(A) is M x K, op(B)
 // K x N. Split-K partials (deterministic reduction) use work.
@@ -51,6 +52,16 @@ cudaError_t dot64(bool cx, bool conj_x, long n, const void* x, long sx,
 // (unit column of L); repair_dead_columns then refills it.
 cudaError_t chol_inv(bool cx, int k, long n, bool shift, void* G, void* Linv,
                      int batch, int* dead, int* err, cudaStream_t s, long* launches);
+
+// One CholeskyQR pass with the factor in shared memory: L = chol(D^-1 G D^-1
+// (+ shift I)) (D = sqrt(diag G) with scale, else I; dead-column detection as
+// in chol_inv), then Q = Z D^-1 L^-H row by row on all SMs. Needs
+// chol_smem_bytes(cx, k) <= the shared memory of one block (k <= ~166
+// complex, ~235 real); dsc receives D (k doubles).
+size_t chol_smem_bytes(bool cx, int k);
+cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, const void* G,
+                         void* L, double* dsc, int* dead, const void* Z, void* Q, int* err,
+                         int num_sms, cudaStream_t s, long* launches);
 
 // Overwrite the dead columns of a rows x k matrix with deterministic
 // pseudo-random entries (a counter-based hash of seed, column, row).

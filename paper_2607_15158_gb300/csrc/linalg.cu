@@ -543,6 +543,134 @@ __global__ void scale_by_kernel(long n, T* x, long stride, const T* fac) {
     xb[i] = mulv(xb[i], f);
 }
 
+// ---------------------------------------------------------------------
+// CholeskyQR pass with the Gram factor in shared memory: one block factors
+// the (optionally Jacobi-scaled, shifted) k x k Gram in packed lower storage
+// (fp64 bound on one SM; k(k+1)/2 elements must fit in shared memory), then
+// every block solves rows of Q L^H = Z D^-1 by forward substitution.
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+
+template <typename T>
+__global__ void __launch_bounds__(256) chol_smem_kernel(int k, long n, int shift, int scale,
+                                                        const T* G, T* L, double* dsc,
+                                                        int* dead, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);
+  double* orig = reinterpret_cast<double*>(S + (size_t)k * (k + 1) / 2);
+  __shared__ double red[8];
+  __shared__ double piv, sft_s;
+  __shared__ int isdead, bad;
+  // scales and packed load (lower triangle)
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double d = realv(G[(size_t)i * k + i]);
+    dsc[i] = scale ? (d > 0.0 ? sqrt(d) : 1.0) : 1.0;
+  }
+  __syncthreads();
+  for (long idx = threadIdx.x; idx < (long)k * (k + 1) / 2; idx += blockDim.x) {
+    // invert the packed index
+    int i = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+    while ((long)i * (i + 1) / 2 > idx) --i;
+    while ((long)(i + 1) * (i + 2) / 2 <= idx) ++i;
+    const int j = (int)(idx - (long)i * (i + 1) / 2);
+    S[idx] = scalev(G[(size_t)i * k + j], 1.0 / (dsc[i] * dsc[j]));
+  }
+  __syncthreads();
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    orig[i] = realv(S[tri(i, i)]);
+    tr += orig[i];
+    if (dead) dead[i] = 0;
+  }
+  tr = warp_sum(tr);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    sft_s = shift ? 11.0 * ((double)n * k + (double)k * (k + 1)) * DBL_EPSILON * t : 0.0;
+    bad = 0;
+  }
+  __syncthreads();
+  const double sft = sft_s;
+  if (sft != 0.0)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      if constexpr (sizeof(T) == 8) S[tri(i, i)] += sft;
+      else S[tri(i, i)].x += sft;
+    }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = realv(S[tri(j, j)]);
+      isdead = 0;
+      if (dead && (shift ? !(d - sft > fmax(1e-9 * sft, 8.0 * k * DBL_EPSILON * (orig[j] + sft)))
+                         : !(d > 1e-10 * orig[j]))) {
+        isdead = 1;
+        piv = 1.0;
+        dead[j] = 1;
+      } else if (!(d > 0.0) || !isfinite(d)) {
+        piv = 1.0;
+        bad = 1;
+      } else {
+        piv = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const double inv = 1.0 / piv;
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
+      S[tri(i, j)] = isdead ? zero_of(T()) : scalev(S[tri(i, j)], inv);
+    if (threadIdx.x == 0) {
+      if constexpr (sizeof(T) == 8) S[tri(j, j)] = isdead ? 1.0 : piv;
+      else S[tri(j, j)] = make_double2(isdead ? 1.0 : piv, 0.0);
+    }
+    __syncthreads();
+    if (!isdead) {
+      const int m = k - j - 1;
+      for (long idx = threadIdx.x; idx < (long)m * (m + 1) / 2; idx += blockDim.x) {
+        int ii = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+        while ((long)ii * (ii + 1) / 2 > idx) --ii;
+        while ((long)(ii + 1) * (ii + 2) / 2 <= idx) ++ii;
+        const int i = j + 1 + ii, l = j + 1 + (int)(idx - (long)ii * (ii + 1) / 2);
+        S[tri(i, l)] = subv(S[tri(i, l)], mulv(S[tri(i, j)], conjv(S[tri(l, j)])));
+      }
+    }
+    __syncthreads();
+  }
+  if (bad && threadIdx.x == 0) atomicOr(err, DEV_CHOL_PIVOT);
+  for (long idx = threadIdx.x; idx < (long)k * k; idx += blockDim.x) {
+    const int i = (int)(idx / k), j = (int)(idx % k);
+    L[idx] = (j <= i) ? S[tri(i, j)] : zero_of(T());
+  }
+}
+
+// rows r of Q: q L^H = z D^-1, i.e. q_j = (z_j / D_j - sum_{i<j} q_i conj(L_ji)) / L_jj
+template <typename T>
+__global__ void __launch_bounds__(32) trsm_rows_kernel(long rows, int k, const T* L,
+                                                        const double* dsc, const T* Z, T* Q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);
+  double* dinv = reinterpret_cast<double*>(S + (size_t)k * (k + 1) / 2);
+  for (long idx = threadIdx.x; idx < (long)k * (k + 1) / 2; idx += blockDim.x) {
+    int i = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+    while ((long)i * (i + 1) / 2 > idx) --i;
+    while ((long)(i + 1) * (i + 2) / 2 <= idx) ++i;
+    const int j = (int)(idx - (long)i * (i + 1) / 2);
+    S[idx] = (i == j) ? L[(size_t)i * k + i] : conjv(L[(size_t)i * k + j]);
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) dinv[i] = 1.0 / dsc[i];
+  __syncthreads();
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < rows;
+       r += (long)gridDim.x * blockDim.x) {
+    const T* z = Z + r * k;
+    T* q = Q + r * k;
+    for (int j = 0; j < k; ++j) {
+      T acc = scalev(z[j], dinv[j]);
+      const T* Lj = S + tri(j, 0);
+      for (int i = 0; i < j; ++i) acc = subv(acc, mulv(q[i], Lj[i]));
+      q[j] = scalev(acc, 1.0 / realv(Lj[j]));
+    }
+  }
+}
+
 unsigned grid_for(long n, int per = 256, long cap = 152L * 8) {
   long g = (n + per - 1) / per;
   if (g < 1) g = 1;
@@ -561,6 +689,49 @@ cudaError_t chol_inv(bool cx, int k, long n, bool shift, void* G, void* Linv,
     chol_inv_kernel<double><<<batch, 256, shm, s>>>(k, n, shift, (double*)G, (double*)Linv,
                                                      dead, err);
   if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+size_t chol_smem_bytes(bool cx, int k) {
+  return (size_t)k * (k + 1) / 2 * (cx ? 16 : 8) + (size_t)k * sizeof(double) + 16;
+}
+
+cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, const void* G,
+                         void* L, double* dsc, int* dead, const void* Z, void* Q, int* err,
+                         int num_sms, cudaStream_t s, long* launches) {
+  const size_t shm = chol_smem_bytes(cx, k);
+  static size_t configured[2] = {0, 0};
+  if (shm > configured[cx ? 1 : 0]) {
+    cudaError_t e;
+    if (cx) {
+      e = cudaFuncSetAttribute(chol_smem_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(trsm_rows_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    } else {
+      e = cudaFuncSetAttribute(chol_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(trsm_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    }
+    if (e != cudaSuccess) return e;
+    configured[cx ? 1 : 0] = shm;
+  }
+  // one warp per block and one block per SM (the factor fills shared
+  // memory): rows spread over every SM's fp64 units
+  long g = (rows + 31) / 32;
+  if (g > num_sms) g = num_sms;
+  if (g < 1) g = 1;
+  if (cx) {
+    chol_smem_kernel<cplx><<<1, 256, shm, s>>>(k, rows, shift, scale, (const cplx*)G, (cplx*)L, dsc,
+                                                dead, err);
+    trsm_rows_kernel<cplx><<<(unsigned)g, 32, shm, s>>>(rows, k, (const cplx*)L, dsc,
+                                                          (const cplx*)Z, (cplx*)Q);
+  } else {
+    chol_smem_kernel<double><<<1, 256, shm, s>>>(k, rows, shift, scale, (const double*)G, (double*)L,
+                                                  dsc, dead, err);
+    trsm_rows_kernel<double><<<(unsigned)g, 32, shm, s>>>(rows, k, (const double*)L, dsc,
+                                                            (const double*)Z, (double*)Q);
+  }
+  if (launches) *launches += 2;
   return cudaGetLastError();
 }
 
