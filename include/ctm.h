@@ -202,6 +202,37 @@ void ctm_free(ctm_ctx* ctx);
  * ctx is NULL); owned by the library, valid until the next call. */
 const char* ctm_last_error(const ctm_ctx* ctx);
 
+/* Singular values of one k x k matrix, with no device allocation.
+ *
+ * The paper has no counterpart to this call: it is a library service for
+ * callers that cannot let a library allocate device memory (an application
+ * that owns all device memory through its own allocator, or a loop in which a
+ * cudaMalloc / cudaFree would stall on a device-wide synchronisation). It runs
+ * the same one-sided Jacobi kernel as ctm_spectrum, but keeps all of its
+ * scratch in one fixed array of 2 MiB + 4 KiB reserved in device memory for
+ * every GPU that loads the library, for the life of the process.
+ *
+ *   A       device pointer, the matrix in column-major order, k*k elements of
+ *           double (CTM_F64) or interleaved (re, im) double pairs (CTM_C128);
+ *           read only, owned by the caller.
+ *   k       1 <= k <= 256 for CTM_C128, k <= 362 for CTM_F64; larger k is
+ *           rejected with CTM_EINVAL before any device work.
+ *   s       device pointer to k doubles, owned by the caller: the singular
+ *           values, not normalised, in descending order.
+ *   stream  the cudaStream_t to run on (NULL: the legacy default stream).
+ *
+ * The first call on a device looks up the device address of the scratch array
+ * with that device current; make it before any stream capture. The call
+ * clears the words that must start at zero (error word, grid-barrier
+ * counters) on the stream itself, then waits for the stream to read the error
+ * word back, so it returns only once s is written. Calls that overlap on one
+ * device (from several threads or streams) share the scratch and race:
+ * serialise them. Returns CTM_OK, CTM_EINVAL, CTM_ECUDA, CTM_ENUMERIC,
+ * CTM_ENOCONV or CTM_ETIMEOUT; the message is read with
+ * ctm_noalloc_last_error() (per host thread). */
+ctm_status ctm_svdvals_noalloc(const void* A, int k, ctm_dtype dtype, double* s, void* stream);
+const char* ctm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

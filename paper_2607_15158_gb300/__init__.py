@@ -77,6 +77,8 @@ def load():
         "ctm_profile_phases": (I, [ctx_p, P(D)]),
         "ctm_free": (None, [ctx_p]),
         "ctm_last_error": (C.c_char_p, [ctx_p]),
+        "ctm_svdvals_noalloc": (I, [VP, I, I, VP, VP]),
+        "ctm_noalloc_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -241,6 +243,17 @@ class Context:
         ms, n = C.c_double(), C.c_long()
         _check(self.lib, self.ptr, self.lib.ctm_last_timing(self.ptr, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+
+def ctm_svdvals_noalloc(A_dev, k, dtype, s_dev, stream=0):
+    """Singular values of the k x k column-major matrix at device address
+    A_dev into k doubles at device address s_dev, with no device allocation
+    (scratch is the library's fixed device array); returns the status."""
+    lib = load()
+    st = lib.ctm_svdvals_noalloc(A_dev, k, dtype, s_dev, stream or None)
+    if st != CTM_OK:
+        raise CTMError(st, (lib.ctm_noalloc_last_error() or b"").decode())
+    return st
 
 
 def ctm_init(Lx, Ly, A, d, D, chi, cplx=None, bra=None, opts=None):

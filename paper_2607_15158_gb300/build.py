@@ -18,7 +18,8 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libctm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ctm.cu", "permute.cu", "gemm64.cu", "linalg.cu", "jacobi.cu", "split_gemm.cu"]
+SOURCES = ["ctm.cu", "permute.cu", "gemm64.cu", "linalg.cu", "jacobi.cu", "split_gemm.cu",
+           "noalloc.cu"]
 
 
 def nvcc():
