@@ -241,12 +241,15 @@ def run_ours(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    # bracket the timed steps for profilers started with --profile-from-start off
+    torch.cuda.profiler.start()
     e0.record(stream)
     launches = 0
     for _ in range(args.steps):
         launches += step()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()

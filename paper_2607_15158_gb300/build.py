@@ -19,7 +19,8 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libctm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ctm.cu", "permute.cu", "gemm64.cu", "linalg.cu", "jacobi.cu", "split_gemm.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "cholqr_mixed.cu",
+           "absorb.cu"]
 
 
 def nvcc():

@@ -83,18 +83,20 @@ struct ctm_ctx {
   void* lastPrH = nullptr;
   int last_dir = -1;
   void* Z[4] = {nullptr};    // N x k blocks
+  void* ZR = nullptr;        // [Lmax][N k] Z_R, Z_L of the cuts of a column
+  void* ZL = nullptr;
   void* Xn = nullptr;
   void* Wn = nullptr;
   void* G = nullptr;         // k x k
   void* Linv = nullptr;
-  void* rho = nullptr;
-  void* u = nullptr;
+  void* rho = nullptr;       // [Lmax][k k]
+  void* u = nullptr;         // [Lmax][k k]
   void* v = nullptr;
-  void* jw = nullptr;        // Jacobi work, max(2 k^2, 8 S chi^2) elements
+  void* jw = nullptr;        // Jacobi work, max(2 Lmax k^2, 8 S chi^2) elements
   void* ph = nullptr;
   void* Vs = nullptr;        // k x chi
   void* Us = nullptr;
-  double* sv = nullptr;      // max(k, 4 S chi)
+  double* sv = nullptr;      // max(Lmax k, 4 S chi)
   void* stC1 = nullptr;      // staging [Lmax][chi^2]
   void* stC4 = nullptr;
   void* stT4 = nullptr;      // [Lmax][chi^2 Dk Db]
@@ -424,6 +426,12 @@ ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
   CK(ein(c, "pm,mnuv->pnuv", tn(Cc, {chi, chi}), false, tn(Ta, {chi, chi, Dk, Db}), false, CT));
   Tn CTT = tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db});
   CK(ein(c, "tplw,pnuv->tlwnuv", tn(Tb, {chi, chi, Dk, Db}), false, CT, false, CTT));
+  if (absorb_ab_supported((int)Dk, (int)Db, (int)d)) {
+    // A and B in one pass over the block (fp32 arithmetic in split contexts)
+    CTM_CUDA_OK(absorb_ab(c->cx, c->split != nullptr, (int)chi, (int)Dk, (int)Db, (int)d, CTT.p,
+                          A, B, Qout, c->num_sms, c->stream, &c->launches));
+    return CTM_OK;
+  }
   Tn R1 = tn(c->pipe[0], {chi, Db, chi, Db, d, Dk, Dk});
   CK(ein(c, "tlwnuv,sulde->twnvsde", CTT, false, tn(A, {d, Dk, Dk, Dk, Dk}), false, R1));
   CK(ein(c, "twnvsde,svwDE->tdDneE", R1, false, tn(B, {d, Db, Db, Db, Db}), false,
@@ -470,6 +478,28 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
   const bool smem_chol = chol_smem_bytes(c->cx, c->k) <= (size_t)(226 * 1024);
   for (int pass = 0; pass < passes; ++pass) {
     const int opH = c->cx ? OP_C : OP_T;
+    if (split && pass == passes - 1) {
+      // last pass of a split context: the block is orthonormal to ~1e-8, so
+      // Q <- Q L^-H with L = chol(Q^H Q) = I + F is applied to first order,
+      // Q <- Q - Q F^H: the fp64 Gram fixes F, and the small correction
+      // Q F^H runs on the tensor cores (its ~1e-7 relative error is ~1e-15
+      // of Q)
+      GemmDesc g;
+      g.opA = opH;
+      g.opB = OP_N;
+      g.M = c->k; g.N = c->k; g.K = c->N;
+      g.A = Zm; g.lda = c->k;
+      g.B = Zm; g.ldb = c->k;
+      g.C = c->G; g.ldc = c->k;
+      g.lower_only = true;
+      CK(gemm(c, g));
+      CTM_CUDA_OK(orth_correction(c->cx, c->k, c->G, c->Linv, c->stream, &c->launches));
+      const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, OP_N, c->Linv, c->k, c->N, c->k,
+                                       c->k, tmp, c->k, c->stream, &c->launches);
+      if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+      CTM_CUDA_OK(sub_inplace(c->cx, c->N * c->k, Zm, tmp, c->stream, &c->launches));
+      break;
+    }
     {
       // the Gram stays fp64: from unsettled rangefinders its columns are
       // nearly parallel and a ~1e-7-accurate Gram would lose the subspace
@@ -526,12 +556,13 @@ ctm_status mm_small(ctm_ctx* c, int opA, int opB, long M, long Nn, long K, const
   return gemm(c, g);
 }
 
-// SI projectors of one cut (paper "QR-based projector", steps 1-4): rounds of
-// X <- qr(M^H M X), W <- qr(M M^H W) with M = Q3 Q4 Q1 Q2 applied one corner
-// at a time; Z_R = Q1 Q2 X, Z_L = (Q3 Q4)^H W, rho = Z_L^H Z_R = u s v^H;
-// phases fixed on the columns of W u; P_l = Z_R v_chi s^-1/2,
-// P_r^H = Z_L u_chi s^-1/2; X <- X v, W <- W u.
-ctm_status si_projectors(ctm_ctx* c, int r, int cut, void* Pl, void* PrH) {
+// SI projectors of one cut (paper "QR-based projector", steps 1-4), first
+// half: rounds of X <- qr(M^H M X), W <- qr(M M^H W) with M = Q3 Q4 Q1 Q2
+// applied one corner at a time; Z_R = Q1 Q2 X and Z_L = (Q3 Q4)^H W into
+// slot y, rho = Z_L^H Z_R (Eq. rho_hat_diag) into slot y. The small SVDs of
+// all cuts of a column then run as one batched launch (si_small_svd), and
+// si_finish builds the projectors.
+ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
   const size_t Nk = (size_t)c->N * c->k;
   void* X = at(c->X, (size_t)(r * c->S + cut) * Nk, c);
   void* W = at(c->W, (size_t)(r * c->S + cut) * Nk, c);
@@ -575,32 +606,69 @@ ctm_status si_projectors(ctm_ctx* c, int r, int cut, void* Pl, void* PrH) {
     CK(apply_corner(c, Q[2], false, Z[0], W));
     CK(qr_inplace(c, W, Z[0], split_qr));
   }
-  // Z_R = Q1 (Q2 X) in Z[2], Z_L = Q4^H (Q3^H W) in Z[3]
+  // Z_R = Q1 (Q2 X), Z_L = Q4^H (Q3^H W)
+  void* ZR = at(c->ZR, y * Nk, c);
+  void* ZL = at(c->ZL, y * Nk, c);
   CK(apply_corner(c, Q[1], false, X, Z[0]));
-  CK(apply_corner(c, Q[0], false, Z[0], Z[2]));
+  CK(apply_corner(c, Q[0], false, Z[0], ZR));
   CK(apply_corner(c, Q[2], true, W, Z[0]));
-  CK(apply_corner(c, Q[3], true, Z[0], Z[3]));
-  const int k = c->k, chi = c->chi;
+  CK(apply_corner(c, Q[3], true, Z[0], ZL));
+  const int k = c->k;
   const int opH = c->cx ? OP_C : OP_T;
   PhaseScope ps(c, PH_SMALL);
-  CK(mm_small(c, opH, OP_N, k, k, c->N, Z[3], k, Z[2], k, c->rho, k));
-  CTM_CUDA_OK(jacobi_svd_coop(c->cx, k, c->rho, 0, c->sv, c->u, c->v, true, c->jw, 1, 80,
-                              c->err, c->num_sms, c->stream, &c->launches));
+  CK(mm_small(c, opH, OP_N, k, k, c->N, ZL, k, ZR, k, at(c->rho, (size_t)y * k * k, c), k));
+  return CTM_OK;
+}
+
+// rho = u s v^H for the slots 0 .. n-1 in one cooperative launch.
+ctm_status si_small_svd(ctm_ctx* c, int n) {
+  PhaseScope ps(c, PH_SMALL);
+  const int k = c->k;
+  CTM_CUDA_OK(jacobi_svd_coop(c->cx, k, c->rho, (long)k * k, c->sv, c->u, c->v, true, c->jw, n,
+                              80, c->err, c->num_sms, c->stream, &c->launches));
+  return CTM_OK;
+}
+
+// Second half for slot y: sign fix (step 4), recycling X <- X v, W <- W u
+// (Eq. xy_recycle), P_l = Z_R v_chi s^-1/2, P_r^H = Z_L u_chi s^-1/2
+// (Eq. projectors_diag).
+ctm_status si_finish(ctm_ctx* c, int r, int cut, int y, void* Pl, void* PrH) {
+  const size_t Nk = (size_t)c->N * c->k;
+  const int k = c->k, chi = c->chi;
+  void* X = at(c->X, (size_t)(r * c->S + cut) * Nk, c);
+  void* W = at(c->W, (size_t)(r * c->S + cut) * Nk, c);
+  void* ZR = at(c->ZR, y * Nk, c);
+  void* ZL = at(c->ZL, y * Nk, c);
+  void* u = at(c->u, (size_t)y * k * k, c);
+  void* v = at(c->v, (size_t)y * k * k, c);
+  const double* sv = c->sv + (size_t)y * k;
+  PhaseScope ps(c, PH_SMALL);
   if (c->opts.sign_fix) {
     // sign fix of the small SVD (step 4): largest-modulus entry of each
     // column of u real positive, v_i takes the same phase
-    CTM_CUDA_OK(column_phase(c->cx, k, k, k, c->u, c->ph, 1, 0, c->stream, &c->launches));
-    CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, c->u, c->ph, c->stream, &c->launches));
-    CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, c->v, c->ph, c->stream, &c->launches));
+    CTM_CUDA_OK(column_phase(c->cx, k, k, k, u, c->ph, 1, 0, c->stream, &c->launches));
+    CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, u, c->ph, c->stream, &c->launches));
+    CTM_CUDA_OK(scale_columns_conj(c->cx, k, k, k, v, c->ph, c->stream, &c->launches));
   }
-  CK(mm_small(c, OP_N, OP_N, c->N, k, k, X, k, c->v, k, c->Xn, k));
-  CK(mm_small(c, OP_N, OP_N, c->N, k, k, W, k, c->u, k, c->Wn, k));
-  CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, c->v, c->sv, c->opts.svd_rel_cutoff, c->Vs,
+  // recycled bases X v, W u: the next update re-orthonormalises them, so in
+  // split contexts they run on the tensor cores
+  if (c->split) {
+    ctm_status st = split_gemm(c->split, OP_N, X, k, OP_N, v, k, (int)c->N, k, k, c->Xn, k,
+                               c->stream, &c->launches);
+    if (st == CTM_OK)
+      st = split_gemm(c->split, OP_N, W, k, OP_N, u, k, (int)c->N, k, k, c->Wn, k, c->stream,
+                      &c->launches);
+    if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+  } else {
+    CK(mm_small(c, OP_N, OP_N, c->N, k, k, X, k, v, k, c->Xn, k));
+    CK(mm_small(c, OP_N, OP_N, c->N, k, k, W, k, u, k, c->Wn, k));
+  }
+  CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, v, sv, c->opts.svd_rel_cutoff, c->Vs,
                                 c->stream, &c->launches));
-  CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, c->u, c->sv, c->opts.svd_rel_cutoff, c->Us,
+  CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, u, sv, c->opts.svd_rel_cutoff, c->Us,
                                 c->stream, &c->launches));
-  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, Z[2], k, c->Vs, chi, Pl, chi));
-  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, Z[3], k, c->Us, chi, PrH, chi));
+  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, ZR, k, c->Vs, chi, Pl, chi));
+  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, ZL, k, c->Us, chi, PrH, chi));
   CTM_CUDA_OK(cudaMemcpyAsync(X, c->Xn, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
   CTM_CUDA_OK(cudaMemcpyAsync(W, c->Wn, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
   return CTM_OK;
@@ -640,6 +708,17 @@ ctm_status absorb_site(ctm_ctx* c, int r, int x, int y, int Lyf) {
   CK(ein(c, "tndD,ndDc->tc", E4, false, tn(Pl_dn, {chi, Dk, Db, chi}), false,
          tn(oC4, {chi, chi})));
   // T4'
+  if (absorb_ab_supported((int)Dk, (int)Db, (int)d)) {
+    Tn Y1 = tn(c->pipe[0], {chi, Dk, Db, chi, Dk, Db});
+    CK(ein(c, "tqlw,quvc->tlwcuv", tn(T4, {chi, chi, Dk, Db}), false,
+           tn(Pl_up, {chi, Dk, Db, chi}), false, Y1));
+    Tn R2 = tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db});
+    CTM_CUDA_OK(absorb_ab(c->cx, c->split != nullptr, (int)chi, (int)Dk, (int)Db, (int)d, Y1.p, A,
+                          B, R2.p, c->num_sms, c->stream, &c->launches));
+    CK(ein(c, "tdDa,tdDceE->aceE", tn(PrH_dn, {chi, Dk, Db, chi}), true, R2, false,
+           tn(oT4, {chi, chi, Dk, Db})));
+    return CTM_OK;
+  }
   Tn Y1 = tn(c->pipe[0], {chi, Dk, Db, Dk, Db, chi});
   CK(ein(c, "tqlw,quvc->tlwuvc", tn(T4, {chi, chi, Dk, Db}), false,
          tn(Pl_up, {chi, Dk, Db, chi}), false, Y1));
@@ -682,8 +761,14 @@ ctm_status move_impl(ctm_ctx* c, int r) {
         const ctm_status st = split_prepare_corners(c->split, c->Q, c->N, c->stream, &c->launches);
         if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
       }
+      CK(si_rho(c, r, y * Lxf + x, y));
+    }
+    // the cuts of a column are independent until the absorption: their
+    // small SVDs share one launch
+    CK(si_small_svd(c, Lyf));
+    for (int y = 0; y < Lyf; ++y) {
       const int cut = y * Lxf + x;
-      CK(si_projectors(c, r, cut, at(c->Pl, y * NC, c), at(c->PrH, y * NC, c)));
+      CK(si_finish(c, r, cut, y, at(c->Pl, y * NC, c), at(c->PrH, y * NC, c)));
       CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPl, cut * NC, c), at(c->Pl, y * NC, c), NC * c->es,
                                   cudaMemcpyDeviceToDevice, c->stream));
       CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPrH, cut * NC, c), at(c->PrH, y * NC, c),
@@ -860,15 +945,17 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->Wn, N * k * es);
   AL(c->G, k * k * es);
   AL(c->Linv, k * k * es);
-  AL(c->rho, k * k * es);
-  AL(c->u, k * k * es);
-  AL(c->v, k * k * es);
-  AL(c->jw, std::max(jacobi_coop_work_bytes(cx, (int)k, 1),
+  AL(c->ZR, Lmax * N * k * es);
+  AL(c->ZL, Lmax * N * k * es);
+  AL(c->rho, Lmax * k * k * es);
+  AL(c->u, Lmax * k * k * es);
+  AL(c->v, Lmax * k * k * es);
+  AL(c->jw, std::max(jacobi_coop_work_bytes(cx, (int)k, Lmax),
                      jacobi_coop_work_bytes(cx, chi, 4 * (int)S)));
   AL(c->ph, std::max(k, (size_t)chi) * es);
   AL(c->Vs, k * chi * es);
   AL(c->Us, k * chi * es);
-  AL(c->sv, std::max(k, 4 * S * (size_t)chi) * sizeof(double));
+  AL(c->sv, std::max(Lmax * k, 4 * S * (size_t)chi) * sizeof(double));
   AL(c->stC1, Lmax * elems_C(c) * es);
   AL(c->stC4, Lmax * elems_C(c) * es);
   AL(c->stT4, Lmax * elems_T(c) * es);

@@ -63,6 +63,26 @@ cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, cons
                          void* L, double* dsc, int* dead, const void* Z, void* Q, int* err,
                          int num_sms, cudaStream_t s, long* launches);
 
+// ------------------------------------------------------------- absorb.cu
+// Out[t,d,D,n,e,E] = sum A[s,u,l,d,e] B[s,v,w,D,E] In[t,l,w,n,u,v] with In,
+// Out [chi, Dk, Db, chi, Dk, Db] (single-layer absorption of the ket and bra
+// tensors into an enlarged corner or edge); fp32 arithmetic when fp32.
+// Supported for Dk, Db <= 6 and d <= 4 (absorb_ab_supported).
+bool absorb_ab_supported(int Dk, int Db, int d);
+cudaError_t absorb_ab(bool cx, bool fp32, int chi, int Dk, int Db, int d, const void* In,
+                      const void* A, const void* B, void* Out, int num_sms, cudaStream_t s,
+                      long* launches);
+
+// ------------------------------------------------------- cholqr_mixed.cu
+// B = F^H with F = tril(G - I, -1) + diag(G - I) / 2 from the lower triangle
+// of an fp64 Gram G of a nearly orthonormal block (first-order Cholesky
+// factor of G = (I + F)(I + F)^H).
+cudaError_t orth_correction(bool cx, int k, const void* G, void* B, cudaStream_t s,
+                            long* launches);
+// z -= d elementwise (n elements).
+cudaError_t sub_inplace(bool cx, long n, void* z, const void* d, cudaStream_t s,
+                        long* launches);
+
 // Overwrite the dead columns of a rows x k matrix with deterministic
 // pseudo-random entries (a counter-based hash of seed, column, row).
 cudaError_t repair_dead_columns(bool cx, long rows, int k, void* Q, const int* dead,

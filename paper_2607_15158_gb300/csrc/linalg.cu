@@ -556,7 +556,8 @@ __global__ void __launch_bounds__(256) chol_smem_kernel(int k, long n, int shift
                                                         int* dead, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);
-  double* orig = reinterpret_cast<double*>(S + (size_t)k * (k + 1) / 2);
+  T* colj = S + (size_t)k * (k + 1) / 2;   // conj of column j of L, contiguous
+  double* orig = reinterpret_cast<double*>(colj + k);
   __shared__ double red[8];
   __shared__ double piv, sft_s;
   __shared__ int isdead, bad;
@@ -616,21 +617,24 @@ __global__ void __launch_bounds__(256) chol_smem_kernel(int k, long n, int shift
     }
     __syncthreads();
     const double inv = 1.0 / piv;
-    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
-      S[tri(i, j)] = isdead ? zero_of(T()) : scalev(S[tri(i, j)], inv);
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+      const T v = isdead ? zero_of(T()) : scalev(S[tri(i, j)], inv);
+      S[tri(i, j)] = v;
+      colj[i] = conjv(v);
+    }
     if (threadIdx.x == 0) {
       if constexpr (sizeof(T) == 8) S[tri(j, j)] = isdead ? 1.0 : piv;
       else S[tri(j, j)] = make_double2(isdead ? 1.0 : piv, 0.0);
     }
     __syncthreads();
     if (!isdead) {
-      const int m = k - j - 1;
-      for (long idx = threadIdx.x; idx < (long)m * (m + 1) / 2; idx += blockDim.x) {
-        int ii = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-        while ((long)ii * (ii + 1) / 2 > idx) --ii;
-        while ((long)(ii + 1) * (ii + 2) / 2 <= idx) ++ii;
-        const int i = j + 1 + ii, l = j + 1 + (int)(idx - (long)ii * (ii + 1) / 2);
-        S[tri(i, l)] = subv(S[tri(i, l)], mulv(S[tri(i, j)], conjv(S[tri(l, j)])));
+      // trailing update S(i, l) -= L(i, j) conj(L(l, j)), j < l <= i: one
+      // row per warp, lanes along the row
+      const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int i = j + 1 + wp; i < k; i += nw) {
+        const T a = S[tri(i, j)];
+        T* Si = S + tri(i, 0);
+        for (int l = j + 1 + ln; l <= i; l += 32) Si[l] = subv(Si[l], mulv(a, colj[l]));
       }
     }
     __syncthreads();
@@ -642,31 +646,65 @@ __global__ void __launch_bounds__(256) chol_smem_kernel(int k, long n, int shift
   }
 }
 
-// rows r of Q: q L^H = z D^-1, i.e. q_j = (z_j / D_j - sum_{i<j} q_i conj(L_ji)) / L_jj
-template <typename T>
-__global__ void __launch_bounds__(32) trsm_rows_kernel(long rows, int k, const T* L,
-                                                        const double* dsc, const T* Z, T* Q) {
+// rows r of Q: q L^H = z D^-1, i.e. q_j = (z_j / D_j - sum_{i<j} q_i conj(L_ji)) / L_jj.
+// One warp per row, right-looking: lane l owns the columns l, l + 32, ...
+// (R of them, in registers); at step j the owner of column j finishes
+// q_j = acc_j / L_jj and broadcasts it, and every lane subtracts
+// q_j conj(L_ij) from its columns i > j. Each row costs k^2 / 2 multiply-adds
+// and no reductions; conj(L) is kept column by column (packed) in shared
+// memory so that the lanes read consecutive entries.
+template <typename T, int R>
+__global__ void __launch_bounds__(1024, 1) trsm_warp_kernel(long rows, int k, const T* L,
+                                                            const double* dsc, const T* Z,
+                                                            T* Q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);
-  double* dinv = reinterpret_cast<double*>(S + (size_t)k * (k + 1) / 2);
-  for (long idx = threadIdx.x; idx < (long)k * (k + 1) / 2; idx += blockDim.x) {
-    int i = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-    while ((long)i * (i + 1) / 2 > idx) --i;
-    while ((long)(i + 1) * (i + 2) / 2 <= idx) ++i;
-    const int j = (int)(idx - (long)i * (i + 1) / 2);
-    S[idx] = (i == j) ? L[(size_t)i * k + i] : conjv(L[(size_t)i * k + j]);
+  T* Lc = reinterpret_cast<T*>(smem_raw);   // column j at Lc[j k - j (j - 1) / 2 + i - j]
+  double* rinv = reinterpret_cast<double*>(Lc + (size_t)k * (k + 1) / 2);
+  double* dinv = rinv + k;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wp; j < k; j += nw) {
+    const int off = j * k - j * (j - 1) / 2;
+    for (int i = j + lane; i < k; i += 32) Lc[off + i - j] = conjv(L[(size_t)i * k + j]);
+    if (lane == 0) {
+      rinv[j] = 1.0 / realv(L[(size_t)j * k + j]);
+      dinv[j] = 1.0 / dsc[j];
+    }
   }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) dinv[i] = 1.0 / dsc[i];
   __syncthreads();
-  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < rows;
-       r += (long)gridDim.x * blockDim.x) {
+  for (long r = (long)blockIdx.x * nw + wp; r < rows; r += (long)gridDim.x * nw) {
     const T* z = Z + r * k;
-    T* q = Q + r * k;
-    for (int j = 0; j < k; ++j) {
-      T acc = scalev(z[j], dinv[j]);
-      const T* Lj = S + tri(j, 0);
-      for (int i = 0; i < j; ++i) acc = subv(acc, mulv(q[i], Lj[i]));
-      q[j] = scalev(acc, 1.0 / realv(Lj[j]));
+    T a[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int i = lane + 32 * e;
+      a[e] = i < k ? scalev(z[i], dinv[i]) : zero_of(T());
+    }
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = 32 * e + jj;
+        if (j >= k) break;
+        if (lane == jj) a[e] = scalev(a[e], rinv[j]);
+        T q;
+        if constexpr (sizeof(T) == 8) {
+          q = __shfl_sync(0xffffffffu, a[e], jj);
+        } else {
+          q.x = __shfl_sync(0xffffffffu, a[e].x, jj);
+          q.y = __shfl_sync(0xffffffffu, a[e].y, jj);
+        }
+        const T* Lj = Lc + (j * k - j * (j - 1) / 2) - j;
+#pragma unroll
+        for (int e2 = e; e2 < R; ++e2) {
+          const int i = lane + 32 * e2;
+          if (i > j && i < k) a[e2] = subv(a[e2], mulv(q, Lj[i]));
+        }
+      }
+    }
+    T* qo = Q + r * k;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int i = lane + 32 * e;
+      if (i < k) qo[i] = a[e];
     }
   }
 }
@@ -693,8 +731,35 @@ cudaError_t chol_inv(bool cx, int k, long n, bool shift, void* G, void* Linv,
 }
 
 size_t chol_smem_bytes(bool cx, int k) {
-  return (size_t)k * (k + 1) / 2 * (cx ? 16 : 8) + (size_t)k * sizeof(double) + 16;
+  return ((size_t)k * (k + 1) / 2 + k) * (cx ? 16 : 8) + (size_t)k * sizeof(double) + 16;
 }
+
+template <typename T>
+cudaError_t trsm_set_smem(int shm) {
+  cudaError_t e = cudaSuccess;
+  const void* fns[] = {(const void*)trsm_warp_kernel<T, 2>, (const void*)trsm_warp_kernel<T, 4>,
+                       (const void*)trsm_warp_kernel<T, 6>, (const void*)trsm_warp_kernel<T, 8>};
+  for (const void* f : fns)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  return e;
+}
+
+// R = columns per lane: the smallest of 2, 4, 6, 8 with 32 R >= k
+#define CTM_TRSM_LAUNCH(T)                                                                     \
+  do {                                                                                         \
+    if (k <= 64)                                                                               \
+      trsm_warp_kernel<T, 2><<<(unsigned)g, 1024, shm, s>>>(rows, k, (const T*)L, dsc,         \
+                                                             (const T*)Z, (T*)Q);              \
+    else if (k <= 128)                                                                         \
+      trsm_warp_kernel<T, 4><<<(unsigned)g, 1024, shm, s>>>(rows, k, (const T*)L, dsc,         \
+                                                             (const T*)Z, (T*)Q);              \
+    else if (k <= 192)                                                                         \
+      trsm_warp_kernel<T, 6><<<(unsigned)g, 1024, shm, s>>>(rows, k, (const T*)L, dsc,         \
+                                                             (const T*)Z, (T*)Q);              \
+    else                                                                                       \
+      trsm_warp_kernel<T, 8><<<(unsigned)g, 1024, shm, s>>>(rows, k, (const T*)L, dsc,         \
+                                                             (const T*)Z, (T*)Q);              \
+  } while (0)
 
 cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, const void* G,
                          void* L, double* dsc, int* dead, const void* Z, void* Q, int* err,
@@ -705,31 +770,27 @@ cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, cons
     cudaError_t e;
     if (cx) {
       e = cudaFuncSetAttribute(chol_smem_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(trsm_rows_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (e == cudaSuccess) e = trsm_set_smem<cplx>((int)shm);
     } else {
       e = cudaFuncSetAttribute(chol_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(trsm_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (e == cudaSuccess) e = trsm_set_smem<double>((int)shm);
     }
     if (e != cudaSuccess) return e;
     configured[cx ? 1 : 0] = shm;
   }
-  // one warp per block and one block per SM (the factor fills shared
-  // memory): rows spread over every SM's fp64 units
+  // one 1024-thread block per SM (the factor fills shared memory), one warp
+  // per row
   long g = (rows + 31) / 32;
   if (g > num_sms) g = num_sms;
   if (g < 1) g = 1;
   if (cx) {
     chol_smem_kernel<cplx><<<1, 256, shm, s>>>(k, rows, shift, scale, (const cplx*)G, (cplx*)L, dsc,
                                                 dead, err);
-    trsm_rows_kernel<cplx><<<(unsigned)g, 32, shm, s>>>(rows, k, (const cplx*)L, dsc,
-                                                          (const cplx*)Z, (cplx*)Q);
+    CTM_TRSM_LAUNCH(cplx);
   } else {
     chol_smem_kernel<double><<<1, 256, shm, s>>>(k, rows, shift, scale, (const double*)G, (double*)L,
                                                   dsc, dead, err);
-    trsm_rows_kernel<double><<<(unsigned)g, 32, shm, s>>>(rows, k, (const double*)L, dsc,
-                                                            (const double*)Z, (double*)Q);
+    CTM_TRSM_LAUNCH(double);
   }
   if (launches) *launches += 2;
   return cudaGetLastError();
