@@ -1,0 +1,229 @@
+// Single-layer absorption of the ket and bra tensors into a corner / edge
+// block (paper Eq. rho_M_diag, Fig. ctmrg-step: A and conj(A) are absorbed
+// one after the other, never as the double-layer A (x) conj(A)):
+//
+//   Out[t,d,D,n,e,E] = sum_{s,u,l,v,w} A[s,u,l,d,e] B[s,v,w,D,E] In[t,l,w,n,u,v]
+//
+// In and Out are [chi, Dk, Db, chi, Dk, Db] row-major. For every (t, n) the
+// work is two small matrix products per physical index s,
+//   Y_s = A_s X       (Dk^2 x Dk^2) (Dk^2 x Db^2),  X[(u,l),(w,v)] = In[t,l,w,n,u,v]
+//   Out += Y_s B_s    (Dk^2 x Db^2) (Db^2 x Db^2),  B_s[(w,v),(D,E)] = B[s,v,w,D,E]
+// so one kernel reads In once and writes Out once (HBM-bound in fp32; the
+// unfused form is two permutes, two GEMMs and a final permute). Each CTA
+// holds A and B in shared memory and runs two groups of 144 threads, one
+// (t, n) pair each; a thread owns a 3 x 3 register tile of the 36 x 36
+// products (Dk, Db <= 6). Arithmetic in F: fp32 (split-precision contexts,
+// ~1e-7 relative like the bf16x3 products) or fp64.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ctm {
+
+namespace {
+
+constexpr int GROUP = 144;      // threads per (t, n) pair: 12 x 12
+constexpr int TILE = 3;         // register tile per thread
+constexpr int MAXD2 = 36;       // Dk^2, Db^2 <= 12 * TILE
+
+__device__ __forceinline__ float cvt(double a, float) { return (float)a; }
+__device__ __forceinline__ float2 cvt(cplx a, float2) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double cvt(double a, double) { return a; }
+__device__ __forceinline__ cplx cvt(cplx a, cplx) { return a; }
+__device__ __forceinline__ double back(float a) { return (double)a; }
+__device__ __forceinline__ cplx back(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ double back(double a) { return a; }
+__device__ __forceinline__ cplx back(cplx a) { return a; }
+
+__device__ __forceinline__ void mac(float& c, float a, float b) { c = fmaf(a, b, c); }
+__device__ __forceinline__ void mac(float2& c, float2 a, float2 b) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(a.y, b.x, c.y);
+}
+__device__ __forceinline__ void mac(double& c, double a, double b) { c = fma(a, b, c); }
+__device__ __forceinline__ void mac(cplx& c, cplx a, cplx b) { fmav(c, a, b); }
+template <typename F> __device__ __forceinline__ F fz();
+template <> __device__ __forceinline__ float fz<float>() { return 0.f; }
+template <> __device__ __forceinline__ float2 fz<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double fz<double>() { return 0.0; }
+template <> __device__ __forceinline__ cplx fz<cplx>() { return make_double2(0.0, 0.0); }
+
+template <typename T, typename F>
+__global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, int Db, int d,
+                                                               const T* __restrict__ In,
+                                                               const T* __restrict__ A,
+                                                               const T* __restrict__ B,
+                                                               T* __restrict__ Out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K1 = Dk * Dk, N1 = Db * Db;          // (u,l) and (w,v); M1 = K1 rows (d,e)
+  F* As = reinterpret_cast<F*>(smem_raw);         // [d][(d,e)][(u,l)]
+  F* Bs = As + (size_t)d * K1 * K1;               // [d][(w,v)][(D,E)]
+  const int grp = threadIdx.x / GROUP, lt = threadIdx.x % GROUP;
+  F* Xs = Bs + (size_t)d * N1 * N1 + (size_t)grp * 2 * K1 * N1;   // [(u,l)][(w,v)]
+  F* Ys = Xs + (size_t)K1 * N1;                                   // [(d,e)][(w,v)], then Out
+  const int ti = lt / 12, tj = lt % 12;
+  for (int i = threadIdx.x; i < d * K1 * K1; i += blockDim.x) {
+    // As[s][(d,e)][(u,l)] = A[s,u,l,d,e]
+    const int s = i / (K1 * K1), rem = i % (K1 * K1);
+    const int r = rem / K1, kk = rem % K1;
+    const int dd = r / Dk, e = r % Dk, u = kk / Dk, l = kk % Dk;
+    As[i] = cvt(A[(((size_t)(s * Dk + u) * Dk + l) * Dk + dd) * Dk + e], F());
+  }
+  for (int i = threadIdx.x; i < d * N1 * N1; i += blockDim.x) {
+    // Bs[s][(w,v)][(D,E)] = B[s,v,w,D,E]
+    const int s = i / (N1 * N1), rem = i % (N1 * N1);
+    const int kk = rem / N1, c = rem % N1;
+    const int w = kk / Db, v = kk % Db, D = c / Db, E = c % Db;
+    Bs[i] = cvt(B[(((size_t)(s * Db + v) * Db + w) * Db + D) * Db + E], F());
+  }
+  const size_t row = (size_t)chi * Dk * Db;       // stride of the (first chi, Dk, Db) index
+  const long npairs = (long)chi * chi;
+  for (long p0 = 2L * blockIdx.x; p0 < npairs; p0 += 2L * gridDim.x) {
+    const long p = p0 + grp;
+    const bool live = p < npairs;
+    const int t = live ? (int)(p / chi) : 0, n = live ? (int)(p % chi) : 0;
+    __syncthreads();   // previous pair's output staging is consumed
+    if (live) {
+      // X[(u,l),(w,v)] = In[t,l,w,n,u,v]: runs of Dk Db contiguous (u, v)
+      for (int i = lt; i < K1 * N1; i += GROUP) {
+        const int lw = i / (Dk * Db), uv = i % (Dk * Db);
+        const int l = lw / Db, w = lw % Db, u = uv / Db, v = uv % Db;
+        Xs[(u * Dk + l) * N1 + w * Db + v] =
+            cvt(In[((size_t)t * Dk + l) * Db * row + (size_t)w * row + (size_t)n * Dk * Db + uv],
+                F());
+      }
+    }
+    F acc[TILE][TILE];
+#pragma unroll
+    for (int a = 0; a < TILE; ++a)
+#pragma unroll
+      for (int b = 0; b < TILE; ++b) acc[a][b] = fz<F>();
+    for (int s = 0; s < d; ++s) {
+      __syncthreads();   // X loaded / previous Y consumed
+      const F* Asb = As + (size_t)s * K1 * K1;
+      if (live) {
+        F y[TILE][TILE];
+#pragma unroll
+        for (int a = 0; a < TILE; ++a)
+#pragma unroll
+          for (int b = 0; b < TILE; ++b) y[a][b] = fz<F>();
+        for (int kk = 0; kk < K1; ++kk) {
+          F xa[TILE], xb[TILE];
+#pragma unroll
+          for (int a = 0; a < TILE; ++a) {
+            const int r = ti * TILE + a;
+            xa[a] = r < K1 ? Asb[r * K1 + kk] : fz<F>();
+          }
+#pragma unroll
+          for (int b = 0; b < TILE; ++b) {
+            const int c = tj * TILE + b;
+            xb[b] = c < N1 ? Xs[kk * N1 + c] : fz<F>();
+          }
+#pragma unroll
+          for (int a = 0; a < TILE; ++a)
+#pragma unroll
+            for (int b = 0; b < TILE; ++b) mac(y[a][b], xa[a], xb[b]);
+        }
+#pragma unroll
+        for (int a = 0; a < TILE; ++a)
+#pragma unroll
+          for (int b = 0; b < TILE; ++b) {
+            const int r = ti * TILE + a, c = tj * TILE + b;
+            if (r < K1 && c < N1) Ys[r * N1 + c] = y[a][b];
+          }
+      }
+      __syncthreads();
+      const F* Bsb = Bs + (size_t)s * N1 * N1;
+      if (live) {
+        for (int kk = 0; kk < N1; ++kk) {
+          F ya[TILE], bb[TILE];
+#pragma unroll
+          for (int a = 0; a < TILE; ++a) {
+            const int r = ti * TILE + a;
+            ya[a] = r < K1 ? Ys[r * N1 + kk] : fz<F>();
+          }
+#pragma unroll
+          for (int b = 0; b < TILE; ++b) {
+            const int c = tj * TILE + b;
+            bb[b] = c < N1 ? Bsb[kk * N1 + c] : fz<F>();
+          }
+#pragma unroll
+          for (int a = 0; a < TILE; ++a)
+#pragma unroll
+            for (int b = 0; b < TILE; ++b) mac(acc[a][b], ya[a], bb[b]);
+        }
+      }
+    }
+    __syncthreads();   // all Y reads done: Ys becomes the output staging
+    if (live) {
+#pragma unroll
+      for (int a = 0; a < TILE; ++a)
+#pragma unroll
+        for (int b = 0; b < TILE; ++b) {
+          const int r = ti * TILE + a, c = tj * TILE + b;
+          if (r < K1 && c < N1) Ys[r * N1 + c] = acc[a][b];
+        }
+    }
+    __syncthreads();
+    if (live) {
+      // Out[t,d,D,n,e,E] = O[(d,e),(D,E)]: runs of Dk Db contiguous (e, E)
+      for (int i = lt; i < K1 * N1; i += GROUP) {
+        const int dD = i / (Dk * Db), eE = i % (Dk * Db);
+        const int dd = dD / Db, D = dD % Db, e = eE / Db, E = eE % Db;
+        Out[((size_t)t * Dk + dd) * Db * row + (size_t)D * row + (size_t)n * Dk * Db + eE] =
+            back(Ys[(dd * Dk + e) * N1 + D * Db + E]);
+      }
+    }
+  }
+}
+
+template <typename T, typename F>
+cudaError_t launch_ab(int chi, int Dk, int Db, int d, const void* In, const void* A,
+                      const void* B, void* Out, int num_sms, cudaStream_t s) {
+  const int K1 = Dk * Dk, N1 = Db * Db;
+  const size_t shm = ((size_t)d * K1 * K1 + (size_t)d * N1 * N1 + 4 * (size_t)K1 * N1) * sizeof(F);
+  static size_t configured = 0;
+  if (shm > configured) {
+    const cudaError_t e = cudaFuncSetAttribute(absorb_ab_kernel<T, F>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)shm);
+    if (e != cudaSuccess) return e;
+    configured = shm;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, absorb_ab_kernel<T, F>,
+                                                                2 * GROUP, shm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long grid = (long)num_sms * per_sm;
+  const long tiles = ((long)chi * chi + 1) / 2;
+  if (grid > tiles) grid = tiles;
+  absorb_ab_kernel<T, F><<<(unsigned)grid, 2 * GROUP, shm, s>>>(
+      chi, Dk, Db, d, static_cast<const T*>(In), static_cast<const T*>(A),
+      static_cast<const T*>(B), static_cast<T*>(Out));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool absorb_ab_supported(int Dk, int Db, int d) {
+  return Dk >= 1 && Db >= 1 && d >= 1 && Dk * Dk <= MAXD2 && Db * Db <= MAXD2 && d <= 4;
+}
+
+cudaError_t absorb_ab(bool cx, bool fp32, int chi, int Dk, int Db, int d, const void* In,
+                      const void* A, const void* B, void* Out, int num_sms, cudaStream_t s,
+                      long* launches) {
+  if (!absorb_ab_supported(Dk, Db, d) || chi < 1) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (cx)
+    e = fp32 ? launch_ab<cplx, float2>(chi, Dk, Db, d, In, A, B, Out, num_sms, s)
+             : launch_ab<cplx, cplx>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  else
+    e = fp32 ? launch_ab<double, float>(chi, Dk, Db, d, In, A, B, Out, num_sms, s)
+             : launch_ab<double, double>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  if (launches) ++*launches;
+  return e;
+}
+
+}  // namespace ctm
