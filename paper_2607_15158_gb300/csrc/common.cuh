@@ -39,6 +39,14 @@ __device__ __forceinline__ void fmav(cplx& c, cplx a, cplx b) {
   c.y = fma(a.x, b.y, c.y);
   c.y = fma(a.y, b.x, c.y);
 }
+// c -= a * b
+__device__ __forceinline__ void fnmav(double& c, double a, double b) { c = fma(-a, b, c); }
+__device__ __forceinline__ void fnmav(cplx& c, cplx a, cplx b) {
+  c.x = fma(-a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(-a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
+}
 // c += conj(a) * b
 __device__ __forceinline__ void fmacv(double& c, double a, double b) { c = fma(a, b, c); }
 __device__ __forceinline__ void fmacv(cplx& c, cplx a, cplx b) {

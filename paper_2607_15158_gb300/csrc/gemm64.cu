@@ -146,6 +146,156 @@ __global__ void splitk_reduce(GemmP p, int batch) {
   }
 }
 
+// ------------------------------------------- tall-skinny C = op(A) B
+// op(A) = A^T or A^H with A (K x M) and B (K x N) tall (K >> M, N): the
+// Gram matrices of the CholeskyQR passes and rho = Z_L^H Z_R. Each CTA
+// takes a contiguous chunk of the K rows (staged through shared memory,
+// TS_ROWS at a time) and a slice of the outputs (TS_OUTS per thread, in
+// registers); per-chunk partials are summed in a second pass in chunk order.
+constexpr int TS_THREADS = 512, TS_OUTS = 12, TS_ROWS = 16, TS_MAXMN = 384;
+
+template <typename T, bool CONJ>
+__global__ void __launch_bounds__(TS_THREADS) gemm_ts_kernel(long K, int M, int N, int lower,
+                                                             const T* __restrict__ A, long lda,
+                                                             const T* __restrict__ B, long ldb,
+                                                             long chunk, long nout,
+                                                             T* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);   // [TS_ROWS][M]
+  T* Bs = As + (size_t)TS_ROWS * M;          // [TS_ROWS][N]
+  const long r0 = blockIdx.x * chunk;
+  const long r1 = min(K, r0 + chunk);
+  const long e0 = (long)blockIdx.y * TS_THREADS * TS_OUTS;
+  int oi[TS_OUTS], oj[TS_OUTS];
+  T acc[TS_OUTS];
+#pragma unroll
+  for (int m = 0; m < TS_OUTS; ++m) {
+    const long e = e0 + threadIdx.x + (long)m * TS_THREADS;
+    oi[m] = -1;
+    oj[m] = 0;
+    acc[m] = zero_of(T());
+    if (e < nout) {
+      if (lower) {
+        int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+        while ((long)i * (i + 1) / 2 > e) --i;
+        while ((long)(i + 1) * (i + 2) / 2 <= e) ++i;
+        oi[m] = i;
+        oj[m] = (int)(e - (long)i * (i + 1) / 2);
+      } else {
+        oi[m] = (int)(e / N);
+        oj[m] = (int)(e % N);
+      }
+    }
+  }
+  for (long rb = r0; rb < r1; rb += TS_ROWS) {
+    const int nr = (int)min((long)TS_ROWS, r1 - rb);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TS_ROWS * M; idx += TS_THREADS) {
+      const int rr = idx / M, i = idx % M;
+      T v = zero_of(T());
+      if (rr < nr) v = A[(rb + rr) * lda + i];
+      As[idx] = CONJ ? conjv(v) : v;
+    }
+    for (int idx = threadIdx.x; idx < TS_ROWS * N; idx += TS_THREADS) {
+      const int rr = idx / N, j = idx % N;
+      Bs[idx] = rr < nr ? B[(rb + rr) * ldb + j] : zero_of(T());
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < TS_ROWS; ++rr) {
+      const T* ar = As + (size_t)rr * M;
+      const T* br = Bs + (size_t)rr * N;
+#pragma unroll
+      for (int m = 0; m < TS_OUTS; ++m)
+        if (oi[m] >= 0) fmav(acc[m], ar[oi[m]], br[oj[m]]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < TS_OUTS; ++m) {
+    const long e = e0 + threadIdx.x + (long)m * TS_THREADS;
+    if (e < nout) part[(size_t)blockIdx.x * nout + e] = acc[m];
+  }
+}
+
+template <typename T>
+__global__ void gemm_ts_reduce(int nchunks, long nout, int N, int lower, const T* part, T* C,
+                               long ldc) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nout;
+       e += (long)gridDim.x * blockDim.x) {
+    T s = zero_of(T());
+    for (int b = 0; b < nchunks; ++b) s = addv(s, part[(size_t)b * nout + e]);
+    long i, j;
+    if (lower) {
+      i = (long)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+      while (i * (i + 1) / 2 > e) --i;
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      j = e - i * (i + 1) / 2;
+    } else {
+      i = e / N;
+      j = e % N;
+    }
+    C[i * ldc + j] = s;
+  }
+}
+
+struct TsPlan {
+  bool use = false;
+  long nout = 0;
+  int gy = 1, gx = 1;
+  long chunk = 0;
+};
+
+TsPlan ts_plan(const GemmDesc& g) {
+  TsPlan t;
+  const bool plain = g.alpha[0] == 1.0 && g.alpha[1] == 0.0 && g.beta[0] == 0.0 &&
+                     g.beta[1] == 0.0;
+  if (!(plain && g.batch == 1 && (g.opA == OP_T || g.opA == OP_C) && g.opB == OP_N &&
+        g.M <= TS_MAXMN && g.N <= TS_MAXMN && g.K >= 4096 && (!g.lower_only || g.M == g.N)))
+    return t;
+  t.use = true;
+  t.nout = g.lower_only ? g.M * (g.M + 1) / 2 : g.M * g.N;
+  t.gy = (int)((t.nout + (long)TS_THREADS * TS_OUTS - 1) / ((long)TS_THREADS * TS_OUTS));
+  t.gx = 152 / t.gy;
+  if (t.gx < 1) t.gx = 1;
+  t.chunk = (g.K + t.gx - 1) / t.gx;
+  t.chunk = (t.chunk + TS_ROWS - 1) / TS_ROWS * TS_ROWS;
+  t.gx = (int)((g.K + t.chunk - 1) / t.chunk);
+  return t;
+}
+
+template <typename T>
+cudaError_t run_ts(const GemmDesc& g, const TsPlan& t, void* work, cudaStream_t s,
+                   long* launches) {
+  const size_t shm = (size_t)TS_ROWS * (g.M + g.N) * sizeof(T);
+  static size_t configured[2] = {0, 0};
+  if (shm > configured[g.opA == OP_C]) {
+    const cudaError_t e =
+        g.opA == OP_C
+            ? cudaFuncSetAttribute(gemm_ts_kernel<T, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)
+            : cudaFuncSetAttribute(gemm_ts_kernel<T, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    configured[g.opA == OP_C] = shm;
+  }
+  dim3 grid((unsigned)t.gx, (unsigned)t.gy);
+  if (g.opA == OP_C)
+    gemm_ts_kernel<T, true><<<grid, TS_THREADS, shm, s>>>(
+        g.K, (int)g.M, (int)g.N, g.lower_only ? 1 : 0, static_cast<const T*>(g.A), g.lda,
+        static_cast<const T*>(g.B), g.ldb, t.chunk, t.nout, static_cast<T*>(work));
+  else
+    gemm_ts_kernel<T, false><<<grid, TS_THREADS, shm, s>>>(
+        g.K, (int)g.M, (int)g.N, g.lower_only ? 1 : 0, static_cast<const T*>(g.A), g.lda,
+        static_cast<const T*>(g.B), g.ldb, t.chunk, t.nout, static_cast<T*>(work));
+  long rg = (t.nout + 255) / 256;
+  if (rg > 152 * 8) rg = 152 * 8;
+  gemm_ts_reduce<T><<<(unsigned)rg, 256, 0, s>>>(t.gx, t.nout, (int)g.N, g.lower_only ? 1 : 0,
+                                                  static_cast<const T*>(work),
+                                                  static_cast<T*>(g.C), g.ldc);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
 int choose_splits(const GemmDesc& g) {
   const long tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * g.batch;
   const long target = 152L * 2;
@@ -236,6 +386,8 @@ __global__ void dot_final(const T* part, int nblk, T* out) {
 }  // namespace
 
 size_t gemm64_work_bytes(const GemmDesc& g) {
+  const TsPlan t = ts_plan(g);
+  if (t.use) return (size_t)t.gx * t.nout * (g.cx ? 16 : 8);
   const int splits = choose_splits(g);
   if (splits == 1) return 0;
   return (size_t)splits * g.batch * g.M * g.N * (g.cx ? 16 : 8);
@@ -244,6 +396,9 @@ size_t gemm64_work_bytes(const GemmDesc& g) {
 cudaError_t gemm64(const GemmDesc& g, void* work, size_t work_bytes,
                    cudaStream_t s, long* launches) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  const TsPlan t = ts_plan(g);
+  if (t.use && work && work_bytes >= gemm64_work_bytes(g))
+    return g.cx ? run_ts<cplx>(g, t, work, s, launches) : run_ts<double>(g, t, work, s, launches);
   GemmP p{};
   p.M = g.M; p.N = g.N; p.K = g.K;
   p.A = g.A; p.lda = g.lda; p.sA = g.strideA;

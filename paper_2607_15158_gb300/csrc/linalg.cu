@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(1024, 1) trsm_warp_kernel(long rows, int k, co
 #pragma unroll
         for (int e2 = e; e2 < R; ++e2) {
           const int i = lane + 32 * e2;
-          if (i > j && i < k) a[e2] = subv(a[e2], mulv(q, Lj[i]));
+          if (i > j && i < k) fnmav(a[e2], q, Lj[i]);
         }
       }
     }
@@ -738,13 +738,14 @@ template <typename T>
 cudaError_t trsm_set_smem(int shm) {
   cudaError_t e = cudaSuccess;
   const void* fns[] = {(const void*)trsm_warp_kernel<T, 2>, (const void*)trsm_warp_kernel<T, 4>,
-                       (const void*)trsm_warp_kernel<T, 6>, (const void*)trsm_warp_kernel<T, 8>};
+                       (const void*)trsm_warp_kernel<T, 5>, (const void*)trsm_warp_kernel<T, 6>,
+                       (const void*)trsm_warp_kernel<T, 8>};
   for (const void* f : fns)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   return e;
 }
 
-// R = columns per lane: the smallest of 2, 4, 6, 8 with 32 R >= k
+// R = columns per lane: the smallest of 2, 4, 5, 6, 8 with 32 R >= k
 #define CTM_TRSM_LAUNCH(T)                                                                     \
   do {                                                                                         \
     if (k <= 64)                                                                               \
@@ -752,6 +753,9 @@ cudaError_t trsm_set_smem(int shm) {
                                                              (const T*)Z, (T*)Q);              \
     else if (k <= 128)                                                                         \
       trsm_warp_kernel<T, 4><<<(unsigned)g, 1024, shm, s>>>(rows, k, (const T*)L, dsc,         \
+                                                             (const T*)Z, (T*)Q);              \
+    else if (k <= 160)                                                                         \
+      trsm_warp_kernel<T, 5><<<(unsigned)g, 1024, shm, s>>>(rows, k, (const T*)L, dsc,         \
                                                              (const T*)Z, (T*)Q);              \
     else if (k <= 192)                                                                         \
       trsm_warp_kernel<T, 6><<<(unsigned)g, 1024, shm, s>>>(rows, k, (const T*)L, dsc,         \
