@@ -264,113 +264,131 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat1
   s2 = __double2bfloat16(r2);
 }
 
-// element (m, kk) of op(A) for a row-major fp64 / complex matrix A
-template <typename T>
-__device__ __forceinline__ T op_elem(const T* A, long lda, int op, long m, long kk) {
-  T v = (op == OP_N || op == OP_R) ? A[m * lda + kk] : A[kk * lda + m];
-  if (op == OP_C || op == OP_R) v = conjv(v);
-  return v;
+__device__ __forceinline__ void emit3(__nv_bfloat16* out, long slice, long o, double x) {
+  __nv_bfloat16 s0, s1, s2;
+  split3(x, s0, s1, s2);
+  out[o] = s0;
+  out[slice + o] = s1;
+  out[2 * slice + o] = s2;
 }
 
+
 // A slices: out[s][m][kr], kr < K: Re op(A)(m, kr); K <= kr < 2K: Im
-// (complex); zero up to Kp. One thread per output element along kr; a 32 x 32
-// shared tile transposes the transposed operands.
+// (complex); zero up to Kp. A 32 x 32 shared tile of op(A) is read along A's
+// contiguous axis (rows for op N / R, columns for op T / C) and each element
+// is read once and written to both halves.
 template <typename T>
 __global__ void prep_a_kernel(const T* A, long lda, int op, int M, int K, int Kp,
                                __nv_bfloat16* out) {
   __shared__ T tile[32][33];
-  const bool cx = sizeof(T) == 16;
+  constexpr bool cx = sizeof(T) == 16;
   const int Kr = cx ? 2 * K : K;
   const long slice = (long)M * Kp;
-  const int tiles_k = (Kp + 31) / 32, tiles_m = (M + 31) / 32;
+  const int tiles_k = (K + 31) / 32, tiles_m = (M + 31) / 32;
   const bool trans = (op == OP_T || op == OP_C);
+  const bool cj = (op == OP_C || op == OP_R);
   for (int t = blockIdx.x; t < tiles_k * tiles_m; t += gridDim.x) {
-    const int tk = t % tiles_k, tm = t / tiles_k;
-    const int m0 = tm * 32, kr0 = tk * 32;
-    if (trans) {
-      // stage op(A)(m0.., kk..) for the kk range this tile needs (per part)
-      // rows of A are kk, contiguous along m
-      for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int kr = kr0 + yy;
-        const int kk = (cx && kr >= K) ? kr - K : kr;
-        const int m = m0 + threadIdx.x;
-        T v = zero_of(T());
-        if (kr < Kr && m < M) v = op_elem(A, lda, op, m, kk);
-        tile[yy][threadIdx.x] = v;
-      }
-      __syncthreads();
-      for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int m = m0 + yy, kr = kr0 + threadIdx.x;
-        if (m >= M) continue;
-        double x = 0.0;
-        if (kr < Kr) {
-          const T v = tile[threadIdx.x][yy];
-          if constexpr (sizeof(T) == 16) x = (kr < K) ? v.x : v.y;
-          else x = v;
-        }
-        __nv_bfloat16 s0, s1, s2;
-        split3(x, s0, s1, s2);
-        const long o = (long)m * Kp + kr;
-        out[o] = s0;
-        out[slice + o] = s1;
-        out[2 * slice + o] = s2;
-      }
-      __syncthreads();
-    } else {
-      for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int m = m0 + yy, kr = kr0 + threadIdx.x;
-        if (m >= M) continue;
-        double x = 0.0;
-        if (kr < Kr) {
-          const int kk = (cx && kr >= K) ? kr - K : kr;
-          const T v = op_elem(A, lda, op, m, kk);
-          if constexpr (sizeof(T) == 16) x = (kr < K) ? v.x : v.y;
-          else x = v;
-        }
-        __nv_bfloat16 s0, s1, s2;
-        split3(x, s0, s1, s2);
-        const long o = (long)m * Kp + kr;
-        out[o] = s0;
-        out[slice + o] = s1;
-        out[2 * slice + o] = s2;
+    const int k0 = (t % tiles_k) * 32, m0 = (t / tiles_k) * 32;
+    // tile[m - m0][kk - k0] = op(A)(m, kk) before conjugation
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      if (!trans) {
+        const int m = m0 + yy, kk = k0 + threadIdx.x;
+        tile[yy][threadIdx.x] = (m < M && kk < K) ? A[(long)m * lda + kk] : zero_of(T());
+      } else {
+        const int kk = k0 + yy, m = m0 + threadIdx.x;
+        tile[threadIdx.x][yy] = (m < M && kk < K) ? A[(long)kk * lda + m] : zero_of(T());
       }
     }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      const int m = m0 + yy, kk = k0 + threadIdx.x;
+      if (m < M && kk < K) {
+        const T v = tile[yy][threadIdx.x];
+        if constexpr (cx) {
+          emit3(out, slice, (long)m * Kp + kk, v.x);
+          emit3(out, slice, (long)m * Kp + K + kk, cj ? -v.y : v.y);
+        } else {
+          emit3(out, slice, (long)m * Kp + kk, v);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // padding columns kr >= Kr
+  const __nv_bfloat16 z = __float2bfloat16(0.0f);
+  const int pc = Kp - Kr;
+  const long tid = (long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x * blockDim.y;
+  for (long idx = tid; idx < (long)M * pc; idx += nth) {
+    const long o = (idx / pc) * Kp + Kr + idx % pc;
+    out[o] = z;
+    out[slice + o] = z;
+    out[2 * slice + o] = z;
   }
 }
 
 // B slices (K-major rows = output real columns): out[s][j][kr] = B_emb[kr][j]
-// with B_emb = [[B_r, B_i], [-B_i, B_r]] for complex, B for real.
+// with B_emb = [[B_r, B_i], [-B_i, B_r]] for complex, B for real. A 32 x 32
+// shared tile of op(B) is read along B's contiguous axis and written along
+// kr; the padding rows and columns are zeroed.
 template <typename T>
 __global__ void prep_b_kernel(const T* B, long ldb, int op, int K, int N, int Kp, int Np,
                               __nv_bfloat16* out) {
-  const bool cx = sizeof(T) == 16;
+  __shared__ T tile[32][33];
+  constexpr bool cx = sizeof(T) == 16;
   const int Kr = cx ? 2 * K : K;
   const int Nr = cx ? 2 * N : N;
   const long slice = (long)Np * Kp;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)Np * Kp;
-       idx += (long)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / Kp), kr = (int)(idx % Kp);
-    double x = 0.0;
-    if (j < Nr && kr < Kr) {
-      const int part_k = (cx && kr >= K) ? 1 : 0, kk = part_k ? kr - K : kr;
-      const int part_n = (cx && j >= N) ? 1 : 0, jj = part_n ? j - N : j;
-      // op(B)(kk, jj)
-      const T v = (op == OP_N || op == OP_R) ? B[(long)kk * ldb + jj] : B[(long)jj * ldb + kk];
-      if constexpr (sizeof(T) == 16) {
-        const bool cj = (op == OP_C || op == OP_R);
-        const double re = v.x, im = cj ? -v.y : v.y;
-        // [[re, im], [-im, re]]
-        if (part_k == 0) x = part_n == 0 ? re : im;
-        else x = part_n == 0 ? -im : re;
+  const int tk = (K + 31) / 32, tn = (N + 31) / 32;
+  const bool trans = (op == OP_T || op == OP_C);
+  const bool cj = (op == OP_C || op == OP_R);
+  for (int t = blockIdx.x; t < tk * tn; t += gridDim.x) {
+    const int k0 = (t % tk) * 32, n0 = (t / tk) * 32;
+    // tile[kk - k0][jj - n0] = op(B)(kk, jj) before conjugation
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      if (!trans) {
+        const int kk = k0 + yy, jj = n0 + threadIdx.x;
+        tile[yy][threadIdx.x] = (kk < K && jj < N) ? B[(long)kk * ldb + jj] : zero_of(T());
       } else {
-        x = v;
+        const int jj = n0 + yy, kk = k0 + threadIdx.x;
+        tile[threadIdx.x][yy] = (kk < K && jj < N) ? B[(long)jj * ldb + kk] : zero_of(T());
       }
     }
-    __nv_bfloat16 s0, s1, s2;
-    split3(x, s0, s1, s2);
-    out[idx] = s0;
-    out[slice + idx] = s1;
-    out[2 * slice + idx] = s2;
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      const int jj = n0 + yy, kk = k0 + threadIdx.x;
+      if (jj < N && kk < K) {
+        const T v = tile[threadIdx.x][yy];
+        if constexpr (cx) {
+          const double re = v.x, im = cj ? -v.y : v.y;
+          emit3(out, slice, (long)jj * Kp + kk, re);
+          emit3(out, slice, (long)jj * Kp + K + kk, -im);
+          emit3(out, slice, (long)(N + jj) * Kp + kk, im);
+          emit3(out, slice, (long)(N + jj) * Kp + K + kk, re);
+        } else {
+          emit3(out, slice, (long)jj * Kp + kk, v);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const __nv_bfloat16 z = __float2bfloat16(0.0f);
+  const long tid = (long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x * blockDim.y;
+  // padding rows j >= Nr
+  for (long idx = tid; idx < (long)(Np - Nr) * Kp; idx += nth) {
+    const long o = (long)Nr * Kp + idx;
+    out[o] = z;
+    out[slice + o] = z;
+    out[2 * slice + o] = z;
+  }
+  // padding columns kr >= Kr of the rows j < Nr
+  const int pc = Kp - Kr;
+  for (long idx = tid; idx < (long)Nr * pc; idx += nth) {
+    const long o = (idx / pc) * Kp + Kr + idx % pc;
+    out[o] = z;
+    out[slice + o] = z;
+    out[2 * slice + o] = z;
   }
 }
 
@@ -570,8 +588,8 @@ ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* B
 
 ctm_status prep_a(SplitCtx* sc, const void* A, long lda, int op, int M, int K, int Kp,
                   __nv_bfloat16* out, cudaStream_t s, long* launches) {
-  const long tiles = (long)((Kp + 31) / 32) * ((M + 31) / 32);
-  const unsigned g = (unsigned)std::min<long>(tiles, 152L * 16);
+  const long tiles = (long)((K + 31) / 32) * ((M + 31) / 32);
+  const unsigned g = (unsigned)std::max<long>(1, std::min<long>(tiles, 152L * 16));
   if (sc->cx) prep_a_kernel<cplx><<<g, dim3(32, 8), 0, s>>>((const cplx*)A, lda, op, M, K, Kp, out);
   else prep_a_kernel<double><<<g, dim3(32, 8), 0, s>>>((const double*)A, lda, op, M, K, Kp, out);
   if (launches) ++*launches;
@@ -580,9 +598,15 @@ ctm_status prep_a(SplitCtx* sc, const void* A, long lda, int op, int M, int K, i
 
 ctm_status prep_b(SplitCtx* sc, const void* B, long ldb, int op, int K, int N, int Kp, int Np,
                   __nv_bfloat16* out, cudaStream_t s, long* launches) {
-  const unsigned g = grid_cap((long)Np * Kp);
-  if (sc->cx) prep_b_kernel<cplx><<<g, 256, 0, s>>>((const cplx*)B, ldb, op, K, N, Kp, Np, out);
-  else prep_b_kernel<double><<<g, 256, 0, s>>>((const double*)B, ldb, op, K, N, Kp, Np, out);
+  long tiles = (long)((K + 31) / 32) * ((N + 31) / 32);
+  if (tiles > 152L * 8) tiles = 152L * 8;
+  if (tiles < 1) tiles = 1;
+  const dim3 blk(32, 8);
+  if (sc->cx)
+    prep_b_kernel<cplx><<<(unsigned)tiles, blk, 0, s>>>((const cplx*)B, ldb, op, K, N, Kp, Np, out);
+  else
+    prep_b_kernel<double><<<(unsigned)tiles, blk, 0, s>>>((const double*)B, ldb, op, K, N, Kp, Np,
+                                                          out);
   if (launches) ++*launches;
   return cudaGetLastError() == cudaSuccess ? CTM_OK : sfail(sc, CTM_ECUDA, "slice launch failed");
 }
