@@ -3,7 +3,8 @@
 // C = op(A) op(B) for fp64 (or complex fp64) operands, computed as sums of
 // bf16 x bf16 products with fp32 accumulation:
 //   * every fp64 value x is split into three bf16 slices x = s0 + s1 + s2 + e
-//     (each slice the bf16 rounding of the remainder; |e| <~ 2^-24 |x|);
+//     (the slices of x rounded to fp32, each the bf16 rounding of the
+//     remainder; |e| <= 2^-24 |x|);
 //   * a product keeps the six slice products of order >= 2^-16
 //     (s0 t0, s0 t1, s1 t0, s0 t2, s1 t1, s2 t0), all accumulated into one
 //     fp32 accumulator in tensor memory;
@@ -255,13 +256,18 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ------------------------------------------------------------ slicing
+// x -> three bf16 slices of its fp32 rounding xf: s0 + s1 + s2 = xf exactly
+// (each remainder has at most 16, then 8 significant bits, so the fp32
+// subtractions are exact); |x - xf| <= 2^-24 |x|. One fp64 operation per
+// value: GB300's fp64 pipe is ~60x narrower than its fp32 pipe.
 __device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat16& s1,
                                        __nv_bfloat16& s2) {
-  s0 = __double2bfloat16(x);
-  const double r1 = x - (double)__bfloat162float(s0);
-  s1 = __double2bfloat16(r1);
-  const double r2 = r1 - (double)__bfloat162float(s1);
-  s2 = __double2bfloat16(r2);
+  const float xf = __double2float_rn(x);
+  s0 = __float2bfloat16_rn(xf);
+  const float r1 = xf - __bfloat162float(s0);
+  s1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(s1);
+  s2 = __float2bfloat16_rn(r2);
 }
 
 __device__ __forceinline__ void emit3(__nv_bfloat16* out, long slice, long o, double x) {
