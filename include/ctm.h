@@ -68,8 +68,11 @@ typedef enum { CTM_PREC_FP64 = 0, CTM_PREC_SPLIT_BF16 = 1 } ctm_prec;
 
 typedef enum { CTM_LEFT = 0, CTM_UP = 1, CTM_RIGHT = 2, CTM_DOWN = 3 } ctm_dir;
 
-/* Projector construction: subspace iteration (QR-based projector) or the
- * standard truncated SVD of M (comparison baseline). */
+/* Projector construction: subspace iteration (QR-based projector, paper
+ * Eqs. xy_iter to xy_recycle) or the standard truncated SVD of the explicit
+ * M = H_L H_R (Eq. svd_projectors_diag; comparison baseline). The standard
+ * method's dense N x N SVD is cuSOLVER's gesvd, opened on first use:
+ * ctm_init returns CTM_EUNSUPPORTED when libcusolver cannot be loaded. */
 typedef enum { CTM_PROJ_SI = 0, CTM_PROJ_SVD = 1 } ctm_method;
 
 typedef struct {
@@ -196,7 +199,17 @@ ctm_status ctm_profile_read(ctm_ctx* ctx, double* ms, long* launches, double* fl
 #define CTM_NPHASES 8
 ctm_status ctm_profile_phases(ctm_ctx* ctx, double ms[CTM_NPHASES]);
 
-void ctm_free(ctm_ctx* ctx);
+/* Checkpoint and resume (host buffers). ctm_save with buf = NULL stores the
+ * needed size in *nbytes; otherwise it writes the iteration state (C, T, the
+ * rangefinders X, W of every direction and cut, the last corner spectra and
+ * the move counters) into buf, *nbytes being its capacity on entry and the
+ * bytes written on return (CTM_EINVAL if too small). ctm_load restores such a
+ * state into a context of the same dimensions (CTM_EINVAL otherwise); the
+ * iteration then continues exactly as in the saved context. */
+ctm_status ctm_save(const ctm_ctx* ctx, void* buf, size_t* nbytes);
+ctm_status ctm_load(ctm_ctx* ctx, const void* buf, size_t nbytes);
+
+void ctm_free(ctm_ctx* ctx);void ctm_free(ctm_ctx* ctx);
 
 /* Message of the last failed call on ctx (or of the last failed creation when
  * ctx is NULL); owned by the library, valid until the next call. */

@@ -75,6 +75,8 @@ def load():
         "ctm_profile_enable": (I, [ctx_p, I]),
         "ctm_profile_read": (I, [ctx_p, P(D), P(C.c_long), P(D), P(D)]),
         "ctm_profile_phases": (I, [ctx_p, P(D)]),
+        "ctm_save": (I, [ctx_p, VP, P(C.c_size_t)]),
+        "ctm_load": (I, [ctx_p, VP, C.c_size_t]),
         "ctm_free": (None, [ctx_p]),
         "ctm_last_error": (C.c_char_p, [ctx_p]),
         "ctm_svdvals_noalloc": (I, [VP, I, I, VP, VP]),
@@ -238,6 +240,18 @@ class Context:
         ms = (C.c_double * len(self.PHASES))()
         _check(self.lib, self.ptr, self.lib.ctm_profile_phases(self.ptr, ms))
         return dict(zip(self.PHASES, list(ms)))
+
+    def ctm_save(self):
+        """Checkpoint of the iteration state as a bytes object."""
+        n = C.c_size_t(0)
+        _check(self.lib, self.ptr, self.lib.ctm_save(self.ptr, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(self.lib, self.ptr, self.lib.ctm_save(self.ptr, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def ctm_load(self, state):
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(self.lib, self.ptr, self.lib.ctm_load(self.ptr, buf, len(state)))
 
     def ctm_last_timing(self):
         ms, n = C.c_double(), C.c_long()

@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "libctm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ctm.cu", "permute.cu", "gemm64.cu", "linalg.cu", "jacobi.cu", "split_gemm.cu",
            "noalloc.cu", "cholqr_mixed.cu",
-           "absorb.cu"]
+           "absorb.cu", "svd_proj.cu"]
 
 
 def nvcc():
@@ -47,7 +47,7 @@ def build(verbose=False, extra=()):
     os.makedirs(LIBDIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
-    cmd = [nvcc(), "-shared", *ARCH, "-cudart", "static", "-o", LIB, *objs]
+    cmd = [nvcc(), "-shared", *ARCH, "-cudart", "static", "-o", LIB, *objs, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

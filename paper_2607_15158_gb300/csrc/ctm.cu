@@ -23,6 +23,7 @@
 #include "ctm.h"
 #include "kernels.h"
 #include "split_gemm.h"
+#include "svd_proj.h"
 
 using namespace ctm;
 
@@ -117,6 +118,11 @@ struct ctm_ctx {
   bool spectra_init = false;
   // split-precision state
   SplitCtx* split = nullptr;
+  // standard truncated-SVD projectors (CTM_PROJ_SVD)
+  SvdCtx* svd = nullptr;
+  void* svdM = nullptr;      // N x N
+  void* svdUs = nullptr;     // N x chi
+  void* svdVs = nullptr;
   // phase timing (profiling)
   bool prof = false;
   std::vector<cudaEvent_t> pev;
@@ -731,6 +737,38 @@ ctm_status absorb_site(ctm_ctx* c, int r, int x, int y, int Lyf) {
   return CTM_OK;
 }
 
+// C = op(A) op(B) for the large products of the standard-SVD path: the
+// tensor cores in split contexts, fp64 otherwise
+ctm_status mm_big(ctm_ctx* c, int opA, int opB, long M, long Nn, long K, const void* A, long lda,
+                  const void* B, long ldb, void* Cm, long ldc) {
+  if (c->split) {
+    const ctm_status st = split_gemm(c->split, opA, A, lda, opB, B, ldb, (int)M, (int)Nn, (int)K,
+                                     Cm, ldc, c->stream, &c->launches);
+    return st == CTM_OK ? CTM_OK : fail(c, st, split_last_error(c->split));
+  }
+  return mm_small(c, opA, opB, M, Nn, K, A, lda, B, ldb, Cm, ldc);
+}
+
+// Standard CTMRG projectors of one cut (Eq. svd_projectors_diag): H_R = Q1 Q2,
+// H_L = Q3 Q4, M = H_L H_R = U S V^H truncated to chi (sign fix on U),
+// P_l = H_R V s^-1/2, P_r^H = H_L^H U s^-1/2.
+ctm_status svd_projectors(ctm_ctx* c, void* Pl, void* PrH) {
+  const long N = c->N, chi = c->chi;
+  void* HR = c->pipe[0];
+  void* HL = c->pipe[1];
+  PhaseScope ps(c, PH_SMALL);
+  CK(mm_big(c, OP_N, OP_N, N, N, N, c->Q[0], N, c->Q[1], N, HR, N));
+  CK(mm_big(c, OP_N, OP_N, N, N, N, c->Q[2], N, c->Q[3], N, HL, N));
+  CK(mm_big(c, OP_N, OP_N, N, N, N, HL, N, HR, N, c->svdM, N));
+  const ctm_status st = svd_truncated(c->svd, c->svdM, (int)chi, c->opts.svd_rel_cutoff,
+                                      c->opts.sign_fix != 0, c->svdUs, c->svdVs, c->err,
+                                      c->stream, &c->launches);
+  if (st != CTM_OK) return fail(c, st, svd_last_error(c->svd));
+  CK(mm_big(c, OP_N, OP_N, N, chi, N, HR, N, c->svdVs, chi, Pl, chi));
+  CK(mm_big(c, c->cx ? OP_C : OP_T, OP_N, N, chi, N, HL, N, c->svdUs, chi, PrH, chi));
+  return CTM_OK;
+}
+
 ctm_status check_err(ctm_ctx* c) {
   int h = 0;
   CTM_CUDA_OK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -748,10 +786,23 @@ ctm_status check_err(ctm_ctx* c) {
 ctm_status move_impl(ctm_ctx* c, int r) {
   const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
   const size_t NC = (size_t)c->N * c->chi;
-  if (c->opts.method != CTM_PROJ_SI)
-    return fail(c, CTM_EUNSUPPORTED, "standard-SVD projectors are not built on the device");
+  const bool svd = c->opts.method == CTM_PROJ_SVD;
   for (int x = 0; x < Lxf; ++x) {
-    for (int y = 0; y < Lyf; ++y) {
+    if (svd) {
+      for (int y = 0; y < Lyf; ++y) {
+        {
+          PhaseScope ps(c, PH_CORNER);
+          for (int i = 0; i < 4; ++i) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
+        }
+        const int cut = y * Lxf + x;
+        CK(svd_projectors(c, at(c->Pl, y * NC, c), at(c->PrH, y * NC, c)));
+        CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPl, cut * NC, c), at(c->Pl, y * NC, c),
+                                    NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
+        CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPrH, cut * NC, c), at(c->PrH, y * NC, c),
+                                    NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
+      }
+    }
+    for (int y = 0; y < (svd ? 0 : Lyf); ++y) {
       {
         PhaseScope ps(c, PH_CORNER);
         for (int i = 0; i < 4; ++i) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
@@ -765,8 +816,8 @@ ctm_status move_impl(ctm_ctx* c, int r) {
     }
     // the cuts of a column are independent until the absorption: their
     // small SVDs share one launch
-    CK(si_small_svd(c, Lyf));
-    for (int y = 0; y < Lyf; ++y) {
+    if (!svd) CK(si_small_svd(c, Lyf));
+    for (int y = 0; y < (svd ? 0 : Lyf); ++y) {
       const int cut = y * Lxf + x;
       CK(si_finish(c, r, cut, y, at(c->Pl, y * NC, c), at(c->PrH, y * NC, c)));
       CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPl, cut * NC, c), at(c->Pl, y * NC, c), NC * c->es,
@@ -1014,6 +1065,16 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       return bail(st);
     }
   }
+  if (c->opts.method == CTM_PROJ_SVD) {
+    st = svd_create(&c->svd, cx, (int)N, chi);
+    if (st != CTM_OK) {
+      c->msg = std::string("dense SVD setup failed: ") + svd_last_error(c->svd);
+      return bail(st);
+    }
+    if ((st = dalloc(c, &c->svdM, N * N * es)) != CTM_OK) return bail(st);
+    if ((st = dalloc(c, &c->svdUs, N * chi * es)) != CTM_OK) return bail(st);
+    if ((st = dalloc(c, &c->svdVs, N * chi * es)) != CTM_OK) return bail(st);
+  }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess)
     return bail(fail(c, CTM_ECUDA, "initialisation failed on the device"));
   *out = c;
@@ -1205,6 +1266,98 @@ ctm_status ctm_set_rangefinders(ctm_ctx* c, const void* X, const void* W) {
   CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
   for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
+  return CTM_OK;
+}
+
+// ---------------------------------------------------- checkpoint / resume
+namespace {
+
+struct SaveHeader {
+  char magic[8];             // "CTMSAVE1"
+  int32_t Lx, Ly, d, Dk, Db, chi, N, k, cx, last_dir;
+  int32_t moves_done[4];
+  int32_t spectra_init;
+  uint64_t qr_calls;
+};
+
+size_t save_bytes(const ctm_ctx* c) {
+  const size_t env = (size_t)4 * c->S * (elems_C(c) + elems_T(c)) * c->es;
+  const size_t rf = (size_t)2 * 4 * c->S * c->N * c->k * c->es;
+  return sizeof(SaveHeader) + env + rf + (size_t)4 * c->S + (size_t)4 * c->S * c->chi * sizeof(double);
+}
+
+}  // namespace
+
+ctm_status ctm_save(const ctm_ctx* cc, void* buf, size_t* nbytes) {
+  ctm_ctx* c = const_cast<ctm_ctx*>(cc);
+  if (!c || !nbytes) return fail(c, CTM_EINVAL, "NULL argument");
+  const size_t need = save_bytes(c);
+  if (!buf) {
+    *nbytes = need;
+    return CTM_OK;
+  }
+  if (*nbytes < need) return fail(c, CTM_EINVAL, "checkpoint buffer too small");
+  Guard gd(c);
+  SaveHeader h{};
+  memcpy(h.magic, "CTMSAVE1", 8);
+  h.Lx = c->Lx; h.Ly = c->Ly; h.d = c->d; h.Dk = c->Dk; h.Db = c->Db; h.chi = c->chi;
+  h.N = c->N; h.k = c->k; h.cx = c->cx ? 1 : 0; h.last_dir = c->last_dir;
+  for (int r = 0; r < 4; ++r) h.moves_done[r] = c->moves_done[r];
+  h.spectra_init = c->spectra_init ? 1 : 0;
+  h.qr_calls = c->qr_calls;
+  char* p = static_cast<char*>(buf);
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  const size_t nC = (size_t)4 * c->S * elems_C(c) * c->es, nT = (size_t)4 * c->S * elems_T(c) * c->es;
+  const size_t nX = (size_t)4 * c->S * c->N * c->k * c->es;
+  const size_t nS = (size_t)4 * c->S * c->chi * sizeof(double);
+  CTM_CUDA_OK(cudaMemcpyAsync(p, c->C, nC, cudaMemcpyDeviceToHost, c->stream));
+  p += nC;
+  CTM_CUDA_OK(cudaMemcpyAsync(p, c->T, nT, cudaMemcpyDeviceToHost, c->stream));
+  p += nT;
+  CTM_CUDA_OK(cudaMemcpyAsync(p, c->X, nX, cudaMemcpyDeviceToHost, c->stream));
+  p += nX;
+  CTM_CUDA_OK(cudaMemcpyAsync(p, c->W, nX, cudaMemcpyDeviceToHost, c->stream));
+  p += nX;
+  CTM_CUDA_OK(cudaMemcpyAsync(p, c->spec_old, nS, cudaMemcpyDeviceToHost, c->stream));
+  p += nS;
+  memcpy(p, c->rf_ready.data(), (size_t)4 * c->S);
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  *nbytes = need;
+  return CTM_OK;
+}
+
+ctm_status ctm_load(ctm_ctx* c, const void* buf, size_t nbytes) {
+  if (!c || !buf) return fail(c, CTM_EINVAL, "NULL argument");
+  if (nbytes < sizeof(SaveHeader) || nbytes < save_bytes(c))
+    return fail(c, CTM_EINVAL, "checkpoint too short for this context");
+  SaveHeader h;
+  memcpy(&h, buf, sizeof h);
+  if (memcmp(h.magic, "CTMSAVE1", 8) != 0) return fail(c, CTM_EINVAL, "not a checkpoint");
+  if (h.Lx != c->Lx || h.Ly != c->Ly || h.d != c->d || h.Dk != c->Dk || h.Db != c->Db ||
+      h.chi != c->chi || h.N != c->N || h.k != c->k || h.cx != (c->cx ? 1 : 0))
+    return fail(c, CTM_EINVAL, "checkpoint dimensions differ from the context");
+  Guard gd(c);
+  const char* p = static_cast<const char*>(buf) + sizeof h;
+  const size_t nC = (size_t)4 * c->S * elems_C(c) * c->es, nT = (size_t)4 * c->S * elems_T(c) * c->es;
+  const size_t nX = (size_t)4 * c->S * c->N * c->k * c->es;
+  const size_t nS = (size_t)4 * c->S * c->chi * sizeof(double);
+  CTM_CUDA_OK(cudaMemcpyAsync(c->C, p, nC, cudaMemcpyHostToDevice, c->stream));
+  p += nC;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->T, p, nT, cudaMemcpyHostToDevice, c->stream));
+  p += nT;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->X, p, nX, cudaMemcpyHostToDevice, c->stream));
+  p += nX;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->W, p, nX, cudaMemcpyHostToDevice, c->stream));
+  p += nX;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->spec_old, p, nS, cudaMemcpyHostToDevice, c->stream));
+  p += nS;
+  memcpy(c->rf_ready.data(), p, (size_t)4 * c->S);
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  for (int r = 0; r < 4; ++r) c->moves_done[r] = h.moves_done[r];
+  c->last_dir = h.last_dir;
+  c->spectra_init = h.spectra_init != 0;
+  c->qr_calls = h.qr_calls;
   return CTM_OK;
 }
 
@@ -1466,6 +1619,7 @@ void ctm_free(ctm_ctx* c) {
   for (auto& e : c->pev) cudaEventDestroy(e);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->split) split_destroy(c->split);
+  if (c->svd) svd_destroy(c->svd);
   for (void* p : c->allocs) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
