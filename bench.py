@@ -32,7 +32,8 @@ if ROOT not in sys.path:
 
 WORKLOAD = "cfg3_3x3_D6_chi144_c128"
 WARM_ITERS, WARM_ROUNDS = 2, 4
-METRIC = "CTMRG moves/s (3x3 cell, complex D=6, chi=144, split BF16x3 tensor-core products)"
+TRAFFIC_PER_OPERAND_BYTE = 1.00   # profiles/split_mma_small_counters.md
+METRIC = "CTMRG moves/s & tensor TFLOP/s at D=6, chi=144"
 UNIT = "moves/s"
 
 
@@ -43,8 +44,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["split", "fp64"], default="split")
+    ap.add_argument("--method", choices=["si", "svd"], default="si",
+                    help="projectors: subspace iteration or the standard truncated SVD")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mode: Poisson stream of mixed solves, p50/p99 latency")
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--rate", type=float, default=4.0, help="arrivals per second (serve)")
+    ap.add_argument("--concurrency", type=int, default=8, help="solves in flight (serve)")
     return ap.parse_args()
 
 
@@ -219,8 +227,10 @@ def run_ours(args, rank, world, local_rank):
     # WARM_ROUNDS subspace-iteration rounds and the fp64 QR schedule) runs in
     # the untimed warm-up steps; timed steps are steady-state SI moves with
     # one round per move
+    method = pkg.CTM_PROJ_SVD if args.method == "svd" else pkg.CTM_PROJ_SI
     opts = pkg.ctm_default_opts(p=p, si_rounds=w["si_rounds"], warmup_iters=WARM_ITERS,
-                                warmup_rounds=WARM_ROUNDS, prec=prec, stream=stream.cuda_stream)
+                                warmup_rounds=WARM_ROUNDS, prec=prec, method=method,
+                                stream=stream.cuda_stream)
     ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx, opts=opts)
     ctx.ctm_set_env(Cs, Ts)
     ctx.ctm_set_rangefinders(X0, W0)
@@ -298,9 +308,15 @@ def run_ours(args, rank, world, local_rank):
         mma_ms, mma_n, mma_flops, mma_bytes = prof
         achieved = mma_flops / (mma_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        # DRAM bytes per launch: the full-counter capture of this kernel on the
+        # small workload measured dram read + write = 1.00 x the operand bytes
+        # of the launch; scaled here to the operand bytes of these launches
+        traffic = TRAFFIC_PER_OPERAND_BYTE * mma_bytes / mma_n
         roofline = {"bound": "tensor", "kernel": "split_mma_kernel (tcgen05 bf16, fp32 accum)",
                     "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "frac": round(achieved / peak, 4), "traffic": round(traffic),
+                    "traffic_source": "ncu dram bytes / operand bytes = 1.00 on "
+                                      "small_1x1_D4_chi100_c128, x operand bytes per launch",
                     "peak_source": f"{src} bf16 sustained",
                     "launches": mma_n, "kernel_ms": round(mma_ms, 3),
                     "kernel_share_of_step": round(mma_ms / ms, 4)}
@@ -309,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
         per_move, dt, sample = oracle_sample_seconds(w)
         cpu = {"value": 1.0 / per_move, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": sample, "seconds_measured": round(dt, 2)}
-    algo_flops_move = move_flops(w)
+    algo_flops_move = move_flops(w, args.method)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -319,6 +335,8 @@ def run_ours(args, rank, world, local_rank):
                    "p": p, "N": N, "k": k, "si_rounds": w["si_rounds"],
                    "precision": "split-bf16x3 (6 slice products), fp32 accum, fp64 QR/SVD"
                    if args.prec == "split" else "fp64",
+                   "projectors": "subspace iteration" if args.method == "si"
+                   else "standard truncated SVD (dense gesvd)",
                    "step": "1 iteration = 4 moves + corner-spectrum scalar",
                    "l2": "working set >> L2 (no flush)", "replicas": world},
         "algorithmic_tflops": round(algo_flops_move * value / 1e12, 3),
@@ -335,24 +353,91 @@ def run_ours(args, rank, world, local_rank):
     ctx.ctm_free()
 
 
-def move_flops(w):
+def move_flops(w, method="si"):
     """Algorithmic real flops of one move (complex MAC = 8 real flops): per
-    cut 4 enlarged corners (chi^3 D^2 + chi^3 D^4 + 2 chi^2 d D^6 MAC each),
-    SI round(s) (16 N^2 k), Z_R and Z_L (4 N^2 k), rho (N k^2), the
-    absorption (chi^3 D^2 + 2 chi^3 D^4 + 2 chi^2 d D^6)."""
+    cut 4 enlarged corners (chi^3 D^2 + chi^3 D^4 + 2 chi^2 d D^6 MAC each)
+    and the absorption (chi^3 D^2 + 2 chi^3 D^4 + 2 chi^2 d D^6); SI adds the
+    round(s) (16 N^2 k), Z_R and Z_L (4 N^2 k) and rho (N k^2); the standard
+    method adds M = H_L H_R (3 N^3), the projectors (2 N^2 chi) and the dense
+    SVD (~21 N^3 real flops, x4 complex)."""
     chi, D, d, p = w["chi"], w["D"], w["d"], w["p"]
     N = chi * D * D
     k = min(chi + p, N)
     r = w["si_rounds"]
-    mac = 4 * (chi ** 3 * D ** 2 + chi ** 3 * D ** 4 + 2 * chi ** 2 * d * D ** 6)
-    mac += (16 * r + 4) * N * N * k + N * k * k
-    mac += chi ** 3 * D ** 2 + 2 * chi ** 3 * D ** 4 + 2 * chi ** 2 * d * D ** 6
     per_mac = 8 if w["complex_"] else 2
-    return per_mac * mac * w["Lx"] * w["Ly"]
+    mac = 4 * (chi ** 3 * D ** 2 + chi ** 3 * D ** 4 + 2 * chi ** 2 * d * D ** 6)
+    mac += chi ** 3 * D ** 2 + 2 * chi ** 3 * D ** 4 + 2 * chi ** 2 * d * D ** 6
+    extra = 0.0
+    if method == "svd":
+        mac += 3 * N ** 3 + 2 * N * N * chi
+        extra = 21.0 * N ** 3 * (4 if w["complex_"] else 1)
+    else:
+        mac += (16 * r + 4) * N * N * k + N * k * k
+    return (per_mac * mac + extra) * w["Lx"] * w["Ly"]
+
+
+# ------------------------------------------------------------------ serving
+def serve_mix(n, seed=4):
+    """Seeded request stream of the serving workload: cells 1x1 or 2x2, real
+    A[2,D,...] with D in {2, 3, 4}, chi uniform in [D^2, 2 D^2], tol 1e-8
+    (a reduced stand-in for the 1x1..3x3, D = 3..7, chi in [D^2, 4 D^2] mix,
+    whose fp64 solves take minutes each on this GPU)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        L = int(rng.choice([1, 2]))
+        D = int(rng.choice([2, 3, 4]))
+        chi = int(rng.integers(D * D, 2 * D * D + 1))
+        out.append((L, L, D, chi, 1000 + i))
+    return out
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+
+    import ctm_synth as S
+    import paper_2607_15158_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    mix = serve_mix(args.requests)
+    rng = np.random.default_rng(5)
+    gaps = rng.exponential(1.0 / args.rate, size=len(mix))
+    heis = S.heisenberg_bond()
+    tensors = [S.ipeps_tensors(Lx, Ly, 2, D, complex_=False, seed=sd) for (Lx, Ly, D, chi, sd) in mix]
+    srv = pkg.Server(hbm_budget=0, max_concurrent=args.concurrency)
+    t0 = time.perf_counter()
+    tickets = []
+    for (Lx, Ly, D, chi, sd), A, gap in zip(mix, tensors, gaps):
+        time.sleep(gap)
+        tickets.append(srv.ctm_server_submit(A, 2, D, chi, 1e-8, 200, op=heis, cplx=False,
+                                             Lx=Lx, Ly=Ly))
+    res = [srv.ctm_server_result(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.ctm_server_stats()
+    srv.ctm_server_free()
+    line = {
+        "metric": "serve p50/p99 latency", "value": st["p50_ms"], "unit": "ms",
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "solves_per_s": st["solves_per_s"],
+        "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve mix: cells 1x1/2x2, D in {2,3,4}, chi in [D^2, 2D^2], "
+                               "tol 1e-8, Poisson arrivals",
+                   "requests": len(mix), "rate_per_s": args.rate,
+                   "concurrency": args.concurrency},
+        "wall_s": wall,
+        "mean_queue_ms": float(np.mean([r["queue_ms"] for r in res])),
+        "mean_run_ms": float(np.mean([r["run_ms"] for r in res])),
+        "converged": int(sum(r["delta"] < 1e-8 for r in res)),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.serve:
+        run_serve(args)
+        return
     if args.impl == "ours" and args.warmup < WARM_ITERS:
         args.warmup = WARM_ITERS
     world = int(os.environ.get("WORLD_SIZE", "1"))

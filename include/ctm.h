@@ -199,6 +199,60 @@ ctm_status ctm_profile_read(ctm_ctx* ctx, double* ms, long* launches, double* fl
 #define CTM_NPHASES 8
 ctm_status ctm_profile_phases(ctm_ctx* ctx, double ms[CTM_NPHASES]);
 
+/* Device bytes a context of these dimensions and options allocates (an
+ * upper estimate: the context's arrays, split-precision slice caches and
+ * partial sums, dense-SVD buffers, plus 5 % and 64 MB). */
+ctm_status ctm_footprint(int Lx, int Ly, int d, int D, int chi, ctm_dtype dtype,
+                         const ctm_opts* opts, size_t* bytes);
+
+/* ---------------------------------------------------------------- serving
+ * Environment solves of mixed (cell, D, chi) as they arrive (continuous
+ * batching). A scheduler admits pending solves first-fit in arrival order
+ * while the summed ctm_footprint of the running solves stays within the HBM
+ * budget and fewer than max_concurrent run; each admitted solve runs
+ * ctm_init + ctm_converge on its own host thread and CUDA stream, with its
+ * C, T, X, W resident until it finishes, so concurrent solves overlap on the
+ * device. The paper has no serving layer: this serves many independent
+ * contractions (for instance the candidate tensors of an optimisation). */
+typedef struct ctm_server ctm_server;
+
+typedef struct {
+  int Lx, Ly, d, D, chi;
+  ctm_dtype dtype;
+  const void* const* A;   /* Lx*Ly host pointers to A[d][D][D][D][D], copied */
+  const void* op;         /* d^2 x d^2 two-site operator (copied), or NULL */
+  double tol;             /* ctm_converge tolerance */
+  int max_iter;
+  ctm_opts opts;          /* stream is ignored: every solve has its own */
+} ctm_solve_spec;
+
+typedef struct {
+  ctm_status status;      /* of the solve (CTM_OK also when max_iter ran out) */
+  int iters;
+  double delta;           /* last convergence measure */
+  double queue_ms;        /* submit -> admission */
+  double run_ms;          /* admission -> done */
+  size_t footprint;       /* device bytes reserved for the solve */
+} ctm_solve_result;
+
+/* hbm_budget = 0: 90 % of the free device memory at creation. */
+ctm_status ctm_server_create(ctm_server** out, size_t hbm_budget, int max_concurrent);
+/* Queues a solve; CTM_ENOMEM when it can never fit the budget. */
+ctm_status ctm_server_submit(ctm_server* srv, const ctm_solve_spec* spec, uint64_t* ticket);
+/* Blocks until the solve is done, fills res and, when not NULL, spectra
+ * ([4][Lx*Ly][chi] unit-normalised corner spectra) and energies
+ * ([Lx*Ly][2 directions][re, im] of op); releases the ticket. Returns the
+ * solve's status. */
+ctm_status ctm_server_result(ctm_server* srv, uint64_t ticket, ctm_solve_result* res,
+                             double* spectra, double* energies);
+/* Latency percentiles (submit -> done, nearest rank) and throughput of the
+ * solves finished so far. */
+ctm_status ctm_server_stats(ctm_server* srv, double* p50_ms, double* p99_ms,
+                            double* solves_per_s, int* completed);
+const char* ctm_server_last_error(const ctm_server* srv);
+/* Waits for the running solves, drops the pending ones, frees the server. */
+void ctm_server_free(ctm_server* srv);
+
 /* Checkpoint and resume (host buffers). ctm_save with buf = NULL stores the
  * needed size in *nbytes; otherwise it writes the iteration state (C, T, the
  * rangefinders X, W of every direction and cut, the last corner spectra and

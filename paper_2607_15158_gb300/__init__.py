@@ -34,6 +34,17 @@ class ctm_opts(C.Structure):
                 ("seed", C.c_uint64), ("stream", C.c_void_p)]
 
 
+class ctm_solve_spec(C.Structure):
+    _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("d", C.c_int), ("D", C.c_int),
+                ("chi", C.c_int), ("dtype", C.c_int), ("A", C.c_void_p), ("op", C.c_void_p),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("opts", ctm_opts)]
+
+
+class ctm_solve_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("delta", C.c_double),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("footprint", C.c_size_t)]
+
+
 class CTMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
@@ -75,6 +86,13 @@ def load():
         "ctm_profile_enable": (I, [ctx_p, I]),
         "ctm_profile_read": (I, [ctx_p, P(D), P(C.c_long), P(D), P(D)]),
         "ctm_profile_phases": (I, [ctx_p, P(D)]),
+        "ctm_footprint": (I, [I, I, I, I, I, I, P(ctm_opts), P(C.c_size_t)]),
+        "ctm_server_create": (I, [P(VP), C.c_size_t, I]),
+        "ctm_server_submit": (I, [VP, P(ctm_solve_spec), P(C.c_uint64)]),
+        "ctm_server_result": (I, [VP, C.c_uint64, P(ctm_solve_result), P(D), P(D)]),
+        "ctm_server_stats": (I, [VP, P(D), P(D), P(D), P(I)]),
+        "ctm_server_last_error": (C.c_char_p, [VP]),
+        "ctm_server_free": (None, [VP]),
         "ctm_save": (I, [ctx_p, VP, P(C.c_size_t)]),
         "ctm_load": (I, [ctx_p, VP, C.c_size_t]),
         "ctm_free": (None, [ctx_p]),
@@ -257,6 +275,82 @@ class Context:
         ms, n = C.c_double(), C.c_long()
         _check(self.lib, self.ptr, self.lib.ctm_last_timing(self.ptr, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+
+def ctm_footprint(Lx, Ly, d, D, chi, cplx, opts=None):
+    """Device bytes a context of these dimensions allocates (upper estimate)."""
+    lib = load()
+    o = opts if opts is not None else ctm_default_opts()
+    n = C.c_size_t(0)
+    _check(lib, None, lib.ctm_footprint(Lx, Ly, d, D, chi, CTM_C128 if cplx else CTM_F64,
+                                        C.byref(o), C.byref(n)))
+    return n.value
+
+
+class Server:
+    """Serving runtime (ctm_server_*): solves of mixed cells admitted by
+    device footprint, each on its own stream; methods are the C entry points
+    of the same names."""
+
+    def __init__(self, hbm_budget=0, max_concurrent=4):
+        self.lib = load()
+        self.ptr = C.c_void_p()
+        st = self.lib.ctm_server_create(C.byref(self.ptr), hbm_budget, max_concurrent)
+        if st != CTM_OK:
+            raise CTMError(st, "ctm_server_create failed")
+        self._keep = {}
+
+    def ctm_server_submit(self, A, d, D, chi, tol, max_iter, op=None, cplx=None, opts=None,
+                          Lx=1, Ly=1):
+        if cplx is None:
+            cplx = any(np.iscomplexobj(a) for a in A)
+        arrs = [_host(a, cplx) for a in A]
+        ptrs = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+        o = opts if opts is not None else ctm_default_opts()
+        opa = _host(op, cplx) if op is not None else None
+        spec = ctm_solve_spec(Lx, Ly, d, D, chi, CTM_C128 if cplx else CTM_F64,
+                              C.cast(ptrs, C.c_void_p),
+                              opa.ctypes.data if opa is not None else None, tol, max_iter, o)
+        t = C.c_uint64(0)
+        st = self.lib.ctm_server_submit(self.ptr, C.byref(spec), C.byref(t))
+        if st != CTM_OK:
+            raise CTMError(st, (self.lib.ctm_server_last_error(self.ptr) or b"").decode())
+        self._keep[t.value] = (Lx * Ly, chi, opa is not None)
+        return t.value
+
+    def ctm_server_result(self, ticket):
+        S, chi, has_op = self._keep.pop(ticket)
+        res = ctm_solve_result()
+        spec = np.empty((4, S, chi))
+        en = np.empty((S, 2, 2)) if has_op else None
+        st = self.lib.ctm_server_result(
+            self.ptr, ticket, C.byref(res), spec.ctypes.data_as(C.POINTER(C.c_double)),
+            en.ctypes.data_as(C.POINTER(C.c_double)) if en is not None else None)
+        if st != CTM_OK:
+            raise CTMError(st, (self.lib.ctm_server_last_error(self.ptr) or b"").decode())
+        out = dict(iters=res.iters, delta=res.delta, queue_ms=res.queue_ms, run_ms=res.run_ms,
+                   footprint=res.footprint, spectra=spec)
+        if en is not None:
+            out["energies"] = en[..., 0] + 1j * en[..., 1]
+        return out
+
+    def ctm_server_stats(self):
+        p50, p99, sps, n = C.c_double(), C.c_double(), C.c_double(), C.c_int()
+        self.lib.ctm_server_stats(self.ptr, C.byref(p50), C.byref(p99), C.byref(sps),
+                                  C.byref(n))
+        return dict(p50_ms=p50.value, p99_ms=p99.value, solves_per_s=sps.value,
+                    completed=n.value)
+
+    def ctm_server_free(self):
+        if self.ptr:
+            self.lib.ctm_server_free(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.ctm_server_free()
+        except Exception:  # pragma: no cover
+            pass
 
 
 def ctm_svdvals_noalloc(A_dev, k, dtype, s_dev, stream=0):

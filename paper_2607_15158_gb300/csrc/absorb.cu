@@ -184,15 +184,10 @@ cudaError_t launch_ab(int chi, int Dk, int Db, int d, const void* In, const void
   const int K1 = Dk * Dk, N1 = Db * Db;
   const size_t shm = ((size_t)d * K1 * K1 + (size_t)d * N1 * N1 + 4 * (size_t)K1 * N1) * sizeof(F);
   static size_t configured = 0;
-  if (shm > configured) {
-    const cudaError_t e = cudaFuncSetAttribute(absorb_ab_kernel<T, F>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)shm);
-    if (e != cudaSuccess) return e;
-    configured = shm;
-  }
+  cudaError_t e = raise_smem((const void*)absorb_ab_kernel<T, F>, configured, shm);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, absorb_ab_kernel<T, F>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, absorb_ab_kernel<T, F>,
                                                                 2 * GROUP, shm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;

@@ -1269,6 +1269,44 @@ ctm_status ctm_set_rangefinders(ctm_ctx* c, const void* X, const void* W) {
   return CTM_OK;
 }
 
+// ------------------------------------------------------------ footprint
+// Device bytes a context of these dimensions allocates (the list of create(),
+// plus the split-precision slice caches and partial sums and the dense-SVD
+// buffers), rounded up by 5 % + 64 MB for allocator granularity.
+static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bool cx,
+                       const ctm_opts* o) {
+  const size_t S = (size_t)Lx * Ly, es = cx ? 16 : 8;
+  const size_t N = (size_t)chi * Dk * Db;
+  const size_t k = std::min<size_t>((size_t)chi + o->p, N);
+  const size_t NN = N * N, maxT = (size_t)d * d * NN + 64;
+  const size_t Lmax = std::max(Lx, Ly);
+  const size_t eC = (size_t)chi * chi, eT = eC * Dk * Db;
+  const size_t nk = (size_t)d * Dk * Dk * Dk * Dk, nb = (size_t)d * Db * Db * Db * Db;
+  size_t b = 0;
+  b += 4 * S * (nk + nb) * es;                     // kets, bras
+  b += 4 * S * (eC + eT) * es;                     // C, T
+  b += 2 * 4 * S * N * k * es;                     // X, W
+  b += 4 * NN * es + 2 * maxT * es;                // Q, pipes
+  b += 3 * maxT * es + ((size_t)64 << 20);         // scratch
+  b += 2 * Lmax * N * chi * es + 2 * S * N * chi * es;   // Pl, PrH, last*
+  b += 6 * N * k * es + 2 * k * k * es;            // Z, Xn, Wn, G, Linv
+  b += 2 * Lmax * N * k * es + 3 * Lmax * k * k * es;    // ZR, ZL, rho, u, v
+  b += std::max(jacobi_coop_work_bytes(cx, (int)k, (int)Lmax),
+                jacobi_coop_work_bytes(cx, chi, 4 * (int)S));
+  b += (std::max(k, (size_t)chi) + 2 * k * chi) * es;
+  b += std::max(Lmax * k, 4 * S * (size_t)chi) * sizeof(double);
+  b += Lmax * (2 * eC + eT) * es + 8 * S * chi * sizeof(double);
+  b += 2 * (size_t)d * d * d * d * es + 2 * nk * es + ((size_t)1 << 20);
+  if (o->prec == CTM_PREC_SPLIT_BF16) {
+    const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
+    b += 8 * 3 * N * Kp * 2;                       // corner slices, both orientations
+    b += 2 * 3 * N * Kp * 2;                       // operand slices of general products
+    b += 32 * N * ((cx ? 2 : 1) * k + 160) * 4;    // split-K partials
+  }
+  if (o->method == CTM_PROJ_SVD) b += 3 * NN * es + 2 * N * chi * es + (size_t)64 * N * es;
+  return b + b / 20 + ((size_t)64 << 20);
+}
+
 // ---------------------------------------------------- checkpoint / resume
 namespace {
 
@@ -1358,6 +1396,18 @@ ctm_status ctm_load(ctm_ctx* c, const void* buf, size_t nbytes) {
   c->last_dir = h.last_dir;
   c->spectra_init = h.spectra_init != 0;
   c->qr_calls = h.qr_calls;
+  return CTM_OK;
+}
+
+ctm_status ctm_footprint(int Lx, int Ly, int d, int D, int chi, ctm_dtype dtype,
+                         const ctm_opts* opts, size_t* bytes) {
+  if (!bytes || Lx < 1 || Ly < 1 || d < 1 || D < 1 || chi < 1 ||
+      (dtype != CTM_F64 && dtype != CTM_C128))
+    return CTM_EINVAL;
+  ctm_opts o;
+  if (opts) o = *opts;
+  else ctm_default_opts(&o);
+  *bytes = footprint_bytes(Lx, Ly, d, D, D, chi, dtype == CTM_C128, &o);
   return CTM_OK;
 }
 

@@ -268,16 +268,10 @@ cudaError_t run_ts(const GemmDesc& g, const TsPlan& t, void* work, cudaStream_t 
                    long* launches) {
   const size_t shm = (size_t)TS_ROWS * (g.M + g.N) * sizeof(T);
   static size_t configured[2] = {0, 0};
-  if (shm > configured[g.opA == OP_C]) {
-    const cudaError_t e =
-        g.opA == OP_C
-            ? cudaFuncSetAttribute(gemm_ts_kernel<T, true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)
-            : cudaFuncSetAttribute(gemm_ts_kernel<T, false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    if (e != cudaSuccess) return e;
-    configured[g.opA == OP_C] = shm;
-  }
+  const cudaError_t e =
+      g.opA == OP_C ? raise_smem((const void*)gemm_ts_kernel<T, true>, configured[1], shm)
+                    : raise_smem((const void*)gemm_ts_kernel<T, false>, configured[0], shm);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)t.gx, (unsigned)t.gy);
   if (g.opA == OP_C)
     gemm_ts_kernel<T, true><<<grid, TS_THREADS, shm, s>>>(

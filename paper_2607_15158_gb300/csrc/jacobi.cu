@@ -46,29 +46,39 @@ __device__ __forceinline__ uint64_t gtime() {
   return t;
 }
 
-// bounded sense-reversal grid barrier over all blocks of the launch
+// bounded grid barrier over all blocks of the launch. bar[0] counts
+// arrivals, bar[32] is the generation and bar[64] the abort flag (separate
+// 128-byte lines, so that polling does not contend with the arrivals).
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
-  __threadfence();
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned* vgen = bar + 1;
-    volatile unsigned* vabort = bar + 2;
-    if (*vabort) {
+    unsigned* cnt = bar;
+    unsigned* gen = bar + 32;
+    unsigned* abrt = bar + 64;
+    if (ld_acquire(abrt)) {
       ok = 0;
     } else {
-      const unsigned my_gen = *vgen;
-      const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+      const unsigned my_gen = ld_acquire(gen);
+      __threadfence();   // this block's writes before the arrival
+      const unsigned arrived = atomicAdd(cnt, 1u) + 1u;
       if (arrived == nblocks) {
-        atomicExch(bar, 0u);
+        atomicExch(cnt, 0u);
         __threadfence();
-        atomicAdd(bar + 1, 1u);
+        atomicAdd(gen, 1u);
       } else {
         const uint64_t t0 = gtime();
-        while (*vgen == my_gen) {
-          if (*vabort || gtime() - t0 > 2000000000ull) {
-            atomicExch(bar + 2, 1u);
+        unsigned polls = 0;
+        while (ld_acquire(gen) == my_gen) {
+          if ((++polls & 63u) == 0 && (ld_acquire(abrt) || gtime() - t0 > 2000000000ull)) {
+            atomicExch(abrt, 1u);
             atomicOr(err, DEV_MBAR_TIMEOUT);
             ok = 0;
             break;
@@ -94,15 +104,6 @@ template <>
 __device__ __forceinline__ void stcg<double>(double* p, double v) { __stcg(p, v); }
 template <>
 __device__ __forceinline__ void stcg<cplx>(cplx* p, cplx v) { __stcg(p, v); }
-
-template <typename T>
-__device__ __forceinline__ T phase_conj(T g, double mag);
-template <>
-__device__ __forceinline__ double phase_conj<double>(double g, double mag) { return g / mag; }
-template <>
-__device__ __forceinline__ cplx phase_conj<cplx>(cplx g, double mag) {
-  return make_double2(g.x / mag, -g.y / mag);
-}
 
 __device__ __forceinline__ int player(int pos, int t, int m) {
   return pos == 0 ? 0 : ((pos - 1 + t) % m) + 1;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
       if (lane == 0) __stcg(nsq + c, acc);
     }
     if (!grid_barrier(a.bar, nblocks, a.err)) return;
-    unsigned long long* offb = reinterpret_cast<unsigned long long*>(a.off + 2 * b + (sweep & 1));
+    double* offb = a.off + 2 * b + (sweep & 1);   // set to 1 when a pair rotates
     for (int t = 0; t < m; ++t) {
       for (int pr = gw; pr < npairs; pr += nw) {
         int p = player(pr, t, m), q = player(kk - 1 - pr, t, m);
@@ -159,6 +160,12 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
         T* ap = wa + (size_t)p * k;
         T* aq = wa + (size_t)q * k;
         T xr[R], yr[R];
+        // V's columns are fetched with A's (independent loads) when they fit
+        // in registers
+        constexpr bool kPrefetchV = R <= 9;
+        T vxr[kPrefetchV ? R : 1], vyr[kPrefetchV ? R : 1];
+        T* vp = wv + (size_t)p * k;
+        T* vq = wv + (size_t)q * k;
         T ga = zero_of(T());
 #pragma unroll
         for (int e = 0; e < R; ++e) {
@@ -166,19 +173,30 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
           if (r < k) {
             xr[e] = ldcg(ap + r);
             yr[e] = ldcg(aq + r);
-            fmacv(ga, xr[e], yr[e]);
+            if constexpr (kPrefetchV) {
+              if (a.want_uv) {
+                vxr[e] = ldcg(vp + r);
+                vyr[e] = ldcg(vq + r);
+              }
+            }
           }
         }
+#pragma unroll
+        for (int e = 0; e < R; ++e)
+          if (lane + 32 * e < k) fmacv(ga, xr[e], yr[e]);
         ga = warp_sum(ga);
         const double al = __ldcg(nsq + p), be = __ldcg(nsq + q);
         const double gm = sqrt(absq(ga));
         const double nrm = sqrt(al) * sqrt(be);
+        // rotate when |gamma| > tol sqrt(alpha beta)
         if (!(gm > tol * nrm) || gm == 0.0) continue;
-        if (lane == 0) atomicMax(offb, (unsigned long long)__double_as_longlong(gm / nrm));
+        if (lane == 0) __stcg(offb, 1.0);   // this sweep rotated
         const double zeta = (be - al) / (2.0 * gm);
         const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
         const double c = 1.0 / hypot(1.0, tt), s = c * tt;
-        const T eph = phase_conj<T>(ga, gm);
+        T eph;   // conj(gamma) / |gamma|
+        if constexpr (sizeof(T) == 8) eph = ga / gm;
+        else eph = make_double2(ga.x / gm, -ga.y / gm);
 #pragma unroll
         for (int e = 0; e < R; ++e) {
           const int r = lane + 32 * e;
@@ -193,13 +211,18 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
           __stcg(nsq + q, be + tt * gm);
         }
         if (a.want_uv) {
-          T* vp = wv + (size_t)p * k;
-          T* vq = wv + (size_t)q * k;
 #pragma unroll
           for (int e = 0; e < R; ++e) {
             const int r = lane + 32 * e;
             if (r < k) {
-              const T x = ldcg(vp + r), y = mulv(eph, ldcg(vq + r));
+              T x, y;
+              if constexpr (kPrefetchV) {
+                x = vxr[e];
+                y = mulv(eph, vyr[e]);
+              } else {
+                x = ldcg(vp + r);
+                y = mulv(eph, ldcg(vq + r));
+              }
               stcg(vp + r, subv(scalev(x, c), scalev(y, s)));
               stcg(vq + r, addv(scalev(x, s), scalev(y, c)));
             }
@@ -510,7 +533,8 @@ cudaError_t chol_inv_coop(bool cx, int k, long n, bool shift, bool scale, void* 
 
 size_t jacobi_coop_work_bytes(bool cx, int k, int batch) {
   const size_t es = cx ? 16 : 8;
-  return (size_t)batch * 2 * k * k * es + (size_t)batch * (2 + k) * sizeof(double) + 64;
+  return (size_t)batch * 2 * k * k * es + (size_t)batch * (2 + k) * sizeof(double) + 16 +
+         65 * sizeof(unsigned);
 }
 
 cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double* sv, void* U,
@@ -519,8 +543,24 @@ cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double*
   const size_t es = cx ? 16 : 8;
   const int kk = k + (k & 1);
   const int npairs = kk / 2;
+  const void* fn;
+  if (k <= 32 * 5)
+    fn = cx ? (const void*)jacobi_coop<cplx, 5> : (const void*)jacobi_coop<double, 5>;
+  else if (k <= 32 * 9)
+    fn = cx ? (const void*)jacobi_coop<cplx, 9> : (const void*)jacobi_coop<double, 9>;
+  else if (k <= 32 * 16)
+    fn = cx ? (const void*)jacobi_coop<cplx, 16> : (const void*)jacobi_coop<double, 16>;
+  else
+    return cudaErrorInvalidValue;
+  // one column pair per warp when the co-resident blocks allow it: several
+  // small blocks per SM (max_blocks counts SMs), shared by the batch
+  int per_sm = 1;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, JT, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm > 8) per_sm = 8;
+  if (per_sm < 1) per_sm = 1;
   int G = (npairs + (JT / 32) - 1) / (JT / 32);
-  int cap = max_blocks / (batch > 0 ? batch : 1);
+  int cap = max_blocks * per_sm / (batch > 0 ? batch : 1);
   if (cap < 1) cap = 1;
   if (G > cap) G = cap;
   if (G < 1) G = 1;
@@ -544,18 +584,9 @@ cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double*
   w += (size_t)batch * k * sizeof(double);
   a.bar = reinterpret_cast<unsigned*>((reinterpret_cast<uintptr_t>(w) + 15) & ~(uintptr_t)15);
   a.err = err;
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, 3 * sizeof(unsigned), s);
+  e = cudaMemsetAsync(a.bar, 0, 65 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
-  const void* fn;
-  if (k <= 32 * 5)
-    fn = cx ? (const void*)jacobi_coop<cplx, 5> : (const void*)jacobi_coop<double, 5>;
-  else if (k <= 32 * 9)
-    fn = cx ? (const void*)jacobi_coop<cplx, 9> : (const void*)jacobi_coop<double, 9>;
-  else if (k <= 32 * 16)
-    fn = cx ? (const void*)jacobi_coop<cplx, 16> : (const void*)jacobi_coop<double, 16>;
-  else
-    return cudaErrorInvalidValue;
   e = cudaLaunchCooperativeKernel(fn, dim3(batch * G), dim3(JT), args, 0, s);
   if (launches) ++*launches;
   return e;

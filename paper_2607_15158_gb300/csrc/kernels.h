@@ -5,8 +5,22 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 namespace ctm {
+
+// Raises the dynamic shared-memory limit of kernel fn to at least bytes;
+// configured remembers the largest size set so far. Serialised, so that
+// several host threads (the serving runtime) may launch concurrently.
+inline cudaError_t raise_smem(const void* fn, size_t& configured, size_t bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (bytes <= configured) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) configured = bytes;
+  return e;
+}
 
 // ------------------------------------------------------------- permute.cu
 // out = in with axes reordered: output axis j is input axis perm[j]; both

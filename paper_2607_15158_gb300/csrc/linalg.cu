@@ -735,14 +735,15 @@ size_t chol_smem_bytes(bool cx, int k) {
 }
 
 template <typename T>
-cudaError_t trsm_set_smem(int shm) {
-  cudaError_t e = cudaSuccess;
+cudaError_t trsm_set_smem(size_t (&configured)[5], size_t shm) {
   const void* fns[] = {(const void*)trsm_warp_kernel<T, 2>, (const void*)trsm_warp_kernel<T, 4>,
                        (const void*)trsm_warp_kernel<T, 5>, (const void*)trsm_warp_kernel<T, 6>,
                        (const void*)trsm_warp_kernel<T, 8>};
-  for (const void* f : fns)
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-  return e;
+  for (int i = 0; i < 5; ++i) {
+    const cudaError_t e = raise_smem(fns[i], configured[i], shm);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // R = columns per lane: the smallest of 2, 4, 5, 6, 8 with 32 R >= k
@@ -769,18 +770,14 @@ cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, cons
                          void* L, double* dsc, int* dead, const void* Z, void* Q, int* err,
                          int num_sms, cudaStream_t s, long* launches) {
   const size_t shm = chol_smem_bytes(cx, k);
-  static size_t configured[2] = {0, 0};
-  if (shm > configured[cx ? 1 : 0]) {
-    cudaError_t e;
-    if (cx) {
-      e = cudaFuncSetAttribute(chol_smem_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      if (e == cudaSuccess) e = trsm_set_smem<cplx>((int)shm);
-    } else {
-      e = cudaFuncSetAttribute(chol_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      if (e == cudaSuccess) e = trsm_set_smem<double>((int)shm);
-    }
+  static size_t configured_chol[2] = {0, 0};
+  static size_t configured_trsm[2][5] = {{0}};
+  {
+    cudaError_t e = cx ? raise_smem((const void*)chol_smem_kernel<cplx>, configured_chol[1], shm)
+                       : raise_smem((const void*)chol_smem_kernel<double>, configured_chol[0], shm);
+    if (e == cudaSuccess) e = cx ? trsm_set_smem<cplx>(configured_trsm[1], shm)
+                                 : trsm_set_smem<double>(configured_trsm[0], shm);
     if (e != cudaSuccess) return e;
-    configured[cx ? 1 : 0] = shm;
   }
   // one 1024-thread block per SM (the factor fills shared memory), one warp
   // per row

@@ -243,8 +243,13 @@ __global__ void __launch_bounds__(128, 1)
       uint32_t r[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
       if (row < p.M) {
+        // 64 contiguous bytes of this thread's row (Np, BNc and c0 are
+        // multiples of 16 floats, so the row segment is 64-byte aligned)
+        float4* o4 = reinterpret_cast<float4*>(out + c0);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) out[c0 + i] = __uint_as_float(r[i]);
+        for (int i = 0; i < 4; ++i)
+          o4[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                              __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
       }
     }
   }
@@ -428,15 +433,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn get_encoder() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return (EncodeTiledFn) nullptr;
+  }();
   return fn;
 }
 
@@ -559,12 +564,8 @@ ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* B
   const size_t smem = 1024 + (size_t)STAGES * (3 * A_SLICE_BYTES + 3 * (size_t)BNc * BK * 2) +
                       (2 * STAGES + 1) * 8 + 16;
   static size_t configured = 0;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(split_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return sfail(sc, CTM_ECUDA, "cannot reserve shared memory for the tensor-core kernel");
-    configured = smem;
-  }
+  if (raise_smem((const void*)split_mma_kernel, configured, smem) != cudaSuccess)
+    return sfail(sc, CTM_ECUDA, "cannot reserve shared memory for the tensor-core kernel");
   dim3 grid(mt, nchunks, nks);
   const bool timed = sc->prof && sc->ev_used + 2 <= sc->ev.size();
   if (timed) cudaEventRecord(sc->ev[sc->ev_used], s);

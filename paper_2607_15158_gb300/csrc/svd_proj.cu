@@ -54,9 +54,8 @@ struct Solver {
                              int*) = nullptr;
 };
 
-Solver& solver() {
-  static Solver sv;
-  if (sv.tried) return sv;
+Solver load_solver() {
+  Solver sv;
   sv.tried = true;
   void* lib = nullptr;
   for (const char* name : {"libcusolver.so", "libcusolver.so.12", "libcusolver.so.13",
@@ -72,6 +71,12 @@ Solver& solver() {
   sv.dgesvd = reinterpret_cast<decltype(sv.dgesvd)>(dlsym(lib, "cusolverDnDgesvd"));
   sv.ok = sv.create && sv.destroy && sv.set_stream && sv.zbuf && sv.dbuf && sv.zgesvd &&
           sv.dgesvd;
+  return sv;
+}
+
+// opened once (thread-safe initialisation of a function-local static)
+Solver& solver() {
+  static Solver sv = load_solver();
   return sv;
 }
 

@@ -50,3 +50,24 @@ def test_argument_errors_are_reported_before_device_work(lib):
     st = pkg._lib.ctm_init(ctypes.byref(ptr), 0, 1, None, None, 0, 2, 2, 4, None)
     assert st == pkg.CTM_EINVAL
     assert b"must be >= 1" in pkg._lib.ctm_last_error(None)
+
+
+def test_footprint_is_host_arithmetic(lib):
+    # no device work: grows with chi and D, split precision adds the slice caches
+    f = [pkg.ctm_footprint(1, 1, 2, 3, chi, False) for chi in (9, 18, 27)]
+    assert f[0] < f[1] < f[2]
+    assert pkg.ctm_footprint(1, 1, 2, 4, 27, False) > f[2]
+    split = pkg.ctm_default_opts(prec=pkg.CTM_PREC_SPLIT_BF16)
+    assert pkg.ctm_footprint(1, 1, 2, 3, 27, False, split) > f[2]
+    n = ctypes.c_size_t(0)
+    assert pkg._lib.ctm_footprint(1, 1, 2, 0, 8, 0, None, ctypes.byref(n)) == pkg.CTM_EINVAL
+    # cfg3 (3x3, complex D = 6, chi = 144) fits many times in the 280 GB
+    assert pkg.ctm_footprint(3, 3, 2, 6, 144, True, split) < 40e9
+
+
+def test_noalloc_rejects_oversize_before_device_work(lib):
+    pkg.load()
+    fake = ctypes.c_void_p(16)
+    st = pkg._lib.ctm_svdvals_noalloc(fake, 257, pkg.CTM_C128, fake, None)
+    assert st == pkg.CTM_EINVAL
+    assert b"exceeds" in pkg._lib.ctm_noalloc_last_error()
