@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: Poisson stream of mixed solves, p50/p99 latency")
     ap.add_argument("--requests", type=int, default=32)
-    ap.add_argument("--rate", type=float, default=4.0, help="arrivals per second (serve)")
+    ap.add_argument("--rate", type=float, default=1.0, help="arrivals per second (serve)")
     ap.add_argument("--concurrency", type=int, default=8, help="solves in flight (serve)")
     return ap.parse_args()
 

@@ -118,6 +118,25 @@ struct ctm_ctx {
   bool spectra_init = false;
   // split-precision state
   SplitCtx* split = nullptr;
+  // lanes: the cuts of a column are independent until their small SVDs, so
+  // they run concurrently, each on its own stream with its own corners and
+  // workspace; use_lane() points the fields above at lane i
+  struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    void* Q[4] = {nullptr};
+    void* pipe[2] = {nullptr};
+    char* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    SplitCtx* split = nullptr;
+    void* Z[4] = {nullptr};
+    void* G = nullptr;
+    void* Linv = nullptr;
+    double* dsc = nullptr;
+    int* dead = nullptr;
+  };
+  std::vector<Lane> lanes;   // lane 0 = the context's own buffers and stream
+  int cur_lane = 0;
   // standard truncated-SVD projectors (CTM_PROJ_SVD)
   SvdCtx* svd = nullptr;
   void* svdM = nullptr;      // N x N
@@ -204,6 +223,9 @@ void phases_fold(ctm_ctx* c) {
 }
 
 // ------------------------------------------------------------ helpers
+// number of lanes (concurrent cuts) for an Lx x Ly cell
+int lanes_for(int Lx, int Ly) { return std::min(3, std::max(Lx, Ly)); }
+
 size_t elems_C(const ctm_ctx* c) { return (size_t)c->chi * c->chi; }
 size_t elems_T(const ctm_ctx* c) { return (size_t)c->chi * c->chi * c->Dk * c->Db; }
 size_t elems_ket(const ctm_ctx* c) { return (size_t)c->d * c->Dk * c->Dk * c->Dk * c->Dk; }
@@ -251,6 +273,32 @@ void* BRAp(ctm_ctx* c, int rot, int site) { return at(c->bra[rot & 3], (size_t)s
 // frame accessors
 void* fC(ctm_ctx* c, int r, int i, int x, int y) { return Cp(c, frame_label(r, i), frame_site(c, r, x, y)); }
 void* fT(ctm_ctx* c, int r, int i, int x, int y) { return Tp(c, frame_label(r, i), frame_site(c, r, x, y)); }
+
+// Point the per-cut workspace fields of c at lane i (see ctm_ctx::Lane).
+void use_lane(ctm_ctx* c, int i) {
+  if (c->lanes.empty() || i == c->cur_lane) return;
+  const ctm_ctx::Lane& L = c->lanes[i];
+  c->stream = L.stream;
+  for (int q = 0; q < 4; ++q) c->Q[q] = L.Q[q];
+  c->pipe[0] = L.pipe[0];
+  c->pipe[1] = L.pipe[1];
+  c->scratch = L.scratch;
+  c->scratch_bytes = L.scratch_bytes;
+  c->scratch_off = 0;
+  c->split = L.split;
+  for (int q = 0; q < 4; ++q) c->Z[q] = L.Z[q];
+  c->G = L.G;
+  c->Linv = L.Linv;
+  c->dsc = L.dsc;
+  c->dead = L.dead;
+  c->cur_lane = i;
+}
+
+// returns c to lane 0 when a move leaves early
+struct LaneReset {
+  ctm_ctx* c;
+  ~LaneReset() { use_lane(c, 0); }
+};
 
 void* scratch_alloc(ctm_ctx* c, size_t bytes) {
   size_t off = (c->scratch_off + 255) & ~(size_t)255;
@@ -802,7 +850,17 @@ ctm_status move_impl(ctm_ctx* c, int r) {
                                     NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
       }
     }
+    // the cuts of the column run on the lanes (round robin), after the
+    // previous column's absorption on lane 0
+    const int nl = svd ? 1 : std::max<int>(1, (int)c->lanes.size());
+    LaneReset lane_reset{c};
+    if (nl > 1) {
+      CTM_CUDA_OK(cudaEventRecord(c->lanes[0].ev, c->lanes[0].stream));
+      for (int l = 1; l < nl; ++l)
+        CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[l].stream, c->lanes[0].ev, 0));
+    }
     for (int y = 0; y < (svd ? 0 : Lyf); ++y) {
+      use_lane(c, y % nl);
       {
         PhaseScope ps(c, PH_CORNER);
         for (int i = 0; i < 4; ++i) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
@@ -813,6 +871,13 @@ ctm_status move_impl(ctm_ctx* c, int r) {
         if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
       }
       CK(si_rho(c, r, y * Lxf + x, y));
+    }
+    use_lane(c, 0);
+    if (nl > 1) {
+      for (int l = 1; l < nl; ++l) {
+        CTM_CUDA_OK(cudaEventRecord(c->lanes[l].ev, c->lanes[l].stream));
+        CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[0].stream, c->lanes[l].ev, 0));
+      }
     }
     // the cuts of a column are independent until the absorption: their
     // small SVDs share one launch
@@ -1065,6 +1130,59 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       return bail(st);
     }
   }
+  {
+    // lane 0: the buffers above; lanes 1 .. nl-1 for the other cuts of a
+    // column (SI path, cells with more than one cut per column)
+    ctm_ctx::Lane L0;
+    L0.stream = c->stream;
+    for (int q = 0; q < 4; ++q) L0.Q[q] = c->Q[q];
+    L0.pipe[0] = c->pipe[0];
+    L0.pipe[1] = c->pipe[1];
+    L0.scratch = c->scratch;
+    L0.scratch_bytes = c->scratch_bytes;
+    L0.split = c->split;
+    for (int q = 0; q < 4; ++q) L0.Z[q] = c->Z[q];
+    L0.G = c->G;
+    L0.Linv = c->Linv;
+    L0.dsc = c->dsc;
+    L0.dead = c->dead;
+    if (cudaEventCreateWithFlags(&L0.ev, cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(c, CTM_ECUDA, "cudaEventCreate failed"));
+    c->lanes.push_back(L0);
+    const int nl = c->opts.method == CTM_PROJ_SI ? lanes_for(Lx, Ly) : 1;
+    for (int l = 1; l < nl; ++l) {
+      ctm_ctx::Lane L;
+      c->lanes.push_back(L);
+      ctm_ctx::Lane& M = c->lanes.back();
+      if (cudaStreamCreateWithFlags(&M.stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&M.ev, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(c, CTM_ECUDA, "lane stream creation failed"));
+      // a lane only builds corners and runs the SI round: its pipelines hold
+      // N^2 elements (d N^2 for the unfused absorption), not the d^2 N^2 of
+      // the two-site observables of lane 0
+      const size_t laneT =
+          (size_t)(absorb_ab_supported((int)Dk, (int)Db, d) ? 1 : d) * NN + 64;
+      M.scratch_bytes = 2 * laneT * es + ((size_t)64 << 20);
+      for (int q = 0; q < 4; ++q)
+        if ((st = dalloc(c, &M.Q[q], NN * es)) != CTM_OK) return bail(st);
+      if ((st = dalloc(c, &M.pipe[0], laneT * es)) != CTM_OK ||
+          (st = dalloc(c, &M.pipe[1], laneT * es)) != CTM_OK ||
+          (st = dalloc(c, (void**)&M.scratch, M.scratch_bytes)) != CTM_OK)
+        return bail(st);
+      for (int q = 0; q < 4; ++q)
+        if ((st = dalloc(c, &M.Z[q], N * k * es)) != CTM_OK) return bail(st);
+      if ((st = dalloc(c, &M.G, k * k * es)) != CTM_OK ||
+          (st = dalloc(c, &M.Linv, k * k * es)) != CTM_OK ||
+          (st = dalloc(c, (void**)&M.dsc, k * sizeof(double))) != CTM_OK ||
+          (st = dalloc(c, (void**)&M.dead, k * sizeof(int))) != CTM_OK)
+        return bail(st);
+      if (c->opts.prec == CTM_PREC_SPLIT_BF16 &&
+          (st = split_create(&M.split, cx, (int)N, (int)k, c->err, M.stream)) != CTM_OK) {
+        c->msg = "split-precision setup failed";
+        return bail(st);
+      }
+    }
+  }
   if (c->opts.method == CTM_PROJ_SVD) {
     st = svd_create(&c->svd, cx, (int)N, chi);
     if (st != CTM_OK) {
@@ -1304,6 +1422,17 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
     b += 32 * N * ((cx ? 2 : 1) * k + 160) * 4;    // split-K partials
   }
   if (o->method == CTM_PROJ_SVD) b += 3 * NN * es + 2 * N * chi * es + (size_t)64 * N * es;
+  if (o->method == CTM_PROJ_SI) {
+    // lanes 1 .. nl-1: corners, pipes, scratch, N x k blocks, QR work, split state
+    const size_t laneT = (size_t)(absorb_ab_supported(Dk, Db, d) ? 1 : d) * NN + 64;
+    size_t lane = 4 * NN * es + 4 * laneT * es + ((size_t)64 << 20) + 4 * N * k * es +
+                  2 * k * k * es + 12 * k;
+    if (o->prec == CTM_PREC_SPLIT_BF16) {
+      const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
+      lane += 10 * 3 * N * Kp * 2 + 32 * N * ((cx ? 2 : 1) * k + 160) * 4;
+    }
+    b += (size_t)(lanes_for(Lx, Ly) - 1) * lane;
+  }
   return b + b / 20 + ((size_t)64 << 20);
 }
 
@@ -1640,8 +1769,11 @@ ctm_status ctm_profile_enable(ctm_ctx* c, int on) {
   c->pev_used = 0;
   for (double& v : c->phase_ms) v = 0.0;
   if (!c->split) return CTM_OK;
-  const ctm_status st = split_profile(c->split, on ? 1 : 0, nullptr, nullptr, nullptr, nullptr);
-  if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+  for (size_t l = 0; l < std::max<size_t>(1, c->lanes.size()); ++l) {
+    SplitCtx* sp = c->lanes.empty() ? c->split : c->lanes[l].split;
+    const ctm_status st = split_profile(sp, on ? 1 : 0, nullptr, nullptr, nullptr, nullptr);
+    if (st != CTM_OK) return fail(c, st, split_last_error(sp));
+  }
   return CTM_OK;
 }
 
@@ -1650,8 +1782,20 @@ ctm_status ctm_profile_read(ctm_ctx* c, double* ms, long* launches, double* flop
   if (!c) return CTM_EINVAL;
   if (!c->split) return fail(c, CTM_EUNSUPPORTED, "profiling covers the split-precision kernel");
   Guard gd(c);
-  const ctm_status st = split_profile(c->split, -1, ms, launches, flops, bytes);
-  if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+  double tms = 0, tfl = 0, tby = 0;
+  long tl = 0;
+  for (size_t l = 0; l < std::max<size_t>(1, c->lanes.size()); ++l) {
+    SplitCtx* sp = c->lanes.empty() ? c->split : c->lanes[l].split;
+    double m = 0, f = 0, b = 0;
+    long n = 0;
+    const ctm_status st = split_profile(sp, -1, &m, &n, &f, &b);
+    if (st != CTM_OK) return fail(c, st, split_last_error(sp));
+    tms += m; tl += n; tfl += f; tby += b;
+  }
+  if (ms) *ms = tms;
+  if (launches) *launches = tl;
+  if (flops) *flops = tfl;
+  if (bytes) *bytes = tby;
   return CTM_OK;
 }
 
@@ -1665,10 +1809,19 @@ ctm_status ctm_profile_phases(ctm_ctx* c, double ms[CTM_NPHASES]) {
 
 void ctm_free(ctm_ctx* c) {
   if (!c) return;
+  use_lane(c, 0);
+  for (auto& L : c->lanes)
+    if (L.stream) cudaStreamSynchronize(L.stream);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& e : c->pev) cudaEventDestroy(e);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->split) split_destroy(c->split);
+  for (size_t l = 1; l < c->lanes.size(); ++l) {
+    if (c->lanes[l].split) split_destroy(c->lanes[l].split);
+    if (c->lanes[l].stream) cudaStreamDestroy(c->lanes[l].stream);
+  }
+  for (auto& L : c->lanes)
+    if (L.ev) cudaEventDestroy(L.ev);
   if (c->svd) svd_destroy(c->svd);
   for (void* p : c->allocs) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);

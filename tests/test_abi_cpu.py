@@ -61,8 +61,8 @@ def test_footprint_is_host_arithmetic(lib):
     assert pkg.ctm_footprint(1, 1, 2, 3, 27, False, split) > f[2]
     n = ctypes.c_size_t(0)
     assert pkg._lib.ctm_footprint(1, 1, 2, 0, 8, 0, None, ctypes.byref(n)) == pkg.CTM_EINVAL
-    # cfg3 (3x3, complex D = 6, chi = 144) fits many times in the 280 GB
-    assert pkg.ctm_footprint(3, 3, 2, 6, 144, True, split) < 40e9
+    # cfg3 (3x3, complex D = 6, chi = 144, three lanes) fits several times in the 280 GB
+    assert pkg.ctm_footprint(3, 3, 2, 6, 144, True, split) < 60e9
 
 
 def test_noalloc_rejects_oversize_before_device_work(lib):
