@@ -143,6 +143,11 @@ ctm_status ctm_converge(ctm_ctx* ctx, double tol, int max_iter,
  * (label 1..4) at site (x, y); s_out has chi entries. */
 ctm_status ctm_spectrum(ctm_ctx* ctx, int x, int y, int label, double* s_out);
 
+/* The same for all corners in one batched call: s_out has 4*Lx*Ly*chi
+ * entries, laid out [label 0..3][site][chi] (the convergence measure of
+ * ctm_converge compares these). */
+ctm_status ctm_spectra(ctm_ctx* ctx, double* s_out);
+
 /* Two-site expectation <O> = Tr(O rho) / Tr(rho) on the bond from (x, y) to
  * its right (dir = 0) or lower (dir = 1) neighbour; op is d^2 x d^2,
  * row-major O[(s1', s2')][(s1, s2)] (row = bra), dtype of the context; site 1

@@ -76,6 +76,7 @@ def load():
         "ctm_move": (I, [ctx_p, I]),
         "ctm_converge": (I, [ctx_p, D, I, P(I), P(D)]),
         "ctm_spectrum": (I, [ctx_p, I, I, I, P(D)]),
+        "ctm_spectra": (I, [ctx_p, P(D)]),
         "ctm_expect": (I, [ctx_p, VP, I, I, I, P(D)]),
         "ctm_rdm2": (I, [ctx_p, I, I, I, P(D)]),
         "ctm_expect_site": (I, [ctx_p, VP, I, I, P(D)]),
@@ -199,6 +200,13 @@ class Context:
         s = np.empty(self.chi)
         _check(self.lib, self.ptr, self.lib.ctm_spectrum(
             self.ptr, x, y, label, s.ctypes.data_as(C.POINTER(C.c_double))))
+        return s
+
+    def ctm_spectra(self):
+        """All corner spectra, [4][Lx*Ly][chi] (unit-normalised)."""
+        s = np.empty((4, self.Lx * self.Ly, self.chi))
+        _check(self.lib, self.ptr, self.lib.ctm_spectra(
+            self.ptr, s.ctypes.data_as(C.POINTER(C.c_double))))
         return s
 
     def ctm_expect(self, op, x, y, direction):

@@ -533,7 +533,7 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
   for (int pass = 0; pass < passes; ++pass) {
     const int opH = c->cx ? OP_C : OP_T;
     if (split && pass == passes - 1) {
-      // last pass of a split context: the block is orthonormal to ~1e-8, so
+      // last pass of a split context: the block is orthonormal to ~1e-7, so
       // Q <- Q L^-H with L = chol(Q^H Q) = I + F is applied to first order,
       // Q <- Q - Q F^H: the fp64 Gram fixes F, and the small correction
       // Q F^H runs on the tensor cores (its ~1e-7 relative error is ~1e-15
@@ -568,7 +568,17 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
       CK(gemm(c, g));
     }
     int* dead = c->dead;   // every pass finds and refills dependent columns
-    if (smem_chol) {
+    if (split && smem_chol && pass == 1) {
+      // second pass of a split context: the block is already conditioned by
+      // the shifted pass, so Q = Z D^-1 L^-H runs on the tensor cores (the
+      // explicit k x k inverse replaces the fp64 row solve; its ~1e-7 error
+      // is removed by the correction pass that follows)
+      CTM_CUDA_OK(chol_factor_inv(c->cx, c->k, c->N, false, true, c->G, c->Linv, c->dsc, dead,
+                                  c->G, c->err, c->stream, &c->launches));
+      const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, OP_N, c->G, c->k, c->N, c->k,
+                                       c->k, tmp, c->k, c->stream, &c->launches);
+      if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+    } else if (smem_chol) {
       // L = chol(D^-1 G D^-1) in shared memory, Q = Z D^-1 L^-H row by row
       CTM_CUDA_OK(chol_qr_pass(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
                                Zm, tmp, c->err, c->num_sms, c->stream, &c->launches));
@@ -1612,6 +1622,23 @@ ctm_status ctm_spectrum(ctm_ctx* c, int x, int y, int label, double* s_out) {
                               &c->launches));
   CTM_CUDA_OK(normalize(false, c->chi, c->sv, 0, 1, c->dscal, true, c->scratch, c->stream, &c->launches));
   CTM_CUDA_OK(cudaMemcpyAsync(s_out, c->sv, c->chi * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  return CTM_OK;
+}
+
+ctm_status ctm_spectra(ctm_ctx* c, double* s_out) {
+  if (!c || !s_out) return fail(c, CTM_EINVAL, "NULL argument");
+  Guard gd(c);
+  const int nb = 4 * c->S;
+  CK(corner_spectra(c, c->sv));
+  const size_t mark = c->scratch_off;
+  double* nrm = static_cast<double*>(scratch_alloc(c, (size_t)nb * sizeof(double)));
+  void* w = scratch_alloc(c, (size_t)nb * 152 * sizeof(double));
+  if (!nrm || !w) return fail(c, CTM_ENOMEM, "scratch arena too small for the spectra");
+  CTM_CUDA_OK(normalize(false, c->chi, c->sv, c->chi, nb, nrm, true, w, c->stream, &c->launches));
+  c->scratch_off = mark;
+  CTM_CUDA_OK(cudaMemcpyAsync(s_out, c->sv, (size_t)nb * c->chi * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
   CK(check_err(c));
   return CTM_OK;
 }

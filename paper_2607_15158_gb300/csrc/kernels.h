@@ -97,6 +97,13 @@ cudaError_t orth_correction(bool cx, int k, const void* G, void* B, cudaStream_t
 cudaError_t sub_inplace(bool cx, long n, void* z, const void* d, cudaStream_t s,
                         long* launches);
 
+// The factor of chol_qr_pass (same options) and, instead of the row solve,
+// W = D^-1 L^-H (k x k, row-major, upper triangular) so that the caller
+// forms Q = Z W with a GEMM. L receives the factor.
+cudaError_t chol_factor_inv(bool cx, int k, long rows, bool shift, bool scale, const void* G,
+                            void* L, double* dsc, int* dead, void* W, int* err, cudaStream_t s,
+                            long* launches);
+
 // Overwrite the dead columns of a rows x k matrix with deterministic
 // pseudo-random entries (a counter-based hash of seed, column, row).
 cudaError_t repair_dead_columns(bool cx, long rows, int k, void* Q, const int* dead,

@@ -746,6 +746,14 @@ cudaError_t trsm_set_smem(size_t (&configured)[5], size_t shm) {
   return cudaSuccess;
 }
 
+// one shared-memory limit per Cholesky kernel instance, raised monotonically
+// (every launcher of chol_smem_kernel goes through here)
+cudaError_t chol_smem_prepare(bool cx, size_t shm) {
+  static size_t configured[2] = {0, 0};
+  return cx ? raise_smem((const void*)chol_smem_kernel<cplx>, configured[1], shm)
+            : raise_smem((const void*)chol_smem_kernel<double>, configured[0], shm);
+}
+
 // R = columns per lane: the smallest of 2, 4, 5, 6, 8 with 32 R >= k
 #define CTM_TRSM_LAUNCH(T)                                                                     \
   do {                                                                                         \
@@ -770,11 +778,9 @@ cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, cons
                          void* L, double* dsc, int* dead, const void* Z, void* Q, int* err,
                          int num_sms, cudaStream_t s, long* launches) {
   const size_t shm = chol_smem_bytes(cx, k);
-  static size_t configured_chol[2] = {0, 0};
   static size_t configured_trsm[2][5] = {{0}};
   {
-    cudaError_t e = cx ? raise_smem((const void*)chol_smem_kernel<cplx>, configured_chol[1], shm)
-                       : raise_smem((const void*)chol_smem_kernel<double>, configured_chol[0], shm);
+    cudaError_t e = chol_smem_prepare(cx, shm);
     if (e == cudaSuccess) e = cx ? trsm_set_smem<cplx>(configured_trsm[1], shm)
                                  : trsm_set_smem<double>(configured_trsm[0], shm);
     if (e != cudaSuccess) return e;
@@ -792,6 +798,55 @@ cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, cons
     chol_smem_kernel<double><<<1, 256, shm, s>>>(k, rows, shift, scale, (const double*)G, (double*)L,
                                                   dsc, dead, err);
     CTM_TRSM_LAUNCH(double);
+  }
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+// W = D^-1 L^-H from the factor of chol_smem_kernel: block c solves the
+// column c of X = L^-1 by forward substitution (one warp, x in shared
+// memory) and writes row c of W, W[c][i] = conj(X[i][c]) / D_c (i >= c).
+template <typename T>
+__global__ void __launch_bounds__(32) trinv_kernel(int k, const T* L, const double* dsc, T* W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  const int c = blockIdx.x, lane = threadIdx.x;
+  for (int i = c; i < k; ++i) {
+    T acc = zero_of(T());
+    const T* Li = L + (size_t)i * k;
+    for (int l = c + lane; l < i; l += 32) fmav(acc, Li[l], xs[l]);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double inv = 1.0 / realv(Li[i]);
+      if (i == c) {
+        if constexpr (sizeof(T) == 8) xs[i] = inv;
+        else xs[i] = make_double2(inv, 0.0);
+      } else {
+        xs[i] = scalev(acc, -inv);
+      }
+    }
+    __syncwarp();
+  }
+  const double id = 1.0 / dsc[c];
+  for (int i = lane; i < k; i += 32)
+    W[(size_t)c * k + i] = i >= c ? scalev(conjv(xs[i]), id) : zero_of(T());
+}
+
+cudaError_t chol_factor_inv(bool cx, int k, long rows, bool shift, bool scale, const void* G,
+                            void* L, double* dsc, int* dead, void* W, int* err, cudaStream_t s,
+                            long* launches) {
+  const size_t shm = chol_smem_bytes(cx, k);
+  const cudaError_t e = chol_smem_prepare(cx, shm);
+  if (e != cudaSuccess) return e;
+  if (cx) {
+    chol_smem_kernel<cplx><<<1, 256, shm, s>>>(k, rows, shift, scale, (const cplx*)G, (cplx*)L,
+                                                dsc, dead, err);
+    trinv_kernel<cplx><<<k, 32, (size_t)k * sizeof(cplx), s>>>(k, (const cplx*)L, dsc, (cplx*)W);
+  } else {
+    chol_smem_kernel<double><<<1, 256, shm, s>>>(k, rows, shift, scale, (const double*)G,
+                                                  (double*)L, dsc, dead, err);
+    trinv_kernel<double><<<k, 32, (size_t)k * sizeof(double), s>>>(k, (const double*)L, dsc,
+                                                                    (double*)W);
   }
   if (launches) *launches += 2;
   return cudaGetLastError();

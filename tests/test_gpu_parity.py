@@ -222,3 +222,15 @@ def test_errors_are_status_codes():
         ctx.ctm_free_energy() if ctx.Lx * ctx.Ly > 1 else ctx.ctm_spectrum(0, 0, 9)
     assert e.value.status == pkg.CTM_EINVAL
     ctx.ctm_free()
+
+
+def test_batched_spectra_match_single_corner_calls():
+    ctx, ref = _pair(2, 2, 2, 2, 8, 5, True, 1)
+    ctx.ctm_converge(0.0, 2)
+    allspec = ctx.ctm_spectra()
+    for lab in range(4):
+        for y in range(2):
+            for x in range(2):
+                s = ctx.ctm_spectrum(x, y, lab + 1)
+                assert np.abs(allspec[lab, y * 2 + x] - s).max() < 1e-13
+    ctx.ctm_free()
