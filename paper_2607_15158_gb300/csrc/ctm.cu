@@ -223,8 +223,12 @@ void phases_fold(ctm_ctx* c) {
 }
 
 // ------------------------------------------------------------ helpers
-// number of lanes (concurrent cuts) for an Lx x Ly cell
-int lanes_for(int Lx, int Ly) { return std::min(3, std::max(Lx, Ly)); }
+// number of lanes for an Lx x Ly cell: lane 0 runs the column-level work
+// (small SVDs, projectors, absorption), lanes 1 .. 3 the cuts
+int lanes_for(int Lx, int Ly) {
+  const int L = std::max(Lx, Ly);
+  return L >= 2 ? std::min(3, L) + 1 : 1;
+}
 
 size_t elems_C(const ctm_ctx* c) { return (size_t)c->chi * c->chi; }
 size_t elems_T(const ctm_ctx* c) { return (size_t)c->chi * c->chi * c->Dk * c->Db; }
@@ -845,6 +849,7 @@ ctm_status move_impl(ctm_ctx* c, int r) {
   const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
   const size_t NC = (size_t)c->N * c->chi;
   const bool svd = c->opts.method == CTM_PROJ_SVD;
+  std::vector<char> prefetched(Lyf, 0);
   for (int x = 0; x < Lxf; ++x) {
     if (svd) {
       for (int y = 0; y < Lyf; ++y) {
@@ -860,33 +865,60 @@ ctm_status move_impl(ctm_ctx* c, int r) {
                                     NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
       }
     }
-    // the cuts of the column run on the lanes (round robin), after the
+    // the cuts of the column run on lanes 1 .. nw (round robin), after the
     // previous column's absorption on lane 0
     const int nl = svd ? 1 : std::max<int>(1, (int)c->lanes.size());
+    const int nw = nl - 1;
+    auto lane_of = [&](int y) { return nw > 0 ? 1 + y % nw : 0; };
     LaneReset lane_reset{c};
-    if (nl > 1) {
+    if (nw > 0) {
       CTM_CUDA_OK(cudaEventRecord(c->lanes[0].ev, c->lanes[0].stream));
       for (int l = 1; l < nl; ++l)
         CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[l].stream, c->lanes[0].ev, 0));
     }
     for (int y = 0; y < (svd ? 0 : Lyf); ++y) {
-      use_lane(c, y % nl);
+      use_lane(c, lane_of(y));
+      const bool pre = prefetched[y] != 0;   // Q2, Q3 already built and sliced
       {
         PhaseScope ps(c, PH_CORNER);
-        for (int i = 0; i < 4; ++i) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
+        for (int i = 0; i < 4; ++i)
+          if (!(pre && (i == 1 || i == 2))) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
       }
       if (c->split) {
         PhaseScope ps(c, PH_SLICE);
-        const ctm_status st = split_prepare_corners(c->split, c->Q, c->N, c->stream, &c->launches);
+        const ctm_status st = split_prepare_corners(c->split, c->Q, c->N, pre ? 0x9u : 0xFu,
+                                                    c->stream, &c->launches);
         if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
       }
+      prefetched[y] = 0;
       CK(si_rho(c, r, y * Lxf + x, y));
     }
     use_lane(c, 0);
-    if (nl > 1) {
+    if (nw > 0) {
       for (int l = 1; l < nl; ++l) {
         CTM_CUDA_OK(cudaEventRecord(c->lanes[l].ev, c->lanes[l].stream));
         CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[0].stream, c->lanes[l].ev, 0));
+      }
+      // Q2 and Q3 of the next column's cuts sit two columns to the right of
+      // this one, which this column's absorption does not touch (Lxf >= 2):
+      // the lanes build and slice them while lane 0 finishes this column
+      if (!svd && x + 1 < Lxf && Lxf >= 2) {
+        for (int y = 0; y < Lyf; ++y) {
+          use_lane(c, lane_of(y));
+          {
+            PhaseScope ps(c, PH_CORNER);
+            CK(enlarged_corner(c, r, 1, x + 1, y, c->Q[1]));
+            CK(enlarged_corner(c, r, 2, x + 1, y, c->Q[2]));
+          }
+          if (c->split) {
+            PhaseScope ps(c, PH_SLICE);
+            const ctm_status st =
+                split_prepare_corners(c->split, c->Q, c->N, 0x6u, c->stream, &c->launches);
+            if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+          }
+          prefetched[y] = 1;
+        }
+        use_lane(c, 0);
       }
     }
     // the cuts of a column are independent until the absorption: their

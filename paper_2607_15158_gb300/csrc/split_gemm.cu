@@ -675,12 +675,13 @@ void split_destroy(SplitCtx* sc) {
   delete sc;
 }
 
-ctm_status split_prepare_corners(SplitCtx* sc, void* const* Q, int N, cudaStream_t s,
-                                 long* launches) {
+ctm_status split_prepare_corners(SplitCtx* sc, void* const* Q, int N, unsigned mask,
+                                 cudaStream_t s, long* launches) {
   const int Kr = sc->cx ? 2 * N : N;
   const int Kp = pad_to(Kr, BK);
   sc->corner_Kp = Kp;
   for (int i = 0; i < 4; ++i) {
+    if (!(mask >> i & 1u)) continue;
     sc->corner_src[i] = Q[i];
     for (int o = 0; o < 2; ++o) {
       if (!sc->cslices[i][o]) {

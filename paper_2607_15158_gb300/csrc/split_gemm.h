@@ -16,10 +16,10 @@ struct SplitCtx;
 ctm_status split_create(SplitCtx** out, bool cx, int N, int k, int* err, cudaStream_t s);
 void split_destroy(SplitCtx* sc);
 
-// Slice the four fp64 corners Q[0..3] (N x N) into bf16 operands, in both
-// orientations (for op(Q) = Q and op(Q) = Q^H).
-ctm_status split_prepare_corners(SplitCtx* sc, void* const* Q, int N, cudaStream_t s,
-                                 long* launches);
+// Slice the fp64 corners Q[i] (N x N) whose bit i is set in mask into bf16
+// operands, in both orientations (for op(Q) = Q and op(Q) = Q^H).
+ctm_status split_prepare_corners(SplitCtx* sc, void* const* Q, int N, unsigned mask,
+                                 cudaStream_t s, long* launches);
 
 // Zout = op(Q) Zin for one of the prepared corners (identified by pointer),
 // Zin, Zout fp64 N x k row-major.
