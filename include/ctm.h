@@ -281,7 +281,7 @@ const char* ctm_last_error(const ctm_ctx* ctx);
  * that owns all device memory through its own allocator, or a loop in which a
  * cudaMalloc / cudaFree would stall on a device-wide synchronisation). It runs
  * the same one-sided Jacobi kernel as ctm_spectrum, but keeps all of its
- * scratch in one fixed array of 2 MiB + 4 KiB reserved in device memory for
+ * scratch in one fixed array of 2 MiB + 8 KiB reserved in device memory for
  * every GPU that loads the library, for the life of the process.
  *
  *   A       device pointer, the matrix in column-major order, k*k elements of

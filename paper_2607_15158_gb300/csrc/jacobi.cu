@@ -36,6 +36,7 @@ struct JacobiArgs {
   void* work;            // per matrix: 2 k^2 elements (A and V, column-major)
   double* off;           // per matrix: 2 sweep slots (bits of a double)
   double* norms;         // per matrix: k
+  unsigned* ver;         // per matrix: k column versions (rounds applied)
   unsigned* bar;         // [count, generation, abort]
   int* err;
 };
@@ -105,6 +106,31 @@ __device__ __forceinline__ void stcg<double>(double* p, double v) { __stcg(p, v)
 template <>
 __device__ __forceinline__ void stcg<cplx>(cplx* p, cplx v) { __stcg(p, v); }
 
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// lane 0 waits until columns p and q (q < 0: none) have been through round
+// r; bounded like the grid barrier (abort flag, 2 s). Returns false on abort.
+__device__ bool wait_columns(const unsigned* ver, int p, int q, unsigned r, unsigned* bar,
+                             int* err, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    unsigned* abrt = bar + 64;
+    const uint64_t t0 = gtime();
+    unsigned polls = 0;
+    while (ld_acquire(ver + p) != r || (q >= 0 && ld_acquire(ver + q) != r)) {
+      if ((++polls & 63u) == 0 && (ld_acquire(abrt) || gtime() - t0 > 2000000000ull)) {
+        atomicExch(abrt, 1u);
+        atomicOr(err, DEV_MBAR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 __device__ __forceinline__ int player(int pos, int t, int m) {
   return pos == 0 ? 0 : ((pos - 1 + t) % m) + 1;
 }
@@ -131,6 +157,8 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
     stcg(wa + (size_t)c * k + r, Ab[idx]);
     if (a.want_uv) stcg(wv + (size_t)c * k + r, (r == c) ? one : zero_of(T()));
   }
+  unsigned* ver = a.ver + (size_t)b * k;
+  for (int c = g * JT + threadIdx.x; c < k; c += G * JT) ver[c] = 0u;
   if (g == 0 && threadIdx.x == 0) {
     a.off[2 * b] = 0.0;
     a.off[2 * b + 1] = 0.0;
@@ -151,89 +179,105 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
       if (lane == 0) __stcg(nsq + c, acc);
     }
     if (!grid_barrier(a.bar, nblocks, a.err)) return;
+    // every block read the previous sweep's flag before this barrier: clear
+    // the slot of the next sweep
+    if (g == 0 && threadIdx.x == 0) a.off[2 * b + ((sweep + 1) & 1)] = 0.0;
     double* offb = a.off + 2 * b + (sweep & 1);   // set to 1 when a pair rotates
+    // rounds without grid barriers: a pair waits only for the two pairs of
+    // the previous round that wrote its columns (column versions), so the
+    // rotations are the same as with a barrier per round
+    bool dead = false;
     for (int t = 0; t < m; ++t) {
+      const unsigned rg = (unsigned)(sweep * m + t);
       for (int pr = gw; pr < npairs; pr += nw) {
         int p = player(pr, t, m), q = player(kk - 1 - pr, t, m);
         if (p > q) { const int tmp = p; p = q; q = tmp; }
-        if (q >= k) continue;
-        T* ap = wa + (size_t)p * k;
-        T* aq = wa + (size_t)q * k;
-        T xr[R], yr[R];
-        // V's columns are fetched with A's (independent loads) when they fit
-        // in registers
-        constexpr bool kPrefetchV = R <= 9;
-        T vxr[kPrefetchV ? R : 1], vyr[kPrefetchV ? R : 1];
-        T* vp = wv + (size_t)p * k;
-        T* vq = wv + (size_t)q * k;
-        T ga = zero_of(T());
-#pragma unroll
-        for (int e = 0; e < R; ++e) {
-          const int r = lane + 32 * e;
-          if (r < k) {
-            xr[e] = ldcg(ap + r);
-            yr[e] = ldcg(aq + r);
-            if constexpr (kPrefetchV) {
-              if (a.want_uv) {
-                vxr[e] = ldcg(vp + r);
-                vyr[e] = ldcg(vq + r);
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int e = 0; e < R; ++e)
-          if (lane + 32 * e < k) fmacv(ga, xr[e], yr[e]);
-        ga = warp_sum(ga);
-        const double al = __ldcg(nsq + p), be = __ldcg(nsq + q);
-        const double gm = sqrt(absq(ga));
-        const double nrm = sqrt(al) * sqrt(be);
-        // rotate when |gamma| > tol sqrt(alpha beta)
-        if (!(gm > tol * nrm) || gm == 0.0) continue;
-        if (lane == 0) __stcg(offb, 1.0);   // this sweep rotated
-        const double zeta = (be - al) / (2.0 * gm);
-        const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-        const double c = 1.0 / hypot(1.0, tt), s = c * tt;
-        T eph;   // conj(gamma) / |gamma|
-        if constexpr (sizeof(T) == 8) eph = ga / gm;
-        else eph = make_double2(ga.x / gm, -ga.y / gm);
-#pragma unroll
-        for (int e = 0; e < R; ++e) {
-          const int r = lane + 32 * e;
-          if (r < k) {
-            const T x = xr[e], y = mulv(eph, yr[e]);
-            stcg(ap + r, subv(scalev(x, c), scalev(y, s)));
-            stcg(aq + r, addv(scalev(x, s), scalev(y, c)));
-          }
-        }
-        if (lane == 0) {
-          __stcg(nsq + p, al - tt * gm);
-          __stcg(nsq + q, be + tt * gm);
-        }
-        if (a.want_uv) {
+        const bool real = q < k;
+        if (!dead) dead = !wait_columns(ver, p, real ? q : -1, rg, a.bar, a.err, lane);
+        if (!dead && real) {
+          T* ap = wa + (size_t)p * k;
+          T* aq = wa + (size_t)q * k;
+          T xr[R], yr[R];
+          // V's columns are fetched with A's (independent loads) when they
+          // fit in registers
+          constexpr bool kPrefetchV = R <= 9;
+          T vxr[kPrefetchV ? R : 1], vyr[kPrefetchV ? R : 1];
+          T* vp = wv + (size_t)p * k;
+          T* vq = wv + (size_t)q * k;
+          T ga = zero_of(T());
 #pragma unroll
           for (int e = 0; e < R; ++e) {
             const int r = lane + 32 * e;
             if (r < k) {
-              T x, y;
+              xr[e] = ldcg(ap + r);
+              yr[e] = ldcg(aq + r);
               if constexpr (kPrefetchV) {
-                x = vxr[e];
-                y = mulv(eph, vyr[e]);
-              } else {
-                x = ldcg(vp + r);
-                y = mulv(eph, ldcg(vq + r));
+                if (a.want_uv) {
+                  vxr[e] = ldcg(vp + r);
+                  vyr[e] = ldcg(vq + r);
+                }
               }
-              stcg(vp + r, subv(scalev(x, c), scalev(y, s)));
-              stcg(vq + r, addv(scalev(x, s), scalev(y, c)));
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < R; ++e)
+            if (lane + 32 * e < k) fmacv(ga, xr[e], yr[e]);
+          ga = warp_sum(ga);
+          const double al = __ldcg(nsq + p), be = __ldcg(nsq + q);
+          const double gm = sqrt(absq(ga));
+          const double nrm = sqrt(al) * sqrt(be);
+          // rotate when |gamma| > tol sqrt(alpha beta)
+          if (gm > tol * nrm && gm != 0.0) {
+            if (lane == 0) __stcg(offb, 1.0);   // this sweep rotated
+            const double zeta = (be - al) / (2.0 * gm);
+            const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+            const double c = 1.0 / hypot(1.0, tt), s = c * tt;
+            T eph;   // conj(gamma) / |gamma|
+            if constexpr (sizeof(T) == 8) eph = ga / gm;
+            else eph = make_double2(ga.x / gm, -ga.y / gm);
+#pragma unroll
+            for (int e = 0; e < R; ++e) {
+              const int r = lane + 32 * e;
+              if (r < k) {
+                const T x = xr[e], y = mulv(eph, yr[e]);
+                stcg(ap + r, subv(scalev(x, c), scalev(y, s)));
+                stcg(aq + r, addv(scalev(x, s), scalev(y, c)));
+              }
+            }
+            if (lane == 0) {
+              __stcg(nsq + p, al - tt * gm);
+              __stcg(nsq + q, be + tt * gm);
+            }
+            if (a.want_uv) {
+#pragma unroll
+              for (int e = 0; e < R; ++e) {
+                const int r = lane + 32 * e;
+                if (r < k) {
+                  T x, y;
+                  if constexpr (kPrefetchV) {
+                    x = vxr[e];
+                    y = mulv(eph, vyr[e]);
+                  } else {
+                    x = ldcg(vp + r);
+                    y = mulv(eph, ldcg(vq + r));
+                  }
+                  stcg(vp + r, subv(scalev(x, c), scalev(y, s)));
+                  stcg(vq + r, addv(scalev(x, s), scalev(y, c)));
+                }
+              }
             }
           }
         }
+        // publish: columns p and q have been through round rg
+        __syncwarp();
+        if (lane == 0 && !dead) {
+          __threadfence();
+          st_release(ver + p, rg + 1u);
+          if (real) st_release(ver + q, rg + 1u);
+        }
       }
-      if (!grid_barrier(a.bar, nblocks, a.err)) return;
-      // after the first barrier of a sweep every block has read the previous
-      // sweep's flag: clear the slot of the next sweep
-      if (t == 0 && g == 0 && threadIdx.x == 0) a.off[2 * b + ((sweep + 1) & 1)] = 0.0;
     }
+    if (!grid_barrier(a.bar, nblocks, a.err)) return;
     // convergence of the whole batch: every block reads every flag
     bool all = true;
     for (int bb = 0; bb < a.batch; ++bb)
@@ -533,8 +577,8 @@ cudaError_t chol_inv_coop(bool cx, int k, long n, bool shift, bool scale, void* 
 
 size_t jacobi_coop_work_bytes(bool cx, int k, int batch) {
   const size_t es = cx ? 16 : 8;
-  return (size_t)batch * 2 * k * k * es + (size_t)batch * (2 + k) * sizeof(double) + 16 +
-         65 * sizeof(unsigned);
+  return (size_t)batch * 2 * k * k * es + (size_t)batch * (2 + k) * sizeof(double) +
+         (size_t)batch * k * sizeof(unsigned) + 16 + 65 * sizeof(unsigned);
 }
 
 cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double* sv, void* U,
@@ -582,6 +626,8 @@ cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double*
   w += (size_t)batch * 2 * sizeof(double);
   a.norms = reinterpret_cast<double*>(w);
   w += (size_t)batch * k * sizeof(double);
+  a.ver = reinterpret_cast<unsigned*>(w);
+  w += (size_t)batch * k * sizeof(unsigned);
   a.bar = reinterpret_cast<unsigned*>((reinterpret_cast<uintptr_t>(w) + 15) & ~(uintptr_t)15);
   a.err = err;
   e = cudaMemsetAsync(a.bar, 0, 65 * sizeof(unsigned), s);

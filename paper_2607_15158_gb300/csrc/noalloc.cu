@@ -25,7 +25,7 @@ namespace {
 constexpr int kMaxKComplex = 256;
 constexpr int kMaxKReal = 362;
 constexpr size_t kHeaderBytes = 256;
-constexpr size_t kScratchBytes = (2u << 20) + 4096;  // 2 MiB + 4 KiB
+constexpr size_t kScratchBytes = (2u << 20) + 8192;  // 2 MiB + 8 KiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
