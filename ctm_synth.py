@@ -176,6 +176,10 @@ WORKLOADS = {
     # 3x3 cell, complex A[2,6,...], chi = 144 (half-system 5184 x 5184)
     "cfg3_3x3_D6_chi144_c128": dict(Lx=3, Ly=3, d=2, D=6, chi=144, p=5,
                                     complex_=True, diag_weight=0.0, si_rounds=1),
+    # 1x1 cell, complex A[2,8,...], chi = 256 (half-system 16384 x 16384): the
+    # throughput run at the larger bond dimension (one cut per move)
+    "cfg3b_1x1_D8_chi256_c128": dict(Lx=1, Ly=1, d=2, D=8, chi=256, p=5,
+                                     complex_=True, diag_weight=0.0, si_rounds=1),
     # 1x1 cell, complex A[2,4,...], chi = 100 (N = 1600): the cfg3 kernels at a
     # size whose working set (~1.5 GB) suits a full counter capture
     "small_1x1_D4_chi100_c128": dict(Lx=1, Ly=1, d=2, D=4, chi=100, p=5, complex_=True,

@@ -589,7 +589,10 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
     } else {
       CTM_CUDA_OK(chol_inv_coop(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, 1, dead,
                                 c->chol_work, c->err, c->num_sms, c->stream, &c->launches));
-      if (split) {
+      // the shifted first pass multiplies by an inverse of norm up to
+      // shift^-1/2 (~1e4): it stays fp64; the conditioned second pass may
+      // run on the tensor cores
+      if (split && pass > 0) {
         const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, opH, c->Linv, c->k, c->N, c->k,
                                          c->k, tmp, c->k, c->stream, &c->launches);
         if (st != CTM_OK) return fail(c, st, split_last_error(c->split));

@@ -114,6 +114,30 @@ def test_single_moves_each_direction():
     ctx.ctm_free()
 
 
+@pytest.mark.parametrize("case", [
+    # k = 175 complex: the packed Gram factor no longer fits one block's
+    # shared memory, so the QR passes take the cooperative Cholesky with an
+    # explicit inverse, and the Jacobi SVD nine columns per lane
+    (1, 1, 2, 2, 170, 5, True, 1),
+    # D = 7 (D^2 = 49 > 36): the enlarged corners and the site absorption run
+    # unfused, as two GEMMs with permutes in between
+    (1, 1, 2, 7, 4, 3, True, 1),
+])
+def test_large_block_and_unfused_absorption_track_oracle(case):
+    Lx, Ly, d, D, chi, p, cplx, rounds = case
+    ctx, ref = _pair(Lx, Ly, d, D, chi, p, cplx, rounds)
+    for r in (0, 1):
+        ctx.ctm_move(r)
+        ref.left_move(r)
+    spec = ref.spectra()
+    for lab in range(4):
+        s = ctx.ctm_spectrum(0, 0, lab + 1)
+        assert np.abs(s - spec[lab][0]).max() < 1e-9, lab
+    Pl, PrH = ctx.ctm_get_projectors(1, 0, 0)
+    assert np.abs(PrH.conj().T @ Pl - np.eye(Pl.shape[1])).max() < 1e-9
+    ctx.ctm_free()
+
+
 def test_cfg1_workload_converges_like_the_oracle():
     """1x1 cell, real A[2,3,3,3,3], chi = 27, p = 5, 2 SI rounds, to
     Delta < 1e-10 (the small workload of the benchmark suite)."""
