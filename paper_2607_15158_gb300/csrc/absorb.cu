@@ -10,10 +10,15 @@
 //   Out += Y_s B_s    (Dk^2 x Db^2) (Db^2 x Db^2),  B_s[(w,v),(D,E)] = B[s,v,w,D,E]
 // so one kernel reads In once and writes Out once (HBM-bound in fp32; the
 // unfused form is two permutes, two GEMMs and a final permute). Each CTA
-// holds A and B in shared memory and runs two groups of 144 threads, one
-// (t, n) pair each; a thread owns a 3 x 3 register tile of the 36 x 36
-// products (Dk, Db <= 6). Arithmetic in F: fp32 (split-precision contexts,
-// ~1e-7 relative like the bf16x3 products) or fp64.
+// holds A and B in shared memory and runs NG groups of GT x GT threads, one
+// (t, n) pair each; a thread owns a TL x TL register tile of the products,
+// rows ti + GT a and columns tj + GT b (consecutive threads read consecutive
+// shared-memory words). Two geometries: GT = 12, TL = 3, two groups for
+// Dk^2, Db^2 <= 36 (D <= 6), and GT = 16, TL = 4, one group for <= 64
+// (D <= 8). Arithmetic in F: fp32 (split-precision contexts, ~1e-7 relative
+// like the bf16x3 products) or fp64.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -21,16 +26,14 @@ namespace ctm {
 
 namespace {
 
-constexpr int GROUP = 144;      // threads per (t, n) pair: 12 x 12
-constexpr int TILE = 3;         // register tile per thread
-constexpr int MAXD2 = 36;       // Dk^2, Db^2 <= 12 * TILE
+constexpr size_t SMEM_MAX = 227 * 1024;   // shared memory of one block
 
-__device__ __forceinline__ float cvt(double a, float) { return (float)a; }
-__device__ __forceinline__ float2 cvt(cplx a, float2) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ float cvt(double a, float) { return f32_of(a); }
+__device__ __forceinline__ float2 cvt(cplx a, float2) { return make_float2(f32_of(a.x), f32_of(a.y)); }
 __device__ __forceinline__ double cvt(double a, double) { return a; }
 __device__ __forceinline__ cplx cvt(cplx a, cplx) { return a; }
-__device__ __forceinline__ double back(float a) { return (double)a; }
-__device__ __forceinline__ cplx back(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ double back(float a) { return f64_of(a); }
+__device__ __forceinline__ cplx back(float2 a) { return make_double2(f64_of(a.x), f64_of(a.y)); }
 __device__ __forceinline__ double back(double a) { return a; }
 __device__ __forceinline__ cplx back(cplx a) { return a; }
 
@@ -49,12 +52,18 @@ template <> __device__ __forceinline__ float2 fz<float2>() { return make_float2(
 template <> __device__ __forceinline__ double fz<double>() { return 0.0; }
 template <> __device__ __forceinline__ cplx fz<cplx>() { return make_double2(0.0, 0.0); }
 
-template <typename T, typename F>
-__global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, int Db, int d,
-                                                               const T* __restrict__ In,
-                                                               const T* __restrict__ A,
-                                                               const T* __restrict__ B,
-                                                               T* __restrict__ Out) {
+// two blocks per SM where their shared memory allows (two groups, 8-byte F)
+template <typename F, int NG>
+constexpr int ab_min_blocks() {
+  return (NG == 2 && sizeof(F) <= 8) ? 2 : 1;
+}
+
+template <typename T, typename F, int GT, int TL, int NG>
+__global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
+    absorb_ab_kernel(int chi, int Dk, int Db, int d, const T* __restrict__ In,
+                     const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Out) {
+  constexpr int GROUP = GT * GT;   // threads per (t, n) pair
+  constexpr int TILE = TL;         // register tile per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K1 = Dk * Dk, N1 = Db * Db;          // (u,l) and (w,v); M1 = K1 rows (d,e)
   F* As = reinterpret_cast<F*>(smem_raw);         // [d][(d,e)][(u,l)]
@@ -62,7 +71,7 @@ __global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, i
   const int grp = threadIdx.x / GROUP, lt = threadIdx.x % GROUP;
   F* Xs = Bs + (size_t)d * N1 * N1 + (size_t)grp * 2 * K1 * N1;   // [(u,l)][(w,v)]
   F* Ys = Xs + (size_t)K1 * N1;                                   // [(d,e)][(w,v)], then Out
-  const int ti = lt / 12, tj = lt % 12;
+  const int ti = lt / GT, tj = lt % GT;
   for (int i = threadIdx.x; i < d * K1 * K1; i += blockDim.x) {
     // As[s][(d,e)][(u,l)] = A[s,u,l,d,e]
     const int s = i / (K1 * K1), rem = i % (K1 * K1);
@@ -79,7 +88,7 @@ __global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, i
   }
   const size_t row = (size_t)chi * Dk * Db;       // stride of the (first chi, Dk, Db) index
   const long npairs = (long)chi * chi;
-  for (long p0 = 2L * blockIdx.x; p0 < npairs; p0 += 2L * gridDim.x) {
+  for (long p0 = (long)NG * blockIdx.x; p0 < npairs; p0 += (long)NG * gridDim.x) {
     const long p = p0 + grp;
     const bool live = p < npairs;
     const int t = live ? (int)(p / chi) : 0, n = live ? (int)(p % chi) : 0;
@@ -112,12 +121,12 @@ __global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, i
           F xa[TILE], xb[TILE];
 #pragma unroll
           for (int a = 0; a < TILE; ++a) {
-            const int r = ti * TILE + a;
+            const int r = ti + GT * a;
             xa[a] = r < K1 ? Asb[r * K1 + kk] : fz<F>();
           }
 #pragma unroll
           for (int b = 0; b < TILE; ++b) {
-            const int c = tj * TILE + b;
+            const int c = tj + GT * b;
             xb[b] = c < N1 ? Xs[kk * N1 + c] : fz<F>();
           }
 #pragma unroll
@@ -129,7 +138,7 @@ __global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, i
         for (int a = 0; a < TILE; ++a)
 #pragma unroll
           for (int b = 0; b < TILE; ++b) {
-            const int r = ti * TILE + a, c = tj * TILE + b;
+            const int r = ti + GT * a, c = tj + GT * b;
             if (r < K1 && c < N1) Ys[r * N1 + c] = y[a][b];
           }
       }
@@ -140,12 +149,12 @@ __global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, i
           F ya[TILE], bb[TILE];
 #pragma unroll
           for (int a = 0; a < TILE; ++a) {
-            const int r = ti * TILE + a;
+            const int r = ti + GT * a;
             ya[a] = r < K1 ? Ys[r * N1 + kk] : fz<F>();
           }
 #pragma unroll
           for (int b = 0; b < TILE; ++b) {
-            const int c = tj * TILE + b;
+            const int c = tj + GT * b;
             bb[b] = c < N1 ? Bsb[kk * N1 + c] : fz<F>();
           }
 #pragma unroll
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, i
       for (int a = 0; a < TILE; ++a)
 #pragma unroll
         for (int b = 0; b < TILE; ++b) {
-          const int r = ti * TILE + a, c = tj * TILE + b;
+          const int r = ti + GT * a, c = tj + GT * b;
           if (r < K1 && c < N1) Ys[r * N1 + c] = acc[a][b];
         }
     }
@@ -178,45 +187,70 @@ __global__ void __launch_bounds__(2 * GROUP) absorb_ab_kernel(int chi, int Dk, i
   }
 }
 
-template <typename T, typename F>
+// shared memory of a geometry with ng groups: A and B, then X and Y per group
+size_t ab_smem(int Dk, int Db, int d, int ng, size_t fsize) {
+  const size_t K1 = (size_t)Dk * Dk, N1 = (size_t)Db * Db;
+  return ((size_t)d * K1 * K1 + (size_t)d * N1 * N1 + 2 * (size_t)ng * K1 * N1) * fsize;
+}
+
+// 0: no fused kernel, 1: 12 x 12 threads x 3 x 3 tiles, two groups (D <= 6),
+// 2: 16 x 16 threads x 4 x 4 tiles, one group (D <= 8)
+int ab_geometry(int Dk, int Db, int d, size_t fsize) {
+  if (Dk < 1 || Db < 1 || d < 1) return 0;
+  const int m = std::max(Dk * Dk, Db * Db);
+  if (m <= 36 && ab_smem(Dk, Db, d, 2, fsize) <= SMEM_MAX) return 1;
+  if (m <= 64 && ab_smem(Dk, Db, d, 1, fsize) <= SMEM_MAX) return 2;
+  return 0;
+}
+
+template <typename T, typename F, int GT, int TL, int NG>
 cudaError_t launch_ab(int chi, int Dk, int Db, int d, const void* In, const void* A,
                       const void* B, void* Out, int num_sms, cudaStream_t s) {
-  const int K1 = Dk * Dk, N1 = Db * Db;
-  const size_t shm = ((size_t)d * K1 * K1 + (size_t)d * N1 * N1 + 4 * (size_t)K1 * N1) * sizeof(F);
+  const size_t shm = ab_smem(Dk, Db, d, NG, sizeof(F));
   static size_t configured = 0;
-  cudaError_t e = raise_smem((const void*)absorb_ab_kernel<T, F>, configured, shm);
+  cudaError_t e = raise_smem((const void*)absorb_ab_kernel<T, F, GT, TL, NG>, configured, shm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, absorb_ab_kernel<T, F>,
-                                                                2 * GROUP, shm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, absorb_ab_kernel<T, F, GT, TL, NG>,
+                                                    NG * GT * GT, shm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long grid = (long)num_sms * per_sm;
-  const long tiles = ((long)chi * chi + 1) / 2;
+  const long tiles = ((long)chi * chi + NG - 1) / NG;
   if (grid > tiles) grid = tiles;
-  absorb_ab_kernel<T, F><<<(unsigned)grid, 2 * GROUP, shm, s>>>(
+  absorb_ab_kernel<T, F, GT, TL, NG><<<(unsigned)grid, NG * GT * GT, shm, s>>>(
       chi, Dk, Db, d, static_cast<const T*>(In), static_cast<const T*>(A),
       static_cast<const T*>(B), static_cast<T*>(Out));
   return cudaGetLastError();
 }
 
+template <typename T, typename F>
+cudaError_t launch_geom(int geom, int chi, int Dk, int Db, int d, const void* In, const void* A,
+                        const void* B, void* Out, int num_sms, cudaStream_t s) {
+  if (geom == 1) return launch_ab<T, F, 12, 3, 2>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  return launch_ab<T, F, 16, 4, 1>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+}
+
+size_t elem_size(bool cx, bool fp32) { return (cx ? 2 : 1) * (fp32 ? 4 : 8); }
+
 }  // namespace
 
-bool absorb_ab_supported(int Dk, int Db, int d) {
-  return Dk >= 1 && Db >= 1 && d >= 1 && Dk * Dk <= MAXD2 && Db * Db <= MAXD2 && d <= 4;
+bool absorb_ab_supported(bool cx, bool fp32, int Dk, int Db, int d) {
+  return ab_geometry(Dk, Db, d, elem_size(cx, fp32)) != 0;
 }
 
 cudaError_t absorb_ab(bool cx, bool fp32, int chi, int Dk, int Db, int d, const void* In,
                       const void* A, const void* B, void* Out, int num_sms, cudaStream_t s,
                       long* launches) {
-  if (!absorb_ab_supported(Dk, Db, d) || chi < 1) return cudaErrorInvalidValue;
+  const int geom = ab_geometry(Dk, Db, d, elem_size(cx, fp32));
+  if (geom == 0 || chi < 1) return cudaErrorInvalidValue;
   cudaError_t e;
   if (cx)
-    e = fp32 ? launch_ab<cplx, float2>(chi, Dk, Db, d, In, A, B, Out, num_sms, s)
-             : launch_ab<cplx, cplx>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+    e = fp32 ? launch_geom<cplx, float2>(geom, chi, Dk, Db, d, In, A, B, Out, num_sms, s)
+             : launch_geom<cplx, cplx>(geom, chi, Dk, Db, d, In, A, B, Out, num_sms, s);
   else
-    e = fp32 ? launch_ab<double, float>(chi, Dk, Db, d, In, A, B, Out, num_sms, s)
-             : launch_ab<double, double>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+    e = fp32 ? launch_geom<double, float>(geom, chi, Dk, Db, d, In, A, B, Out, num_sms, s)
+             : launch_geom<double, double>(geom, chi, Dk, Db, d, In, A, B, Out, num_sms, s);
   if (launches) ++*launches;
   return e;
 }

@@ -6,10 +6,73 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstring>
 
 namespace ctm {
 
 typedef double2 cplx;
+
+// fp64 <-> fp32 conversions on the integer pipes, from the IEEE 754 binary64
+// and binary32 layouts: the hardware conversions issue on this GPU's narrow
+// fp64 pipe (about 1.6 operations per clock per SM), which bounds kernels that
+// convert every element (operand slicing, the fused absorption, split-K
+// reduction). Round to nearest even; results below the fp32 normal range
+// (|x| < 2^-126) become a signed zero; inf and NaN are kept.
+__host__ __device__ __forceinline__ float f32_of(double x) {
+#ifdef __CUDA_ARCH__
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+#else
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+#endif
+  const unsigned sign = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);   // the 23 kept bits
+  const unsigned rest = lo & 0x1fffffffu;                       // the 29 dropped bits
+  const int e = (int)ex - 1023 + 127;
+  unsigned bits;
+  if (ex == 0x7ffu) {
+    bits = 0x7f800000u | ((mant | rest) ? 0x400000u : 0u);
+  } else if (e >= 255) {
+    bits = 0x7f800000u;
+  } else if (e <= 0) {
+    bits = 0u;
+  } else {
+    bits = ((unsigned)e << 23) | mant;
+    // a carry out of the mantissa correctly bumps the exponent (to inf at most)
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  }
+  bits |= sign;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(bits);
+#else
+  float f;
+  memcpy(&f, &bits, 4);
+  return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ double f64_of(float f) {
+#ifdef __CUDA_ARCH__
+  const unsigned u = __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, 4);
+#endif
+  const unsigned sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, mant = u & 0x7fffffu;
+  unsigned hi = sign;
+  const unsigned lo = ex == 0u ? 0u : mant << 29;
+  if (ex == 0xffu) hi |= 0x7ff00000u | (mant >> 3);
+  else if (ex != 0u) hi |= ((ex + 1023u - 127u) << 20) | (mant >> 3);   // (zero: +-0)
+#ifdef __CUDA_ARCH__
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  const uint64_t b = ((uint64_t)hi << 32) | lo;
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+#endif
+}
 
 // ---------------------------------------------------------------- scalars
 __host__ __device__ __forceinline__ double zero_of(double) { return 0.0; }

@@ -484,7 +484,7 @@ ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
   CK(ein(c, "pm,mnuv->pnuv", tn(Cc, {chi, chi}), false, tn(Ta, {chi, chi, Dk, Db}), false, CT));
   Tn CTT = tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db});
   CK(ein(c, "tplw,pnuv->tlwnuv", tn(Tb, {chi, chi, Dk, Db}), false, CT, false, CTT));
-  if (absorb_ab_supported((int)Dk, (int)Db, (int)d)) {
+  if (absorb_ab_supported(c->cx, c->split != nullptr, (int)Dk, (int)Db, (int)d)) {
     // A and B in one pass over the block (fp32 arithmetic in split contexts)
     CTM_CUDA_OK(absorb_ab(c->cx, c->split != nullptr, (int)chi, (int)Dk, (int)Db, (int)d, CTT.p,
                           A, B, Qout, c->num_sms, c->stream, &c->launches));
@@ -779,7 +779,7 @@ ctm_status absorb_site(ctm_ctx* c, int r, int x, int y, int Lyf) {
   CK(ein(c, "tndD,ndDc->tc", E4, false, tn(Pl_dn, {chi, Dk, Db, chi}), false,
          tn(oC4, {chi, chi})));
   // T4'
-  if (absorb_ab_supported((int)Dk, (int)Db, (int)d)) {
+  if (absorb_ab_supported(c->cx, c->split != nullptr, (int)Dk, (int)Db, (int)d)) {
     Tn Y1 = tn(c->pipe[0], {chi, Dk, Db, chi, Dk, Db});
     CK(ein(c, "tqlw,quvc->tlwcuv", tn(T4, {chi, chi, Dk, Db}), false,
            tn(Pl_up, {chi, Dk, Db, chi}), false, Y1));
@@ -1008,15 +1008,17 @@ ctm_status upload_default_state(ctm_ctx* c) {
       const double inv = 1.0 / std::sqrt(s2);
       for (size_t i = 0; i < n * per; ++i) h[t * n * per + i] *= inv;
     }
-    CTM_CUDA_OK(cudaMemcpy(kind == 0 ? c->C : c->T, h.data(), h.size() * sizeof(double),
-                           cudaMemcpyHostToDevice));
+    CTM_CUDA_OK(cudaMemcpyAsync(kind == 0 ? c->C : c->T, h.data(), h.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream));
   }
   const size_t nrf = (size_t)4 * c->S * c->N * c->k * per;
   h.assign(nrf, 0.0);
   fill_normal(h, c->opts.seed, 3, sc);
-  CTM_CUDA_OK(cudaMemcpy(c->X, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice));
+  CTM_CUDA_OK(cudaMemcpyAsync(c->X, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice,
+                              c->stream));
   fill_normal(h, c->opts.seed, 4, sc);
-  CTM_CUDA_OK(cudaMemcpy(c->W, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice));
+  CTM_CUDA_OK(cudaMemcpyAsync(c->W, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice,
+                              c->stream));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
   c->spectra_init = false;
   for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
@@ -1133,19 +1135,24 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->dsc, k * sizeof(double));
   AL(c->fac, Lmax * es);
 #undef AL
-  if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess)
+  // every upload goes through the context's stream: a copy on the legacy
+  // default stream is not ordered before kernels on a non-blocking stream
+  if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess)
     return bail(fail(c, CTM_ECUDA, "cudaMemset failed"));
   c->rf_ready.assign(4 * S, 0);
   // tensors: upload rotation 0, derive the other three on the device
   for (int i = 0; i < c->S; ++i) {
-    if (cudaMemcpy(at(c->ket[0], i * nk, c), kets[i], nk * es, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpyAsync(at(c->ket[0], i * nk, c), kets[i], nk * es, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
       return bail(fail(c, CTM_ECUDA, "upload of A failed"));
     if (classical) {
       const double one[2] = {1.0, 0.0};
-      if (cudaMemcpy(at(c->bra[0], i * nb, c), one, es, cudaMemcpyHostToDevice) != cudaSuccess)
+      if (cudaMemcpyAsync(at(c->bra[0], i * nb, c), one, es, cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess)
         return bail(fail(c, CTM_ECUDA, "upload of B failed"));
     } else if (bras) {
-      if (cudaMemcpy(at(c->bra[0], i * nb, c), bras[i], nb * es, cudaMemcpyHostToDevice) != cudaSuccess)
+      if (cudaMemcpyAsync(at(c->bra[0], i * nb, c), bras[i], nb * es, cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess)
         return bail(fail(c, CTM_ECUDA, "upload of B failed"));
     } else {
       const long dims1[1] = {(long)nk};
@@ -1205,8 +1212,9 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       // a lane only builds corners and runs the SI round: its pipelines hold
       // N^2 elements (d N^2 for the unfused absorption), not the d^2 N^2 of
       // the two-site observables of lane 0
-      const size_t laneT =
-          (size_t)(absorb_ab_supported((int)Dk, (int)Db, d) ? 1 : d) * NN + 64;
+      const bool fused = absorb_ab_supported(cx, c->opts.prec == CTM_PREC_SPLIT_BF16, (int)Dk,
+                                             (int)Db, d);
+      const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
       M.scratch_bytes = 2 * laneT * es + ((size_t)64 << 20);
       for (int q = 0; q < 4; ++q)
         if ((st = dalloc(c, &M.Q[q], NN * es)) != CTM_OK) return bail(st);
@@ -1469,7 +1477,8 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
   if (o->method == CTM_PROJ_SVD) b += 3 * NN * es + 2 * N * chi * es + (size_t)64 * N * es;
   if (o->method == CTM_PROJ_SI) {
     // lanes 1 .. nl-1: corners, pipes, scratch, N x k blocks, QR work, split state
-    const size_t laneT = (size_t)(absorb_ab_supported(Dk, Db, d) ? 1 : d) * NN + 64;
+    const bool fused = absorb_ab_supported(cx, o->prec == CTM_PREC_SPLIT_BF16, Dk, Db, d);
+    const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
     size_t lane = 4 * NN * es + 4 * laneT * es + ((size_t)64 << 20) + 4 * N * k * es +
                   2 * k * k * es + 12 * k;
     if (o->prec == CTM_PREC_SPLIT_BF16) {

@@ -6,11 +6,13 @@
 // GB300 has ~6.6 fp64 GFLOP/s per SM, so one block per matrix is bounded by a
 // single SM's fp64 units (a 149 x 149 complex sweep is ~1.2e8 flops). Here
 // the k/2 disjoint column pairs of each round-robin round are shared by the
-// warps of G blocks on G SMs; columns of A and V live in global memory (L2
-// resident, accessed with .cg loads and stores that bypass the incoherent
-// L1) and rounds are separated by a grid barrier. The barrier spins are
-// bounded (2 s of %globaltimer); a timeout sets DEV_MBAR_TIMEOUT and a global
-// abort flag after which every block leaves.
+// warps of G blocks on G SMs, one pair per warp; columns of A and V live in
+// global memory (L2 resident, accessed with .cg loads and stores that bypass
+// the incoherent L1). A pair waits only for the two pairs of the previous
+// round that wrote its columns (per-column version counters, release /
+// acquire), and grid barriers separate the sweeps. Every wait is bounded
+// (2 s of %globaltimer); a timeout sets DEV_MBAR_TIMEOUT and a global abort
+// flag after which every block leaves.
 //
 // Result: A = U diag(s) V^H with s descending (ties keep the lower column
 // first); exactly-zero columns of U are completed to a unitary by
@@ -110,25 +112,27 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// lane 0 waits until columns p and q (q < 0: none) have been through round
-// r; bounded like the grid barrier (abort flag, 2 s). Returns false on abort.
+// the warp waits until columns p and q (q < 0: none) have been through
+// round r; every lane polls with acquire loads, so each lane's later reads of
+// the columns are ordered after the release that published them. Bounded
+// like the grid barrier (abort flag, 2 s, decided by lane 0). Returns false
+// on abort.
 __device__ bool wait_columns(const unsigned* ver, int p, int q, unsigned r, unsigned* bar,
                              int* err, int lane) {
-  int ok = 1;
-  if (lane == 0) {
-    unsigned* abrt = bar + 64;
-    const uint64_t t0 = gtime();
-    unsigned polls = 0;
-    while (ld_acquire(ver + p) != r || (q >= 0 && ld_acquire(ver + q) != r)) {
-      if ((++polls & 63u) == 0 && (ld_acquire(abrt) || gtime() - t0 > 2000000000ull)) {
-        atomicExch(abrt, 1u);
-        atomicOr(err, DEV_MBAR_TIMEOUT);
-        ok = 0;
-        break;
-      }
+  unsigned* abrt = bar + 64;
+  const uint64_t t0 = gtime();
+  unsigned polls = 0;
+  while (true) {
+    const bool ready = ld_acquire(ver + p) == r && (q < 0 || ld_acquire(ver + q) == r);
+    if (__all_sync(0xffffffffu, ready)) return true;
+    int stop = 0;
+    if (lane == 0 && (++polls & 63u) == 0 && (ld_acquire(abrt) || gtime() - t0 > 2000000000ull)) {
+      atomicExch(abrt, 1u);
+      atomicOr(err, DEV_MBAR_TIMEOUT);
+      stop = 1;
     }
+    if (__shfl_sync(0xffffffffu, stop, 0)) return false;
   }
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __forceinline__ int player(int pos, int t, int m) {

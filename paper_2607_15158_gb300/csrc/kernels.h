@@ -81,8 +81,10 @@ cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, cons
 // Out[t,d,D,n,e,E] = sum A[s,u,l,d,e] B[s,v,w,D,E] In[t,l,w,n,u,v] with In,
 // Out [chi, Dk, Db, chi, Dk, Db] (single-layer absorption of the ket and bra
 // tensors into an enlarged corner or edge); fp32 arithmetic when fp32.
-// Supported for Dk, Db <= 6 and d <= 4 (absorb_ab_supported).
-bool absorb_ab_supported(int Dk, int Db, int d);
+// Supported for Dk, Db <= 8 when A, B and the per-pair tiles fit in one
+// block's shared memory (absorb_ab_supported; e.g. D <= 6 for any
+// precision at d = 2, D = 7, 8 at d = 2 in fp32 or real fp64).
+bool absorb_ab_supported(bool cx, bool fp32, int Dk, int Db, int d);
 cudaError_t absorb_ab(bool cx, bool fp32, int chi, int Dk, int Db, int d, const void* In,
                       const void* A, const void* B, void* Out, int num_sms, cudaStream_t s,
                       long* launches);

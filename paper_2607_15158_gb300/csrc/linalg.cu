@@ -671,7 +671,9 @@ __global__ void __launch_bounds__(1024, 1) trsm_warp_kernel(long rows, int k, co
     }
   }
   __syncthreads();
-  for (long r = (long)blockIdx.x * nw + wp; r < rows; r += (long)gridDim.x * nw) {
+  // row r = wp G + b + t G nw: a partial last pass over the rows spreads
+  // over all blocks (a few warps each) instead of filling a few blocks
+  for (long r = (long)wp * gridDim.x + blockIdx.x; r < rows; r += (long)gridDim.x * nw) {
     const T* z = Z + r * k;
     T a[R];
 #pragma unroll

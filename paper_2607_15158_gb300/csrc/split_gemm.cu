@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(128, 1)
 // value: GB300's fp64 pipe is ~60x narrower than its fp32 pipe.
 __device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat16& s1,
                                        __nv_bfloat16& s2) {
-  const float xf = __double2float_rn(x);
+  const float xf = f32_of(x);   // integer pipes, not the narrow fp64 pipe
   s0 = __float2bfloat16_rn(xf);
   const float r1 = xf - __bfloat162float(s0);
   s1 = __float2bfloat16_rn(r1);
@@ -403,7 +403,20 @@ __global__ void prep_b_kernel(const T* B, long ldb, int op, int K, int N, int Kp
   }
 }
 
-// C[m][j] = sum over splits of the partials (fp64), complex from [C_r | C_i]
+// error-free sum of two fp32 values (Knuth's TwoSum): hi + lo == a + b
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += e;
+}
+
+// C[m][j] = sum over splits of the partials, complex from [C_r | C_i]. The
+// sum is carried as an unevaluated fp32 pair (TwoSum on the fp32 pipe) and
+// converted to fp64 once, because this GPU's fp64 pipe (conversions and
+// additions alike) would bound the kernel; the pair is exact up to the
+// rounding of its low part, ~2^-48 relative.
 template <typename T>
 __global__ void reduce_kernel(const float* part, int nks, int M, int N, int Np, T* C, long ldc) {
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)M * N;
@@ -411,7 +424,7 @@ __global__ void reduce_kernel(const float* part, int nks, int M, int N, int Np, 
     const int m = (int)(idx / N), j = (int)(idx % N);
     const float* row = part + (size_t)m * Np + j;
     const size_t sstep = (size_t)M * Np;
-    double re = 0.0, im = 0.0;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     int s = 0;
     // four splits' loads in flight at a time (the sum keeps the split order)
     for (; s + 4 <= nks; s += 4) {
@@ -423,15 +436,16 @@ __global__ void reduce_kernel(const float* part, int nks, int M, int N, int Np, 
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        re += (double)a[u];
-        if constexpr (sizeof(T) == 16) im += (double)b[u];
+        two_sum_acc(rh, rl, a[u]);
+        if constexpr (sizeof(T) == 16) two_sum_acc(ih, il, b[u]);
       }
     }
     for (; s < nks; ++s) {
-      re += (double)__ldcs(row + s * sstep);
-      if constexpr (sizeof(T) == 16) im += (double)__ldcs(row + s * sstep + N);
+      two_sum_acc(rh, rl, __ldcs(row + s * sstep));
+      if constexpr (sizeof(T) == 16) two_sum_acc(ih, il, __ldcs(row + s * sstep + N));
     }
-    if constexpr (sizeof(T) == 16) C[(long)m * ldc + j] = make_double2(re, im);
+    const double re = f64_of(rh) + f64_of(rl);
+    if constexpr (sizeof(T) == 16) C[(long)m * ldc + j] = make_double2(re, f64_of(ih) + f64_of(il));
     else C[(long)m * ldc + j] = re;
   }
 }

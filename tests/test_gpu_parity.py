@@ -119,9 +119,11 @@ def test_single_moves_each_direction():
     # shared memory, so the QR passes take the cooperative Cholesky with an
     # explicit inverse, and the Jacobi SVD nine columns per lane
     (1, 1, 2, 2, 170, 5, True, 1),
-    # D = 7 (D^2 = 49 > 36): the enlarged corners and the site absorption run
-    # unfused, as two GEMMs with permutes in between
+    # D = 7 complex fp64: A, B and the 49 x 49 pair tiles exceed one block's
+    # shared memory, so the absorption runs unfused (two GEMMs, permutes)
     (1, 1, 2, 7, 4, 3, True, 1),
+    # D = 7 real fp64: the fused absorption with 16 x 16 threads, 4 x 4 tiles
+    (1, 1, 2, 7, 4, 3, False, 1),
 ])
 def test_large_block_and_unfused_absorption_track_oracle(case):
     Lx, Ly, d, D, chi, p, cplx, rounds = case

@@ -42,7 +42,8 @@ def _spectra(ctx):
     (1, 1, 2, 2, 8, 5, False, 1),
     (2, 1, 2, 3, 10, 5, True, 1),        # N = 90 complex: ragged tiles
     (1, 1, 2, 4, 12, 5, True, 1),        # N = 192: two 128-row tiles
-    (1, 1, 2, 7, 6, 5, True, 1),         # D = 7: unfused absorption as split GEMMs
+    (1, 1, 2, 7, 6, 5, True, 1),         # D = 7: fused absorption, 16 x 16 threads
+    (1, 1, 2, 8, 3, 3, True, 1),         # D = 8: the same geometry at 64 x 64 tiles
     (1, 1, 2, 2, 170, 5, True, 1),       # k = 175: cooperative Cholesky, split 2nd pass
 ])
 def test_one_move_split_matches_fp64(case):
