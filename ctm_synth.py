@@ -184,6 +184,11 @@ WORKLOADS = {
     # size whose working set (~1.5 GB) suits a full counter capture
     "small_1x1_D4_chi100_c128": dict(Lx=1, Ly=1, d=2, D=4, chi=100, p=5, complex_=True,
                                      diag_weight=0.0, si_rounds=1),
+    # 1x1 cell, complex A[2,6,...], chi = 80 (N = 2880): the D = 6 fused
+    # absorption at a size suited to a full counter capture (its 133 MB input
+    # block exceeds L2)
+    "small_1x1_D6_chi80_c128": dict(Lx=1, Ly=1, d=2, D=6, chi=80, p=5, complex_=True,
+                                    diag_weight=0.0, si_rounds=1),
     # 1x1 cell, real A[2,5,...], chi = 100 (differentiation workload shape)
     "cfg5_1x1_D5_chi100": dict(Lx=1, Ly=1, d=2, D=5, chi=100, p=5,
                                complex_=False, diag_weight=0.0, si_rounds=1),

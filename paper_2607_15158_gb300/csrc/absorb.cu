@@ -28,12 +28,15 @@ namespace {
 
 constexpr size_t SMEM_MAX = 227 * 1024;   // shared memory of one block
 
-__device__ __forceinline__ float cvt(double a, float) { return f32_of(a); }
-__device__ __forceinline__ float2 cvt(cplx a, float2) { return make_float2(f32_of(a.x), f32_of(a.y)); }
+// hardware conversions here: they issue on the narrow fp64 pipe, but that
+// pipe is otherwise idle in this kernel and other warps' fp32 work covers
+// them (the integer-pipe conversions of common.cuh measured 12 % slower)
+__device__ __forceinline__ float cvt(double a, float) { return (float)a; }
+__device__ __forceinline__ float2 cvt(cplx a, float2) { return make_float2((float)a.x, (float)a.y); }
 __device__ __forceinline__ double cvt(double a, double) { return a; }
 __device__ __forceinline__ cplx cvt(cplx a, cplx) { return a; }
-__device__ __forceinline__ double back(float a) { return f64_of(a); }
-__device__ __forceinline__ cplx back(float2 a) { return make_double2(f64_of(a.x), f64_of(a.y)); }
+__device__ __forceinline__ double back(float a) { return (double)a; }
+__device__ __forceinline__ cplx back(float2 a) { return make_double2((double)a.x, (double)a.y); }
 __device__ __forceinline__ double back(double a) { return a; }
 __device__ __forceinline__ cplx back(cplx a) { return a; }
 
@@ -52,13 +55,31 @@ template <> __device__ __forceinline__ float2 fz<float2>() { return make_float2(
 template <> __device__ __forceinline__ double fz<double>() { return 0.0; }
 template <> __device__ __forceinline__ cplx fz<cplx>() { return make_double2(0.0, 0.0); }
 
+// asynchronous global -> shared copies of one input element (Ampere+ cp.async)
+__device__ __forceinline__ void cp_async_elem(cplx* dst, const cplx* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // two blocks per SM where their shared memory allows (two groups, 8-byte F)
 template <typename F, int NG>
 constexpr int ab_min_blocks() {
   return (NG == 2 && sizeof(F) <= 8) ? 2 : 1;
 }
 
-template <typename T, typename F, int GT, int TL, int NG>
+// ST: the next pair's input block is copied into a staging buffer with
+// cp.async while the current pair is computed (fp32 arithmetic, D <= 6)
+template <typename T, typename F, int GT, int TL, int NG, bool ST>
 __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
     absorb_ab_kernel(int chi, int Dk, int Db, int d, const T* __restrict__ In,
                      const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Out) {
@@ -72,6 +93,13 @@ __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
   F* Xs = Bs + (size_t)d * N1 * N1 + (size_t)grp * 2 * K1 * N1;   // [(u,l)][(w,v)]
   F* Ys = Xs + (size_t)K1 * N1;                                   // [(d,e)][(w,v)], then Out
   const int ti = lt / GT, tj = lt % GT;
+  // staging buffers (raw input elements, 16-byte aligned) after all groups' X, Y
+  T* St = nullptr;
+  if constexpr (ST) {
+    const uintptr_t end = reinterpret_cast<uintptr_t>(Bs + (size_t)d * N1 * N1 +
+                                                      (size_t)NG * 2 * K1 * N1);
+    St = reinterpret_cast<T*>((end + 15) & ~(uintptr_t)15) + (size_t)grp * K1 * N1;
+  }
   for (int i = threadIdx.x; i < d * K1 * K1; i += blockDim.x) {
     // As[s][(d,e)][(u,l)] = A[s,u,l,d,e]
     const int s = i / (K1 * K1), rem = i % (K1 * K1);
@@ -88,19 +116,47 @@ __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
   }
   const size_t row = (size_t)chi * Dk * Db;       // stride of the (first chi, Dk, Db) index
   const long npairs = (long)chi * chi;
+  // element i = (l w, u v) of pair pp's block: In[t,l,w,n,u,v], runs of Dk Db
+  // contiguous (u, v)
+  auto src_of = [&](long pp, int i) {
+    const int tt = (int)(pp / chi), nn = (int)(pp % chi);
+    const int lw = i / (Dk * Db), uv = i % (Dk * Db);
+    const int l = lw / Db, w = lw % Db;
+    return In + ((size_t)tt * Dk + l) * Db * row + (size_t)w * row + (size_t)nn * Dk * Db + uv;
+  };
+  if constexpr (ST) {
+    const long pf = (long)NG * blockIdx.x + grp;
+    if (pf < npairs)
+      for (int i = lt; i < K1 * N1; i += GROUP) cp_async_elem(St + i, src_of(pf, i));
+    cp_async_commit();
+  }
   for (long p0 = (long)NG * blockIdx.x; p0 < npairs; p0 += (long)NG * gridDim.x) {
     const long p = p0 + grp;
     const bool live = p < npairs;
     const int t = live ? (int)(p / chi) : 0, n = live ? (int)(p % chi) : 0;
-    __syncthreads();   // previous pair's output staging is consumed
-    if (live) {
-      // X[(u,l),(w,v)] = In[t,l,w,n,u,v]: runs of Dk Db contiguous (u, v)
-      for (int i = lt; i < K1 * N1; i += GROUP) {
-        const int lw = i / (Dk * Db), uv = i % (Dk * Db);
-        const int l = lw / Db, w = lw % Db, u = uv / Db, v = uv % Db;
-        Xs[(u * Dk + l) * N1 + w * Db + v] =
-            cvt(In[((size_t)t * Dk + l) * Db * row + (size_t)w * row + (size_t)n * Dk * Db + uv],
-                F());
+    if constexpr (ST) {
+      cp_async_wait_all();
+      __syncthreads();   // staged blocks complete; previous output staging consumed
+      if (live)
+        for (int i = lt; i < K1 * N1; i += GROUP) {
+          const int lw = i / (Dk * Db), uv = i % (Dk * Db);
+          const int l = lw / Db, w = lw % Db, u = uv / Db, v = uv % Db;
+          Xs[(u * Dk + l) * N1 + w * Db + v] = cvt(St[i], F());
+        }
+      __syncthreads();   // the staging buffers are free again
+      const long pn = p + (long)NG * gridDim.x;
+      if (pn < npairs)
+        for (int i = lt; i < K1 * N1; i += GROUP) cp_async_elem(St + i, src_of(pn, i));
+      cp_async_commit();
+    } else {
+      __syncthreads();   // previous pair's output staging is consumed
+      if (live) {
+        // X[(u,l),(w,v)] = In[t,l,w,n,u,v]
+        for (int i = lt; i < K1 * N1; i += GROUP) {
+          const int lw = i / (Dk * Db), uv = i % (Dk * Db);
+          const int l = lw / Db, w = lw % Db, u = uv / Db, v = uv % Db;
+          Xs[(u * Dk + l) * N1 + w * Db + v] = cvt(*src_of(p, i), F());
+        }
       }
     }
     F acc[TILE][TILE];
@@ -187,48 +243,57 @@ __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
   }
 }
 
-// shared memory of a geometry with ng groups: A and B, then X and Y per group
-size_t ab_smem(int Dk, int Db, int d, int ng, size_t fsize) {
+// shared memory of a geometry with ng groups: A and B, then X and Y per
+// group, then (staged) one raw input block per group
+size_t ab_smem(int Dk, int Db, int d, int ng, size_t fsize, size_t tsize, bool staged) {
   const size_t K1 = (size_t)Dk * Dk, N1 = (size_t)Db * Db;
-  return ((size_t)d * K1 * K1 + (size_t)d * N1 * N1 + 2 * (size_t)ng * K1 * N1) * fsize;
+  size_t b = ((size_t)d * K1 * K1 + (size_t)d * N1 * N1 + 2 * (size_t)ng * K1 * N1) * fsize;
+  if (staged) b = (b + 15) / 16 * 16 + (size_t)ng * K1 * N1 * tsize;
+  return b;
 }
 
-// 0: no fused kernel, 1: 12 x 12 threads x 3 x 3 tiles, two groups (D <= 6),
-// 2: 16 x 16 threads x 4 x 4 tiles, one group (D <= 8)
-int ab_geometry(int Dk, int Db, int d, size_t fsize) {
+// 0: no fused kernel; 3: 12 x 12 threads x 3 x 3 tiles, four groups with
+// staged input (fp32, D <= 6); 1: the same tiles, two groups; 2: 16 x 16
+// threads x 4 x 4 tiles, one group (D <= 8)
+int ab_geometry(int Dk, int Db, int d, size_t fsize, size_t tsize) {
   if (Dk < 1 || Db < 1 || d < 1) return 0;
   const int m = std::max(Dk * Dk, Db * Db);
-  if (m <= 36 && ab_smem(Dk, Db, d, 2, fsize) <= SMEM_MAX) return 1;
-  if (m <= 64 && ab_smem(Dk, Db, d, 1, fsize) <= SMEM_MAX) return 2;
+  if (m <= 36 && fsize < tsize && ab_smem(Dk, Db, d, 4, fsize, tsize, true) <= SMEM_MAX) return 3;
+  if (m <= 36 && ab_smem(Dk, Db, d, 2, fsize, tsize, false) <= SMEM_MAX) return 1;
+  if (m <= 64 && ab_smem(Dk, Db, d, 1, fsize, tsize, false) <= SMEM_MAX) return 2;
   return 0;
 }
 
-template <typename T, typename F, int GT, int TL, int NG>
+template <typename T, typename F, int GT, int TL, int NG, bool ST>
 cudaError_t launch_ab(int chi, int Dk, int Db, int d, const void* In, const void* A,
                       const void* B, void* Out, int num_sms, cudaStream_t s) {
-  const size_t shm = ab_smem(Dk, Db, d, NG, sizeof(F));
+  const size_t shm = ab_smem(Dk, Db, d, NG, sizeof(F), sizeof(T), ST);
   static size_t configured = 0;
-  cudaError_t e = raise_smem((const void*)absorb_ab_kernel<T, F, GT, TL, NG>, configured, shm);
+  auto* fn = absorb_ab_kernel<T, F, GT, TL, NG, ST>;
+  cudaError_t e = raise_smem((const void*)fn, configured, shm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, absorb_ab_kernel<T, F, GT, TL, NG>,
-                                                    NG * GT * GT, shm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NG * GT * GT, shm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long grid = (long)num_sms * per_sm;
   const long tiles = ((long)chi * chi + NG - 1) / NG;
   if (grid > tiles) grid = tiles;
-  absorb_ab_kernel<T, F, GT, TL, NG><<<(unsigned)grid, NG * GT * GT, shm, s>>>(
-      chi, Dk, Db, d, static_cast<const T*>(In), static_cast<const T*>(A),
-      static_cast<const T*>(B), static_cast<T*>(Out));
+  fn<<<(unsigned)grid, NG * GT * GT, shm, s>>>(chi, Dk, Db, d, static_cast<const T*>(In),
+                                                 static_cast<const T*>(A),
+                                                 static_cast<const T*>(B), static_cast<T*>(Out));
   return cudaGetLastError();
 }
 
 template <typename T, typename F>
 cudaError_t launch_geom(int geom, int chi, int Dk, int Db, int d, const void* In, const void* A,
                         const void* B, void* Out, int num_sms, cudaStream_t s) {
-  if (geom == 1) return launch_ab<T, F, 12, 3, 2>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
-  return launch_ab<T, F, 16, 4, 1>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  if constexpr (sizeof(F) < sizeof(T)) {
+    if (geom == 3)
+      return launch_ab<T, F, 12, 3, 4, true>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  }
+  if (geom == 1) return launch_ab<T, F, 12, 3, 2, false>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  return launch_ab<T, F, 16, 4, 1, false>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
 }
 
 size_t elem_size(bool cx, bool fp32) { return (cx ? 2 : 1) * (fp32 ? 4 : 8); }
@@ -236,13 +301,13 @@ size_t elem_size(bool cx, bool fp32) { return (cx ? 2 : 1) * (fp32 ? 4 : 8); }
 }  // namespace
 
 bool absorb_ab_supported(bool cx, bool fp32, int Dk, int Db, int d) {
-  return ab_geometry(Dk, Db, d, elem_size(cx, fp32)) != 0;
+  return ab_geometry(Dk, Db, d, elem_size(cx, fp32), elem_size(cx, false)) != 0;
 }
 
 cudaError_t absorb_ab(bool cx, bool fp32, int chi, int Dk, int Db, int d, const void* In,
                       const void* A, const void* B, void* Out, int num_sms, cudaStream_t s,
                       long* launches) {
-  const int geom = ab_geometry(Dk, Db, d, elem_size(cx, fp32));
+  const int geom = ab_geometry(Dk, Db, d, elem_size(cx, fp32), elem_size(cx, false));
   if (geom == 0 || chi < 1) return cudaErrorInvalidValue;
   cudaError_t e;
   if (cx)

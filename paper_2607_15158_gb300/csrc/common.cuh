@@ -15,7 +15,7 @@ typedef double2 cplx;
 // fp64 <-> fp32 conversions on the integer pipes, from the IEEE 754 binary64
 // and binary32 layouts: the hardware conversions issue on this GPU's narrow
 // fp64 pipe (about 1.6 operations per clock per SM), which bounds kernels that
-// convert every element (operand slicing, the fused absorption, split-K
+// do little else than convert every element (operand slicing, split-K
 // reduction). Round to nearest even; results below the fp32 normal range
 // (|x| < 2^-126) become a signed zero; inf and NaN are kept.
 __host__ __device__ __forceinline__ float f32_of(double x) {

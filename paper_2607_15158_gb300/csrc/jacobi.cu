@@ -139,6 +139,24 @@ __device__ __forceinline__ int player(int pos, int t, int m) {
   return pos == 0 ? 0 : ((pos - 1 + t) % m) + 1;
 }
 
+// (x, y) -> (c x - se y, s x + ce y) with se = s eph and ce = c eph folded
+// once per pair: 12 fp64 operations per complex element pair instead of 16
+// (the fp64 pipe bounds a rotation on this GPU)
+__device__ __forceinline__ double rot_lo(double x, double y, double c, double se) {
+  return fma(-se, y, c * x);
+}
+__device__ __forceinline__ double rot_hi(double x, double y, double s, double ce) {
+  return fma(ce, y, s * x);
+}
+__device__ __forceinline__ cplx rot_lo(cplx x, cplx y, double c, cplx se) {
+  return make_double2(fma(-se.x, y.x, fma(se.y, y.y, c * x.x)),
+                      fma(-se.x, y.y, fma(-se.y, y.x, c * x.y)));
+}
+__device__ __forceinline__ cplx rot_hi(cplx x, cplx y, double s, cplx ce) {
+  return make_double2(fma(ce.x, y.x, fma(-ce.y, y.y, s * x.x)),
+                      fma(ce.x, y.y, fma(ce.y, y.x, s * x.y)));
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
   // R: elements of a column held per lane (k <= 32 R); the pair's columns
@@ -239,13 +257,13 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
             T eph;   // conj(gamma) / |gamma|
             if constexpr (sizeof(T) == 8) eph = ga / gm;
             else eph = make_double2(ga.x / gm, -ga.y / gm);
+            const T se = scalev(eph, s), ce = scalev(eph, c);
 #pragma unroll
             for (int e = 0; e < R; ++e) {
               const int r = lane + 32 * e;
               if (r < k) {
-                const T x = xr[e], y = mulv(eph, yr[e]);
-                stcg(ap + r, subv(scalev(x, c), scalev(y, s)));
-                stcg(aq + r, addv(scalev(x, s), scalev(y, c)));
+                stcg(ap + r, rot_lo(xr[e], yr[e], c, se));
+                stcg(aq + r, rot_hi(xr[e], yr[e], s, ce));
               }
             }
             if (lane == 0) {
@@ -260,13 +278,13 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
                   T x, y;
                   if constexpr (kPrefetchV) {
                     x = vxr[e];
-                    y = mulv(eph, vyr[e]);
+                    y = vyr[e];
                   } else {
                     x = ldcg(vp + r);
-                    y = mulv(eph, ldcg(vq + r));
+                    y = ldcg(vq + r);
                   }
-                  stcg(vp + r, subv(scalev(x, c), scalev(y, s)));
-                  stcg(vq + r, addv(scalev(x, s), scalev(y, c)));
+                  stcg(vp + r, rot_lo(x, y, c, se));
+                  stcg(vq + r, rot_hi(x, y, s, ce));
                 }
               }
             }

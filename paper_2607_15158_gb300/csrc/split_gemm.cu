@@ -275,12 +275,17 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat1
   s2 = __float2bfloat16_rn(r2);
 }
 
-__device__ __forceinline__ void emit3(__nv_bfloat16* out, long slice, long o, double x) {
-  __nv_bfloat16 s0, s1, s2;
-  split3(x, s0, s1, s2);
+__device__ __forceinline__ void put3(__nv_bfloat16* out, long slice, long o, __nv_bfloat16 s0,
+                                     __nv_bfloat16 s1, __nv_bfloat16 s2) {
   out[o] = s0;
   out[slice + o] = s1;
   out[2 * slice + o] = s2;
+}
+
+__device__ __forceinline__ void emit3(__nv_bfloat16* out, long slice, long o, double x) {
+  __nv_bfloat16 s0, s1, s2;
+  split3(x, s0, s1, s2);
+  put3(out, slice, o, s0, s1, s2);
 }
 
 
@@ -317,7 +322,10 @@ __global__ void prep_a_kernel(const T* A, long lda, int op, int M, int K, int Kp
         const T v = tile[yy][threadIdx.x];
         if constexpr (cx) {
           emit3(out, slice, (long)m * Kp + kk, v.x);
-          emit3(out, slice, (long)m * Kp + K + kk, cj ? -v.y : v.y);
+          __nv_bfloat16 i0, i1, i2;
+          split3(v.y, i0, i1, i2);
+          if (cj) { i0 = __hneg(i0); i1 = __hneg(i1); i2 = __hneg(i2); }
+          put3(out, slice, (long)m * Kp + K + kk, i0, i1, i2);
         } else {
           emit3(out, slice, (long)m * Kp + kk, v);
         }
@@ -371,11 +379,16 @@ __global__ void prep_b_kernel(const T* B, long ldb, int op, int K, int N, int Kp
       if (jj < N && kk < K) {
         const T v = tile[threadIdx.x][yy];
         if constexpr (cx) {
-          const double re = v.x, im = cj ? -v.y : v.y;
-          emit3(out, slice, (long)jj * Kp + kk, re);
-          emit3(out, slice, (long)jj * Kp + K + kk, -im);
-          emit3(out, slice, (long)(N + jj) * Kp + kk, im);
-          emit3(out, slice, (long)(N + jj) * Kp + K + kk, re);
+          // the slices of -x are the negated slices of x: each part is
+          // sliced once
+          __nv_bfloat16 r0, r1, r2, i0, i1, i2;
+          split3(v.x, r0, r1, r2);
+          split3(v.y, i0, i1, i2);
+          if (cj) { i0 = __hneg(i0); i1 = __hneg(i1); i2 = __hneg(i2); }
+          put3(out, slice, (long)jj * Kp + kk, r0, r1, r2);
+          put3(out, slice, (long)jj * Kp + K + kk, __hneg(i0), __hneg(i1), __hneg(i2));
+          put3(out, slice, (long)(N + jj) * Kp + kk, i0, i1, i2);
+          put3(out, slice, (long)(N + jj) * Kp + K + kk, r0, r1, r2);
         } else {
           emit3(out, slice, (long)jj * Kp + kk, v);
         }
