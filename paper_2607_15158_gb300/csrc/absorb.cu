@@ -79,13 +79,17 @@ constexpr int ab_min_blocks() {
 
 // ST: the next pair's input block is copied into a staging buffer with
 // cp.async while the current pair is computed (fp32 arithmetic, D <= 6)
-template <typename T, typename F, int GT, int TL, int NG, bool ST>
+// DK > 0: Dk = Db = DK fixed at compile time (constant index arithmetic, and
+// no bounds tests when the DK^2 x DK^2 tile fills the threads exactly)
+template <typename T, typename F, int GT, int TL, int NG, bool ST, int DK>
 __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
-    absorb_ab_kernel(int chi, int Dk, int Db, int d, const T* __restrict__ In,
+    absorb_ab_kernel(int chi, int dk_arg, int db_arg, int d, const T* __restrict__ In,
                      const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Out) {
   constexpr int GROUP = GT * GT;   // threads per (t, n) pair
   constexpr int TILE = TL;         // register tile per thread
+  constexpr bool kFull = DK > 0 && DK * DK == GT * TL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Dk = DK > 0 ? DK : dk_arg, Db = DK > 0 ? DK : db_arg;
   const int K1 = Dk * Dk, N1 = Db * Db;          // (u,l) and (w,v); M1 = K1 rows (d,e)
   F* As = reinterpret_cast<F*>(smem_raw);         // [d][(d,e)][(u,l)]
   F* Bs = As + (size_t)d * K1 * K1;               // [d][(w,v)][(D,E)]
@@ -173,17 +177,18 @@ __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
         for (int a = 0; a < TILE; ++a)
 #pragma unroll
           for (int b = 0; b < TILE; ++b) y[a][b] = fz<F>();
+#pragma unroll 4
         for (int kk = 0; kk < K1; ++kk) {
           F xa[TILE], xb[TILE];
 #pragma unroll
           for (int a = 0; a < TILE; ++a) {
             const int r = ti + GT * a;
-            xa[a] = r < K1 ? Asb[r * K1 + kk] : fz<F>();
+            xa[a] = (kFull || r < K1) ? Asb[r * K1 + kk] : fz<F>();
           }
 #pragma unroll
           for (int b = 0; b < TILE; ++b) {
             const int c = tj + GT * b;
-            xb[b] = c < N1 ? Xs[kk * N1 + c] : fz<F>();
+            xb[b] = (kFull || c < N1) ? Xs[kk * N1 + c] : fz<F>();
           }
 #pragma unroll
           for (int a = 0; a < TILE; ++a)
@@ -195,23 +200,24 @@ __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
 #pragma unroll
           for (int b = 0; b < TILE; ++b) {
             const int r = ti + GT * a, c = tj + GT * b;
-            if (r < K1 && c < N1) Ys[r * N1 + c] = y[a][b];
+            if (kFull || (r < K1 && c < N1)) Ys[r * N1 + c] = y[a][b];
           }
       }
       __syncthreads();
       const F* Bsb = Bs + (size_t)s * N1 * N1;
       if (live) {
+#pragma unroll 4
         for (int kk = 0; kk < N1; ++kk) {
           F ya[TILE], bb[TILE];
 #pragma unroll
           for (int a = 0; a < TILE; ++a) {
             const int r = ti + GT * a;
-            ya[a] = r < K1 ? Ys[r * N1 + kk] : fz<F>();
+            ya[a] = (kFull || r < K1) ? Ys[r * N1 + kk] : fz<F>();
           }
 #pragma unroll
           for (int b = 0; b < TILE; ++b) {
             const int c = tj + GT * b;
-            bb[b] = c < N1 ? Bsb[kk * N1 + c] : fz<F>();
+            bb[b] = (kFull || c < N1) ? Bsb[kk * N1 + c] : fz<F>();
           }
 #pragma unroll
           for (int a = 0; a < TILE; ++a)
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(NG * GT * GT, ab_min_blocks<F, NG>())
 #pragma unroll
         for (int b = 0; b < TILE; ++b) {
           const int r = ti + GT * a, c = tj + GT * b;
-          if (r < K1 && c < N1) Ys[r * N1 + c] = acc[a][b];
+          if (kFull || (r < K1 && c < N1)) Ys[r * N1 + c] = acc[a][b];
         }
     }
     __syncthreads();
@@ -264,12 +270,12 @@ int ab_geometry(int Dk, int Db, int d, size_t fsize, size_t tsize) {
   return 0;
 }
 
-template <typename T, typename F, int GT, int TL, int NG, bool ST>
+template <typename T, typename F, int GT, int TL, int NG, bool ST, int DK>
 cudaError_t launch_ab(int chi, int Dk, int Db, int d, const void* In, const void* A,
                       const void* B, void* Out, int num_sms, cudaStream_t s) {
   const size_t shm = ab_smem(Dk, Db, d, NG, sizeof(F), sizeof(T), ST);
   static size_t configured = 0;
-  auto* fn = absorb_ab_kernel<T, F, GT, TL, NG, ST>;
+  auto* fn = absorb_ab_kernel<T, F, GT, TL, NG, ST, DK>;
   cudaError_t e = raise_smem((const void*)fn, configured, shm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -288,12 +294,18 @@ cudaError_t launch_ab(int chi, int Dk, int Db, int d, const void* In, const void
 template <typename T, typename F>
 cudaError_t launch_geom(int geom, int chi, int Dk, int Db, int d, const void* In, const void* A,
                         const void* B, void* Out, int num_sms, cudaStream_t s) {
+  const bool sq = Dk == Db;
   if constexpr (sizeof(F) < sizeof(T)) {
+    if (geom == 3 && sq && Dk == 6)
+      return launch_ab<T, F, 12, 3, 4, true, 6>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
     if (geom == 3)
-      return launch_ab<T, F, 12, 3, 4, true>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+      return launch_ab<T, F, 12, 3, 4, true, 0>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+    if (geom == 2 && sq && Dk == 8)
+      return launch_ab<T, F, 16, 4, 1, false, 8>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
   }
-  if (geom == 1) return launch_ab<T, F, 12, 3, 2, false>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
-  return launch_ab<T, F, 16, 4, 1, false>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  if (geom == 1)
+    return launch_ab<T, F, 12, 3, 2, false, 0>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
+  return launch_ab<T, F, 16, 4, 1, false, 0>(chi, Dk, Db, d, In, A, B, Out, num_sms, s);
 }
 
 size_t elem_size(bool cx, bool fp32) { return (cx ? 2 : 1) * (fp32 ? 4 : 8); }
