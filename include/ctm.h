@@ -145,7 +145,9 @@ ctm_status ctm_spectrum(ctm_ctx* ctx, int x, int y, int label, double* s_out);
 
 /* The same for all corners in one batched call: s_out has 4*Lx*Ly*chi
  * entries, laid out [label 0..3][site][chi] (the convergence measure of
- * ctm_converge compares these). */
+ * ctm_converge compares these). Right after ctm_converge, with no move,
+ * ctm_set_env or ctm_load in between, it returns the spectra that the last
+ * convergence measure computed instead of computing them again. */
 ctm_status ctm_spectra(ctm_ctx* ctx, double* s_out);
 
 /* Two-site expectation <O> = Tr(O rho) / Tr(rho) on the bond from (x, y) to

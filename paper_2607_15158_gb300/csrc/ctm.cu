@@ -116,6 +116,9 @@ struct ctm_ctx {
   int moves_done[4] = {0, 0, 0, 0};
   int num_sms = 1;
   bool spectra_init = false;
+  // spec_old holds the normalised spectra of the current C (set by the
+  // convergence measure, cleared by anything that changes C)
+  bool spectra_fresh = false;
   // split-precision state
   SplitCtx* split = nullptr;
   // lanes: the cuts of a column are independent until their small SVDs, so
@@ -849,6 +852,7 @@ ctm_status check_err(ctm_ctx* c) {
 }
 
 ctm_status move_impl(ctm_ctx* c, int r) {
+  c->spectra_fresh = false;
   const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
   const size_t NC = (size_t)c->N * c->chi;
   const bool svd = c->opts.method == CTM_PROJ_SVD;
@@ -1021,6 +1025,7 @@ ctm_status upload_default_state(ctm_ctx* c) {
                               c->stream));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
   c->spectra_init = false;
+  c->spectra_fresh = false;
   for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
   return CTM_OK;
 }
@@ -1416,6 +1421,7 @@ ctm_status ctm_set_env(ctm_ctx* c, const void* C, const void* T) {
   CTM_CUDA_OK(cudaMemcpyAsync(c->T, T, 4 * c->S * elems_T(c) * c->es, cudaMemcpyHostToDevice, c->stream));
   CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
   c->spectra_init = false;
+  c->spectra_fresh = false;
   return CTM_OK;
 }
 
@@ -1578,6 +1584,7 @@ ctm_status ctm_load(ctm_ctx* c, const void* buf, size_t nbytes) {
   for (int r = 0; r < 4; ++r) c->moves_done[r] = h.moves_done[r];
   c->last_dir = h.last_dir;
   c->spectra_init = h.spectra_init != 0;
+  c->spectra_fresh = false;
   c->qr_calls = h.qr_calls;
   return CTM_OK;
 }
@@ -1629,6 +1636,7 @@ ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, do
     CTM_CUDA_OK(cudaMemsetAsync(c->spec_old, 0, nspec * sizeof(double), c->stream));
     CTM_CUDA_OK(spectra_delta(c->chi, 4 * c->S, c->spec_new, c->spec_old, c->dscal, c->stream, &c->launches));
     c->spectra_init = true;
+    c->spectra_fresh = true;
   }
   double delta = INFINITY;
   int it = 0;
@@ -1637,6 +1645,7 @@ ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, do
     ++it;
     CK(corner_spectra(c, c->spec_new));
     CTM_CUDA_OK(spectra_delta(c->chi, 4 * c->S, c->spec_new, c->spec_old, c->dscal + 1, c->stream, &c->launches));
+    c->spectra_fresh = true;
     CTM_CUDA_OK(cudaMemcpyAsync(&delta, c->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(check_err(c));
     if (delta < tol) break;
@@ -1674,6 +1683,13 @@ ctm_status ctm_spectra(ctm_ctx* c, double* s_out) {
   if (!c || !s_out) return fail(c, CTM_EINVAL, "NULL argument");
   Guard gd(c);
   const int nb = 4 * c->S;
+  if (c->spectra_fresh) {
+    // the convergence measure of the last iteration already holds them
+    CTM_CUDA_OK(cudaMemcpyAsync(s_out, c->spec_old, (size_t)nb * c->chi * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+    CK(check_err(c));
+    return CTM_OK;
+  }
   CK(corner_spectra(c, c->sv));
   const size_t mark = c->scratch_off;
   double* nrm = static_cast<double*>(scratch_alloc(c, (size_t)nb * sizeof(double)));

@@ -259,4 +259,10 @@ def test_batched_spectra_match_single_corner_calls():
             for x in range(2):
                 s = ctx.ctm_spectrum(x, y, lab + 1)
                 assert np.abs(allspec[lab, y * 2 + x] - s).max() < 1e-13
+    # right after ctm_converge the batched call returns the convergence
+    # measure's spectra; re-uploading the same environment forces a fresh
+    # computation, which must agree
+    C, T = ctx.ctm_get_env()
+    ctx.ctm_set_env(C, T)
+    assert np.abs(ctx.ctm_spectra() - allspec).max() < 1e-13
     ctx.ctm_free()
