@@ -200,6 +200,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- rank aggregation
+def max_over_ranks(x, dist, device):
+    """The largest value of a per-rank float over all ranks (x itself for a
+    single process): the slowest rank times the whole job."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job rate: the units all ranks processed (each rank an independent
+    replica of the same workload) over the time of the slowest rank."""
+    return units_per_rank * world / seconds
+
+
 # -------------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -266,12 +284,9 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     prof = ctx.ctm_profile_read() if prec == pkg.CTM_PREC_SPLIT_BF16 else None
     phases = {k_: round(v / args.steps, 2) for k_, v in ctx.ctm_profile_phases().items()}
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     moves = 4 * args.steps * world
-    value = moves / (ms / 1000.0)
+    value = job_throughput(4 * args.steps, world, ms / 1000.0)
 
     # end to end through the C ABI with host buffers: per step the
     # environment is copied in from pinned host memory, the iteration runs,
@@ -290,11 +305,8 @@ def run_ours(args, rank, world, local_rank):
         ctx.ctm_spectra()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = moves / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_value = job_throughput(4 * args.steps, world, e2e_s)
     h2d = Ch.nbytes + Th.nbytes
     d2h = 4 * Lx * Ly * chi * 8
 
