@@ -8,14 +8,16 @@
 // work is two small matrix products per physical index s,
 //   Y_s = A_s X       (Dk^2 x Dk^2) (Dk^2 x Db^2),  X[(u,l),(w,v)] = In[t,l,w,n,u,v]
 //   Out += Y_s B_s    (Dk^2 x Db^2) (Db^2 x Db^2),  B_s[(w,v),(D,E)] = B[s,v,w,D,E]
-// so one kernel reads In once and writes Out once (HBM-bound in fp32; the
-// unfused form is two permutes, two GEMMs and a final permute). Each CTA
-// holds A and B in shared memory and runs NG groups of GT x GT threads, one
-// (t, n) pair each; a thread owns a TL x TL register tile of the products,
-// rows ti + GT a and columns tj + GT b (consecutive threads read consecutive
-// shared-memory words). Two geometries: GT = 12, TL = 3, two groups for
-// Dk^2, Db^2 <= 36 (D <= 6), and GT = 16, TL = 4, one group for <= 64
-// (D <= 8). Arithmetic in F: fp32 (split-precision contexts, ~1e-7 relative
+// so one kernel reads In once and writes Out once (the unfused form is two
+// permutes, two GEMMs and a final permute); the fp32 arithmetic, not HBM,
+// bounds it. Each CTA holds A and B in shared memory and runs NG groups of
+// GT x GT threads, one (t, n) pair each; a thread owns a TL x TL register
+// tile of the products, rows ti + GT a and columns tj + GT b (consecutive
+// threads read consecutive shared-memory words). Geometries: GT = 12,
+// TL = 3 for Dk^2, Db^2 <= 36 (D <= 6), with four groups and the next
+// pair's input staged by cp.async in fp32, else two groups; GT = 16, TL = 4,
+// one group for <= 64 (D <= 8). D = 6 and D = 8 also have compile-time
+// variants. Arithmetic in F: fp32 (split-precision contexts, ~1e-7 relative
 // like the bf16x3 products) or fp64.
 #include <algorithm>
 
