@@ -285,7 +285,6 @@ def run_ours(args, rank, world, local_rank):
     prof = ctx.ctm_profile_read() if prec == pkg.CTM_PREC_SPLIT_BF16 else None
     phases = {k_: round(v / args.steps, 2) for k_, v in ctx.ctm_profile_phases().items()}
     ms = max_over_ranks(ms, dist, "cuda")
-    moves = 4 * args.steps * world
     value = job_throughput(4 * args.steps, world, ms / 1000.0)
 
     # end to end through the C ABI with host buffers: per step the
