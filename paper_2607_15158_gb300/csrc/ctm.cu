@@ -137,6 +137,7 @@ struct ctm_ctx {
     void* Linv = nullptr;
     double* dsc = nullptr;
     int* dead = nullptr;
+    void* chol_work = nullptr;   // cooperative Cholesky scratch (large k)
   };
   std::vector<Lane> lanes;   // lane 0 = the context's own buffers and stream
   int cur_lane = 0;
@@ -298,6 +299,7 @@ void use_lane(ctm_ctx* c, int i) {
   c->Linv = L.Linv;
   c->dsc = L.dsc;
   c->dead = L.dead;
+  c->chol_work = L.chol_work;
   c->cur_lane = i;
 }
 
@@ -1203,6 +1205,7 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
     L0.Linv = c->Linv;
     L0.dsc = c->dsc;
     L0.dead = c->dead;
+    L0.chol_work = c->chol_work;
     if (cudaEventCreateWithFlags(&L0.ev, cudaEventDisableTiming) != cudaSuccess)
       return bail(fail(c, CTM_ECUDA, "cudaEventCreate failed"));
     c->lanes.push_back(L0);
@@ -1232,7 +1235,8 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       if ((st = dalloc(c, &M.G, k * k * es)) != CTM_OK ||
           (st = dalloc(c, &M.Linv, k * k * es)) != CTM_OK ||
           (st = dalloc(c, (void**)&M.dsc, k * sizeof(double))) != CTM_OK ||
-          (st = dalloc(c, (void**)&M.dead, k * sizeof(int))) != CTM_OK)
+          (st = dalloc(c, (void**)&M.dead, k * sizeof(int))) != CTM_OK ||
+          (st = dalloc(c, &M.chol_work, chol_coop_work_bytes((int)k, 1))) != CTM_OK)
         return bail(st);
       if (c->opts.prec == CTM_PREC_SPLIT_BF16 &&
           (st = split_create(&M.split, cx, (int)N, (int)k, c->err, M.stream)) != CTM_OK) {
@@ -1486,7 +1490,7 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
     const bool fused = absorb_ab_supported(cx, o->prec == CTM_PREC_SPLIT_BF16, Dk, Db, d);
     const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
     size_t lane = 4 * NN * es + 4 * laneT * es + ((size_t)64 << 20) + 4 * N * k * es +
-                  2 * k * k * es + 12 * k;
+                  2 * k * k * es + 12 * k + chol_coop_work_bytes((int)k, 1);
     if (o->prec == CTM_PREC_SPLIT_BF16) {
       const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
       lane += 10 * 3 * N * Kp * 2 + 32 * N * ((cx ? 2 : 1) * k + 160) * 4;
