@@ -559,8 +559,10 @@ __global__ void __launch_bounds__(JT) chol_coop(CholArgs a) {
 
 }  // namespace
 
+// aux block, then the grid-barrier words (count, generation and abort flag at
+// word offsets 0, 32 and 64, see grid_barrier) after a 16-byte alignment
 size_t chol_coop_work_bytes(int k, int batch) {
-  return (size_t)batch * (2 * k + 2) * sizeof(double) + 64;
+  return (size_t)batch * (2 * k + 2) * sizeof(double) + 16 + 65 * sizeof(unsigned);
 }
 
 cudaError_t chol_inv_coop(bool cx, int k, long n, bool shift, bool scale, void* Gm, void* Linv,
@@ -588,7 +590,7 @@ cudaError_t chol_inv_coop(bool cx, int k, long n, bool shift, bool scale, void* 
   w += (size_t)batch * (2 * k + 2) * sizeof(double);
   a.bar = reinterpret_cast<unsigned*>((reinterpret_cast<uintptr_t>(w) + 15) & ~(uintptr_t)15);
   a.err = err;
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, 3 * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 65 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
   const void* fn = cx ? (const void*)chol_coop<cplx> : (const void*)chol_coop<double>;

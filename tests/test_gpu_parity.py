@@ -15,6 +15,7 @@ import pytest
 import ctm_synth as S
 import paper_2607_15158_gb300 as pkg
 from oracle import ctmrg, ising
+from pairs import make_pair
 
 pytestmark = pytest.mark.gpu
 HEIS = S.heisenberg_bond()
@@ -22,18 +23,7 @@ TOL = 1e-10
 
 
 def _pair(Lx, Ly, d, D, chi, p, cplx, rounds, seed=0, diag=0.0):
-    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, seed=seed, diag_weight=diag)
-    Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx, seed=1)
-    N = chi * D * D
-    k = min(chi + p, N)
-    X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx, seed=2)
-    ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx,
-                       opts=pkg.ctm_default_opts(p=p, si_rounds=rounds))
-    ctx.ctm_set_env(Cs, Ts)
-    ctx.ctm_set_rangefinders(X0, W0)
-    ref = ctmrg.CTM(Lx, Ly, A, [a.conj() for a in A], Cs, Ts, chi, method="si", p=p,
-                    si_rounds=rounds, X0=X0, W0=W0, warmup_iters=5, warmup_rounds=8)
-    return ctx, ref
+    return make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, seed=seed, diag=diag)
 
 
 def _compare(ctx, ref, energies=True, tol=TOL):

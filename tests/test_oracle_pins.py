@@ -267,13 +267,15 @@ def test_si_projectors_depend_only_on_spans():
         assert np.abs(ov - 1).max() < 1e-10
 
 
-def test_si_converges_to_svd_fixed_point():
+@pytest.mark.parametrize("cplx", [False, True])
+def test_si_converges_to_svd_fixed_point(cplx):
     """P7: with a gapped spectrum SI-CTMRG and standard CTMRG reach the same
     fixed point: corner spectra and bond energies agree, and the SI subspaces
-    stop moving (sin^2 theta -> 0)."""
+    stop moving (sin^2 theta -> 0). On complex A this also fixes the reading
+    M^T -> M^dagger of the rangefinder update (Eq. xy_iter)."""
     res = {}
     for method in ("svd", "si"):
-        ctm = _random_cell(method, Lx=1, Ly=1, D=2, chi=12, cplx=False, rounds=2, seed=4)
+        ctm = _random_cell(method, Lx=1, Ly=1, D=2, chi=12, cplx=cplx, rounds=2, seed=4)
         it, delta = ctm.converge(1e-13, 400)
         assert delta < 1e-12
         res[method] = ctm
@@ -283,6 +285,53 @@ def test_si_converges_to_svd_fixed_point():
     for direction in (0, 1):
         assert abs(a.expect2(HEIS, 0, 0, direction) - b.expect2(HEIS, 0, 0, direction)) < 1e-10
     assert max(d["sin2"] for d in b.last.values()) < 1e-12
+
+
+def _complex_cut(seed=6, D=2, chi=6):
+    ctm = _random_cell("svd", Lx=1, Ly=1, D=D, chi=chi, cplx=True, seed=seed)
+    for _ in range(3):
+        ctm.iteration()
+    return ctm.cut_corners(ctmrg.Frame(1, 1, 0), 0, 0), chi
+
+
+def _oblique(Pl, Pr):
+    P = Pl @ Pr
+    return P / np.abs(P).max()
+
+
+def test_si_rounds_reach_svd_projector_on_complex_cut():
+    """P7 on one complex cut: repeated rounds of the rangefinder update from
+    random bases converge to the leading singular subspaces of M, so the SI
+    oblique projector P_l P_r equals the truncated-SVD one. With M^T in place
+    of M^dagger (a mistake planted on the CPU below) the rounds converge to
+    the leading subspaces of the wrong operator and the check fails."""
+    Q, chi = _complex_cut()
+    N = Q[1].shape[1]
+    k = chi + 4
+    rng = np.random.default_rng(11)
+    X = ctmrg.qr_q(rng.standard_normal((N, k)) + 1j * rng.standard_normal((N, k)))
+    W = ctmrg.qr_q(rng.standard_normal((N, k)) + 1j * rng.standard_normal((N, k)))
+    svd = ctmrg.projectors_svd(*Q, chi)
+    si = ctmrg.projectors_si(*Q, X, W, chi, rounds=60)
+    ref = _oblique(svd[0], svd[1])
+    assert np.abs(_oblique(si[0], si[1]) - ref).max() < 1e-9
+    assert np.abs(si[2] - svd[2]).max() / svd[2][0] < 1e-10
+
+
+def test_planted_transpose_reading_fails_the_complex_pin(monkeypatch):
+    """The complex P7 pin is sensitive to the M^T / M^dagger reading: with the
+    conjugation dropped from M^dagger Z the SI projector misses the SVD one."""
+    Q, chi = _complex_cut()
+    N = Q[1].shape[1]
+    k = chi + 4
+    rng = np.random.default_rng(11)
+    X = ctmrg.qr_q(rng.standard_normal((N, k)) + 1j * rng.standard_normal((N, k)))
+    W = ctmrg.qr_q(rng.standard_normal((N, k)) + 1j * rng.standard_normal((N, k)))
+    monkeypatch.setattr(ctmrg, "apply_Mh",
+                        lambda Q1, Q2, Q3, Q4, Z: Q2.T @ (Q1.T @ (Q4.T @ (Q3.T @ Z))))
+    svd = ctmrg.projectors_svd(*Q, chi)
+    si = ctmrg.projectors_si(*Q, X, W, chi, rounds=60)
+    assert np.abs(_oblique(si[0], si[1]) - _oblique(svd[0], svd[1])).max() > 1e-3
 
 
 def test_si_fixed_point_is_elementwise():
