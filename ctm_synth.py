@@ -43,23 +43,31 @@ def _normal(rng, shape, complex_: bool):
 
 
 def ipeps_tensors(Lx, Ly, d, D, complex_=False, seed=SEED_A, diag_weight=0.0,
-                  normalize=True):
+                  normalize=True, bond_decay=1.0):
     """One random on-site tensor A[s,u,l,d,r] per site of an Lx x Ly cell.
 
     Entries are N(0,1) (complex: Re, Im ~ N(0,1/2)); ``diag_weight`` adds that
     weight to every entry whose four virtual indices are equal (any physical
-    index) -- the "identity-like diagonal" of the 3x3 D=4 workload. Each tensor
-    is scaled to unit Frobenius norm when ``normalize``.
+    index) -- the "identity-like diagonal" of the 3x3 D=4 workload.
+    ``bond_decay`` q < 1 multiplies entry [s,u,l,d,r] by q^(u+l+d+r): a random
+    state whose bond weights fall off geometrically (weakly entangled, short
+    correlation length), whose environment converges at small chi even for
+    large D. Each tensor is scaled to unit Frobenius norm when ``normalize``.
     Returns a list indexed by site ``y * Lx + x``.
     """
     rng = _rng(seed)
     out = []
+    lam = float(bond_decay) ** np.arange(D)
+    w = (lam[:, None, None, None] * lam[None, :, None, None] * lam[None, None, :, None]
+         * lam[None, None, None, :])
     for _ in range(Lx * Ly):
         A = _normal(rng, (d, D, D, D, D), complex_)
         if diag_weight:
             for s in range(d):
                 for k in range(D):
                     A[s, k, k, k, k] += diag_weight
+        if bond_decay != 1.0:
+            A = A * w[None]
         if normalize:
             A = A / np.linalg.norm(A)
         out.append(A)

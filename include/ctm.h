@@ -89,11 +89,34 @@ typedef struct {
                              real positive */
   int sign_fix;           /* phase fix of the small SVD of rho */
   uint64_t seed;          /* seed of the default random C, T, X, W */
+  int svd_max_sweeps;     /* sweep budget of the Jacobi SVDs (small problem,
+                             corner spectra); running out is CTM_ENOCONV */
+  int init_mode;          /* initial C, T: 0 = seeded random normal,
+                             1 = from the on-site tensors (CTM_INIT_FROM_A) */
+  double recycle_sin2;    /* recycling policy of paper step 4: once the mean
+                             sin^2 of the principal angles between successive
+                             leading chi-subspaces of a cut falls below this
+                             value (paper: 1e-3) after at least min_si_steps
+                             updates, the cut's rangefinders are only
+                             recycled, with no subspace-iteration round, until
+                             the angle grows above it again; 0 = always update */
+  int min_si_steps;       /* see recycle_sin2 (paper: at least 3) */
   void* stream;           /* cudaStream_t to run on, NULL = a private stream */
 } ctm_opts;
 
+/* init_mode values. CTM_INIT_FROM_A: every corner is the double-layer tensor
+ * of its site with the two outer bond pairs traced (C1 = sum over s, u, l of
+ * A[s,u,l,d,r] conj(A)[s,u,l,d',r'] as a (d d') x (r r') matrix, the other
+ * corners the same form of the turned tensor), every edge the double layer
+ * with its outer pair traced, and both are embedded in the top-left block of
+ * the chi x chi bonds (zero elsewhere) or cut to it when D^2 > chi; then
+ * normalised. */
+enum { CTM_INIT_RANDOM = 0, CTM_INIT_FROM_A = 1 };
+
 /* Defaults: p = 5, si_rounds = 1, warmup_iters = 5, warmup_rounds = 8, SI,
- * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0, stream = NULL. */
+ * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0,
+ * svd_max_sweeps = 80, init_mode = CTM_INIT_RANDOM, recycle_sin2 = 0 (always
+ * update), min_si_steps = 3, stream = NULL. */
 void ctm_default_opts(ctm_opts* opts);
 
 /* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz
@@ -136,13 +159,19 @@ ctm_status ctm_move(ctm_ctx* ctx, ctm_dir dir);
 
 /* Iterations of the four moves (left, up, right, down) until the
  * corner-spectrum change Delta < tol or max_iter; Delta = max over corners
- * and sites of ||s_new - s_old||_2 of unit-normalised spectra. Returns
- * CTM_ENOCONV (not fatal) when max_iter is reached. */
+ * and sites of ||s_new - s_old||_2 of unit-normalised spectra. The paper
+ * iterates CTMRG steps until the environment converges (section "CTMRG" and
+ * step 4 of the QR-based projector: with the sign fix, C and T converge
+ * element-wise); the corner-spectrum change is the gauge-invariant form of
+ * that criterion. Returns CTM_ENOCONV (not fatal) when max_iter is reached.
+ * iters_out, delta_out may be NULL. */
 ctm_status ctm_converge(ctm_ctx* ctx, double tol, int max_iter,
                         int* iters_out, double* delta_out);
 
 /* Normalised singular values (descending, unit 2-norm) of corner C_label
- * (label 1..4) at site (x, y); s_out has chi entries. */
+ * (label 1..4) at site (x, y); s_out has chi entries (host). The corner
+ * spectrum is the quantity whose change measures convergence (see
+ * ctm_converge); the paper's corners are the C_i of Fig. ctmrg-step. */
 ctm_status ctm_spectrum(ctm_ctx* ctx, int x, int y, int label, double* s_out);
 
 /* The same for all corners in one batched call: s_out has 4*Lx*Ly*chi
@@ -155,7 +184,9 @@ ctm_status ctm_spectra(ctm_ctx* ctx, double* s_out);
 /* Two-site expectation <O> = Tr(O rho) / Tr(rho) on the bond from (x, y) to
  * its right (dir = 0) or lower (dir = 1) neighbour; op is d^2 x d^2,
  * row-major O[(s1', s2')][(s1, s2)] (row = bra), dtype of the context; site 1
- * is (x, y). out = (re, im). */
+ * is (x, y). out = (re, im). This is the observable g(A, C*, T*) of the
+ * paper's optimisation section, evaluated on the converged environment
+ * (for the Heisenberg model, the bond energy <S.S>). */
 ctm_status ctm_expect(ctm_ctx* ctx, const void* op, int x, int y, int dir,
                       double out[2]);
 
@@ -184,6 +215,26 @@ ctm_status ctm_free_energy(ctm_ctx* ctx, double* ln_kappa);
  * the context. */
 ctm_status ctm_get_projectors(ctm_ctx* ctx, ctm_dir dir, int x, int y,
                               void* Pl, void* PrH);
+
+/* The enlarged corner Q_i (i = 1..4: upper-left, upper-right, lower-right,
+ * lower-left) of the 2x2 block whose upper-left position is (x, y) in the
+ * frame of direction dir, as an N x N matrix (row-major, N = chi*Dk*Db,
+ * rows: the corner's incoming ring bond and the ket/bra legs, columns: its
+ * outgoing ones), built by the context's own path and precision from the
+ * current environment (Eq. rho_M_diag, Fig. ctmrg-step). Q_out: host, N*N
+ * elements of the context's dtype. */
+ctm_status ctm_corner(ctm_ctx* ctx, ctm_dir dir, int x, int y, int i, void* Q_out);
+
+/* Z_out = op(Q_i) Z_in for that corner and a host block Z_in of N x k
+ * (row-major, k = ctm_dims' k), op = identity (herm = 0) or the conjugate
+ * transpose (herm = 1): the corner x block product of the rangefinder
+ * update (Eq. xy_iter), run by the context's own kernels and precision. */
+ctm_status ctm_corner_apply(ctm_ctx* ctx, ctm_dir dir, int x, int y, int i, int herm,
+                            const void* Z_in, void* Z_out);
+
+/* Subspace-iteration updates made and skipped (recycling policy of
+ * opts.recycle_sin2) over all cuts since the context was created. */
+ctm_status ctm_si_stats(const ctm_ctx* ctx, long* updates, long* skipped);
 
 /* Device milliseconds of the last ctm_move / ctm_converge call and the
  * number of kernels it launched. */
@@ -272,11 +323,18 @@ void ctm_server_free(ctm_server* srv);
 ctm_status ctm_save(const ctm_ctx* ctx, void* buf, size_t* nbytes);
 ctm_status ctm_load(ctm_ctx* ctx, const void* buf, size_t nbytes);
 
-void ctm_free(ctm_ctx* ctx);void ctm_free(ctm_ctx* ctx);
+void ctm_free(ctm_ctx* ctx);
 
 /* Message of the last failed call on ctx (or of the last failed creation when
  * ctx is NULL); owned by the library, valid until the next call. */
 const char* ctm_last_error(const ctm_ctx* ctx);
+
+/* Fault injection for tests of the error paths (the paper has no
+ * counterpart): after this call the library's device allocations succeed
+ * `after` more times, then the next one fails on the host, before
+ * cudaMalloc is called, as if the device were out of memory (CTM_ENOMEM);
+ * the hook then disarms itself. after < 0 disarms it. Process-wide. */
+void ctm_debug_fail_alloc(int after);
 
 /* Singular values of one k x k matrix, with no device allocation.
  *
@@ -298,7 +356,10 @@ const char* ctm_last_error(const ctm_ctx* ctx);
  *   stream  the cudaStream_t to run on (NULL: the legacy default stream).
  *
  * The first call on a device looks up the device address of the scratch array
- * with that device current; make it before any stream capture. The call
+ * with that device current; make it before any stream capture. The address is
+ * kept for the life of the process: after cudaDeviceReset (or any teardown of
+ * the device's primary context) the array lives at a new address, so do not
+ * call this entry point again in that process. The call
  * clears the words that must start at zero (error word, grid-barrier
  * counters) on the stream itself, then waits for the stream to read the error
  * word back, so it returns only once s is written. Calls that overlap on one

@@ -97,8 +97,11 @@ def enlarged_corner(C, Tb, Ta, A, B):
     the edge after it. The other three corners are this form applied to the
     tensor turned by 1, 2, 3 quarter turns.
     Pinned by: exact finite-patch growth (P3) and Onsager/Yang (P1, P2)."""
-    Q = np.einsum("pm,mnuv,tplw,sulde,svwDE->tdDneE", C, Ta, Tb, A, B,
-                  optimize=True)
+    # the same sum, one pairwise contraction at a time (each a BLAS product)
+    CT = np.tensordot(C, Ta, axes=([1], [0]))                    # [p,n,u,v]
+    CTT = np.tensordot(Tb, CT, axes=([1], [0]))                  # [t,l,w,n,u,v]
+    R = np.einsum("tlwnuv,sulde->twnvsde", CTT, A, optimize=True)
+    Q = np.einsum("twnvsde,svwDE->tdDneE", R, B, optimize=True)
     t, d, D, n, e, E = Q.shape
     return Q.reshape(t * d * D, n * e * E)
 
@@ -212,6 +215,71 @@ def projectors_si(Q1, Q2, Q3, Q4, X, W, chi, rounds=1, cutoff=1e-12,
     return Pl, Pr, s, Xn, Wn, s_all
 
 
+def unit_norm_phase(t):
+    """t / ||t||_F times the conjugate phase of its largest-modulus entry
+    (lowest flat index on a tie); returns (normalised t, ||t||_F)."""
+    n = np.linalg.norm(t)
+    flat = t.reshape(-1)
+    piv = flat[np.argmax(np.abs(flat))]
+    ph = piv / abs(piv) if abs(piv) > 0 else 1.0
+    return t * (np.conj(ph) / n), n
+
+
+def env_from_tensors(Lx, Ly, kets, bras, chi):
+    """Initial environment built from the on-site tensors (reading of the
+    usual CTMRG start from the network itself): corner i of a site is the
+    double layer of the site's tensor turned by i quarter turns with its up
+    and left bond pairs traced, C[(d d'), (r r')]; edge i is the double layer
+    of the turned tensor with its up pair traced, T[(l l'), (r r'), d, d'].
+    Bond pairs of dimension D^2 are embedded in the top-left block of the chi
+    bonds (zeros elsewhere) or cut to chi; every tensor is normalised like a
+    move's output. Returns C[label][site], T[label][site]."""
+    C = [[None] * (Lx * Ly) for _ in range(4)]
+    T = [[None] * (Lx * Ly) for _ in range(4)]
+    for i in range(4):
+        for site in range(Lx * Ly):
+            A = rotate_tensor(kets[site], i)
+            B = rotate_tensor(bras[site], i)
+            Dk, Db = A.shape[1], B.shape[1]
+            DD = Dk * Db
+            m = min(chi, DD)
+            dt = np.result_type(A, B, 1.0)
+            c = np.einsum("sulde,sulDE->dDeE", A, B).reshape(DD, DD)
+            t = np.einsum("sulde,suLDE->lLeEdD", A, B).reshape(DD, DD, Dk, Db)
+            Cc = np.zeros((chi, chi), dtype=dt)
+            Cc[:m, :m] = c[:m, :m]
+            Tt = np.zeros((chi, chi, Dk, Db), dtype=dt)
+            Tt[:m, :m] = t[:m, :m]
+            C[i][site] = unit_norm_phase(Cc)[0]
+            T[i][site] = unit_norm_phase(Tt)[0]
+    return C, T
+
+
+def absorb_site(C1, T1, T3, C4, T4, A, B, Pl_up, Pr_up, Pl_dn, Pr_dn):
+    """New C1, T4, C4 of one site of the absorbed column (End Matter, left
+    move): C1' = P_r (C1 T1) with the projectors of the cut above,
+    C4' = (T3 C4) P_l with those of the cut below, and
+    T4' = P_r (T4 A B) P_l with P_l of the cut above and P_r of the cut below,
+    contracted as ((T4 P_l) A) B then P_r so that no intermediate exceeds
+    chi^2 d D^4. Not normalised."""
+    # C1' = P_r (C1 T1): C1 T1 has legs [(p, u, u'), n]
+    E1 = np.einsum("pm,mnuv->puvn", C1, T1)
+    E1 = E1.reshape(-1, T1.shape[1])
+    C1n = Pr_up @ E1
+    # C4' = (T3 C4) P_l: T3 C4 has legs [t, (n, d, d')]
+    E4 = np.einsum("tmdD,mn->tndD", T3, C4)
+    E4 = E4.reshape(T3.shape[0], -1)
+    C4n = E4 @ Pl_dn
+    Dk, Db = A.shape[1], B.shape[1]
+    Pl4 = Pl_up.reshape(T4.shape[1], Dk, Db, -1)       # [q,u,v,c]
+    Pr4 = Pr_dn.reshape(-1, T4.shape[0], Dk, Db)       # [c',t,d,D]
+    Y = np.einsum("tqlw,quvc->tlwuvc", T4, Pl4, optimize=True)
+    Y = np.einsum("tlwuvc,sulde->twvcsde", Y, A, optimize=True)
+    Y = np.einsum("twvcsde,svwDE->tdDceE", Y, B, optimize=True)
+    T4n = np.einsum("atdD,tdDceE->aceE", Pr4, Y, optimize=True)
+    return C1n, T4n, C4n
+
+
 # --------------------------------------------------------------- the CTM
 
 class CTM:
@@ -226,11 +294,18 @@ class CTM:
     before the recycled bases settle), later moves si_rounds.
     X0, W0: raw Gaussian N x k blocks per [direction][cut]; they are
     orthonormalised on first use (QR of a Gaussian matrix, step 1).
+    recycle_sin2, min_si_steps: recycling policy of step 4 -- once the mean
+    sin^2 of the principal angles between the leading chi-subspaces before
+    and after a cut's move is below recycle_sin2 (paper: 1e-3) and the cut
+    has had at least min_si_steps updates (paper: at least three), its next
+    moves make no update round and only recycle the bases, until the angle
+    grows above the threshold again; recycle_sin2 = 0 always updates.
     """
 
     def __init__(self, Lx, Ly, kets, bras, C, T, chi, method="si", p=5,
                  si_rounds=1, X0=None, W0=None, cutoff=1e-12, normalize=True,
-                 sign_fix=True, warmup_iters=0, warmup_rounds=8):
+                 sign_fix=True, warmup_iters=0, warmup_rounds=8, recycle_sin2=0.0,
+                 min_si_steps=3):
         self.Lx, self.Ly = Lx, Ly
         self.kets = [np.asarray(a) for a in kets]
         self.bras = [np.asarray(b) for b in bras]
@@ -250,6 +325,12 @@ class CTM:
         self.warmup_iters = warmup_iters
         self.warmup_rounds = warmup_rounds
         self.moves_done = [0, 0, 0, 0]   # moves per direction
+        self.recycle_sin2 = recycle_sin2
+        self.min_si_steps = min_si_steps
+        self.si_updates = {}             # (r, cut) -> update rounds made
+        self.si_skip = {}                # (r, cut) -> next move only recycles
+        self.n_updates = 0
+        self.n_skipped = 0
 
     # -- frame accessors
     def _get(self, f, kind, i, x, y):
@@ -311,16 +392,27 @@ class CTM:
         dtype = np.result_type(Q1, Q2, Q3, Q4)
         cut = (y % f.Ly) * f.Lx + (x % f.Lx)
         X, W = self._rangefinder(f.r, cut, Nc, Nr, k, dtype)
-        rounds = (self.warmup_rounds if self.moves_done[f.r] < self.warmup_iters
-                  else self.si_rounds)
+        key = (f.r, cut)
+        if self.moves_done[f.r] < self.warmup_iters:
+            rounds = self.warmup_rounds
+        else:
+            rounds = 0 if self.si_skip.get(key, False) else self.si_rounds
+        if rounds > 0:
+            self.si_updates[key] = self.si_updates.get(key, 0) + 1
+            self.n_updates += 1
+        else:
+            self.n_skipped += 1
         Pl, Pr, s, Xn, Wn, s_all = projectors_si(
             Q1, Q2, Q3, Q4, X, W, self.chi, rounds, self.cutoff,
             self.sign_fix)
         # principal angles between the old and new leading chi-subspaces
         c = min(self.chi, k)
         sv = np.linalg.svd(X[:, :c].conj().T @ Xn[:, :c], compute_uv=False)
-        self.last[(f.r, x, y)] = dict(s=s, s_all=s_all, Pl=Pl, Pr=Pr,
-                                      sin2=float(np.mean(1 - np.minimum(sv, 1) ** 2)))
+        sin2 = float(np.mean(1 - sv ** 2))
+        self.last[(f.r, x, y)] = dict(s=s, s_all=s_all, Pl=Pl, Pr=Pr, sin2=sin2)
+        if self.recycle_sin2 > 0:
+            self.si_skip[key] = (sin2 < self.recycle_sin2
+                                 and self.si_updates.get(key, 0) >= self.min_si_steps)
         self.rf[(f.r, cut)] = (Xn, Wn)
         return Pl, Pr
 
@@ -330,12 +422,9 @@ class CTM:
         each new tensor so that C and T can converge element-wise."""
         if not self.normalize:
             return t
-        n = np.linalg.norm(t)
+        t, n = unit_norm_phase(t)
         self.log_norms.append(np.log(n))
-        flat = t.reshape(-1)
-        piv = flat[np.argmax(np.abs(flat))]
-        ph = piv / abs(piv) if abs(piv) > 0 else 1.0
-        return t * (np.conj(ph) / n)
+        return t
 
     def left_move(self, r):
         """Left move of the frame turned by r quarter turns (End Matter):
@@ -349,31 +438,11 @@ class CTM:
             for y in range(f.Ly):
                 Pl_up, Pr_up = P[(y - 1) % f.Ly]   # cut between rows y-1 and y
                 Pl_dn, Pr_dn = P[y]                # cut between rows y and y+1
-                C1 = self._get(f, "C", 0, x, y)
-                T1 = self._get(f, "T", 0, x, y)
-                T3 = self._get(f, "T", 2, x, y)
-                C4 = self._get(f, "C", 3, x, y)
-                T4 = self._get(f, "T", 3, x, y)
-                A = self._ket(f, x, y)
-                B = self._bra(f, x, y)
-                # C1' = P_r (C1 T1): C1 T1 has legs [(p, u, u'), n]
-                E1 = np.einsum("pm,mnuv->puvn", C1, T1)
-                E1 = E1.reshape(-1, T1.shape[1])
-                C1n = Pr_up @ E1
-                # C4' = (T3 C4) P_l: T3 C4 has legs [t, (n, d, d')]
-                E4 = np.einsum("tmdD,mn->tndD", T3, C4)
-                E4 = E4.reshape(T3.shape[0], -1)
-                C4n = E4 @ Pl_dn
-                # T4' = P_r (T4 A B) P_l, contracted as ((T4 P_l) A) B then P_r
-                # so that no intermediate exceeds chi^2 d D^4
-                Dk, Db = A.shape[1], B.shape[1]
-                Pl4 = Pl_up.reshape(T4.shape[1], Dk, Db, -1)       # [q,u,v,c]
-                Pr4 = Pr_dn.reshape(-1, T4.shape[0], Dk, Db)       # [c',t,d,D]
-                Y = np.einsum("tqlw,quvc->tlwuvc", T4, Pl4, optimize=True)
-                Y = np.einsum("tlwuvc,sulde->twvcsde", Y, A, optimize=True)
-                Y = np.einsum("twvcsde,svwDE->tdDceE", Y, B, optimize=True)
-                T4n = np.einsum("atdD,tdDceE->aceE", Pr4, Y, optimize=True)
-                new.append((C1n, T4n, C4n))
+                new.append(absorb_site(
+                    self._get(f, "C", 0, x, y), self._get(f, "T", 0, x, y),
+                    self._get(f, "T", 2, x, y), self._get(f, "C", 3, x, y),
+                    self._get(f, "T", 3, x, y), self._ket(f, x, y), self._bra(f, x, y),
+                    Pl_up, Pr_up, Pl_dn, Pr_dn))
             for y in range(f.Ly):
                 C1n, T4n, C4n = new[y]
                 self._set(f, "C", 0, x + 1, y, self._norm(C1n))

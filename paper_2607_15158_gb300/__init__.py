@@ -24,6 +24,7 @@ CTM_F64, CTM_C128 = 0, 1
 CTM_PREC_FP64, CTM_PREC_SPLIT_BF16 = 0, 1
 CTM_LEFT, CTM_UP, CTM_RIGHT, CTM_DOWN = 0, 1, 2, 3
 CTM_PROJ_SI, CTM_PROJ_SVD = 0, 1
+CTM_INIT_RANDOM, CTM_INIT_FROM_A = 0, 1
 
 
 class ctm_opts(C.Structure):
@@ -31,7 +32,9 @@ class ctm_opts(C.Structure):
                 ("warmup_rounds", C.c_int), ("method", C.c_int),
                 ("prec", C.c_int), ("svd_rel_cutoff", C.c_double),
                 ("normalize", C.c_int), ("sign_fix", C.c_int),
-                ("seed", C.c_uint64), ("stream", C.c_void_p)]
+                ("seed", C.c_uint64), ("svd_max_sweeps", C.c_int), ("init_mode", C.c_int),
+                ("recycle_sin2", C.c_double), ("min_si_steps", C.c_int),
+                ("stream", C.c_void_p)]
 
 
 class ctm_solve_spec(C.Structure):
@@ -83,6 +86,10 @@ def load():
         "ctm_expect_bond": (I, [ctx_p, VP, VP, I, I, I, P(D)]),
         "ctm_free_energy": (I, [ctx_p, P(D)]),
         "ctm_get_projectors": (I, [ctx_p, I, I, I, VP, VP]),
+        "ctm_corner": (I, [ctx_p, I, I, I, I, VP]),
+        "ctm_corner_apply": (I, [ctx_p, I, I, I, I, I, VP, VP]),
+        "ctm_si_stats": (I, [ctx_p, P(C.c_long), P(C.c_long)]),
+        "ctm_debug_fail_alloc": (None, [I]),
         "ctm_last_timing": (I, [ctx_p, P(D), P(C.c_long)]),
         "ctm_profile_enable": (I, [ctx_p, I]),
         "ctm_profile_read": (I, [ctx_p, P(D), P(C.c_long), P(D), P(D)]),
@@ -250,6 +257,27 @@ class Context:
             self.ptr, int(direction), x, y, Pl.ctypes.data, PrH.ctypes.data))
         return Pl, PrH
 
+    def ctm_corner(self, direction, x, y, i):
+        """Enlarged corner Q_i (1..4) of cut (x, y) in the frame of direction,
+        N x N, built by the context's own path and precision."""
+        Q = np.empty((self.N, self.N), self.dtype)
+        _check(self.lib, self.ptr, self.lib.ctm_corner(self.ptr, int(direction), x, y, i,
+                                                       Q.ctypes.data))
+        return Q
+
+    def ctm_corner_apply(self, direction, x, y, i, Z, herm=False):
+        """op(Q_i) Z for a host N x k block (op = conjugate transpose when herm)."""
+        z = _host(Z, self.cplx)
+        out = np.empty((self.N, self.k), self.dtype)
+        _check(self.lib, self.ptr, self.lib.ctm_corner_apply(
+            self.ptr, int(direction), x, y, i, 1 if herm else 0, z.ctypes.data, out.ctypes.data))
+        return out
+
+    def ctm_si_stats(self):
+        u, sk = C.c_long(), C.c_long()
+        _check(self.lib, self.ptr, self.lib.ctm_si_stats(self.ptr, C.byref(u), C.byref(sk)))
+        return u.value, sk.value
+
     def ctm_profile_enable(self, on=True):
         _check(self.lib, self.ptr, self.lib.ctm_profile_enable(self.ptr, 1 if on else 0))
 
@@ -370,6 +398,12 @@ def ctm_svdvals_noalloc(A_dev, k, dtype, s_dev, stream=0):
     if st != CTM_OK:
         raise CTMError(st, (lib.ctm_noalloc_last_error() or b"").decode())
     return st
+
+
+def ctm_debug_fail_alloc(after):
+    """Make the device allocation after `after` successful ones fail (test
+    hook of the error paths); after < 0 disarms it."""
+    load().ctm_debug_fail_alloc(int(after))
 
 
 def ctm_init(Lx, Ly, A, d, D, chi, cplx=None, bra=None, opts=None):

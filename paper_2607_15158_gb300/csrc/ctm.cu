@@ -13,6 +13,7 @@
 //   workspace: four enlarged corners Q[4][N][N], two pipeline buffers and a
 //   scratch arena for the permutes of the pairwise contractions, the N x k
 //   blocks of the subspace iteration and the k x k small problem.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -113,6 +114,14 @@ struct ctm_ctx {
   double* dsc = nullptr;       // column scales of the Jacobi-scaled Gram
   void* fac = nullptr;         // per-tensor normalisation factors
   uint64_t qr_calls = 0;       // counter of the repair directions
+  // recycling policy (opts.recycle_sin2): per direction and cut, the number of
+  // subspace-iteration updates made and whether the next move only recycles
+  std::vector<int> si_updates;
+  std::vector<char> si_skip;
+  std::vector<char> si_rounds_used;   // rounds > 0 in the last move of (r, cut)
+  double* dsin2 = nullptr;     // [4 S] mean sin^2 of the last move of each cut
+  void* sinG = nullptr;        // [Lmax][k k] X_old^H X_upd of the cuts of a column
+  long n_updates = 0, n_skipped = 0;
   int moves_done[4] = {0, 0, 0, 0};
   int num_sms = 1;
   bool spectra_init = false;
@@ -243,8 +252,23 @@ char* at(void* base, size_t elems, const ctm_ctx* c) {
   return static_cast<char*>(base) + elems * c->es;
 }
 
+// remaining successful allocations before an injected failure (< 0: off)
+std::atomic<int> g_fail_alloc_after{-1};
+
 ctm_status dalloc(ctm_ctx* c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  {
+    int left = g_fail_alloc_after.load();
+    while (left >= 0) {
+      if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+        if (left == 0) {
+          *p = nullptr;
+          return fail(c, CTM_ENOMEM, "device allocation failed (injected by ctm_debug_fail_alloc)");
+        }
+        break;
+      }
+    }
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -651,7 +675,21 @@ ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
     ready = 1;
   }
   const bool warm = c->moves_done[r] < c->opts.warmup_iters;
-  const int rounds = warm ? c->opts.warmup_rounds : c->opts.si_rounds;
+  const int rc = r * c->S + cut;
+  // recycling policy (paper step 4): a cut whose leading subspace stopped
+  // moving only recycles its bases, with no update round
+  const int rounds = warm ? c->opts.warmup_rounds
+                          : (c->si_skip[rc] ? 0 : c->opts.si_rounds);
+  c->si_rounds_used[rc] = rounds > 0;
+  if (rounds > 0) {
+    ++c->si_updates[rc];
+    ++c->n_updates;
+  } else {
+    ++c->n_skipped;
+  }
+  const bool track = c->opts.recycle_sin2 > 0.0;
+  if (track && rounds > 0)
+    CTM_CUDA_OK(cudaMemcpyAsync(Z[3], X, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
   // fp64 QR schedule in fp64 contexts and during warm-up, split afterwards
   const bool split_qr = c->split != nullptr && !warm;
   // fp64: a QR after each application of M or M^H (the span of M^H M X
@@ -682,6 +720,13 @@ ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
     CK(apply_corner(c, Q[2], false, Z[0], W));
     CK(qr_inplace(c, W, Z[0], split_qr));
   }
+  if (track && rounds > 0) {
+    // overlap of the bases before and after the update, for the principal
+    // angles of the recycling policy
+    const int opH0 = c->cx ? OP_C : OP_T;
+    CK(mm_small(c, opH0, OP_N, c->k, c->k, c->N, Z[3], c->k, X, c->k,
+                at(c->sinG, (size_t)y * c->k * c->k, c), c->k));
+  }
   // Z_R = Q1 (Q2 X), Z_L = Q4^H (Q3^H W)
   void* ZR = at(c->ZR, y * Nk, c);
   void* ZL = at(c->ZL, y * Nk, c);
@@ -701,7 +746,7 @@ ctm_status si_small_svd(ctm_ctx* c, int n) {
   PhaseScope ps(c, PH_SMALL);
   const int k = c->k;
   CTM_CUDA_OK(jacobi_svd_coop(c->cx, k, c->rho, (long)k * k, c->sv, c->u, c->v, true, c->jw, n,
-                              80, c->err, c->num_sms, c->stream, &c->launches));
+                              c->opts.svd_max_sweeps, c->err, c->num_sms, c->stream, &c->launches));
   return CTM_OK;
 }
 
@@ -738,6 +783,19 @@ ctm_status si_finish(ctm_ctx* c, int r, int cut, int y, void* Pl, void* PrH) {
   } else {
     CK(mm_small(c, OP_N, OP_N, c->N, k, k, X, k, v, k, c->Xn, k));
     CK(mm_small(c, OP_N, OP_N, c->N, k, k, W, k, u, k, c->Wn, k));
+  }
+  if (c->opts.recycle_sin2 > 0.0) {
+    // mean sin^2 of the principal angles between the leading chi-subspaces
+    // of the bases before (X_old) and after (X_upd v) this move:
+    // 1 - ||(X_old^H X_upd v)[:chi, :chi]||_F^2 / chi, with X_old = X_upd when
+    // the move made no update round
+    const int rc = r * c->S + cut;
+    const void* Gv = v;
+    if (c->si_rounds_used[rc]) {
+      CK(mm_small(c, OP_N, OP_N, k, k, k, at(c->sinG, (size_t)y * k * k, c), k, v, k, c->G, k));
+      Gv = c->G;
+    }
+    CTM_CUDA_OK(mean_sin2(c->cx, k, chi, Gv, c->dsin2 + rc, c->stream, &c->launches));
   }
   CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, v, sv, c->opts.svd_rel_cutoff, c->Vs,
                                 c->stream, &c->launches));
@@ -976,7 +1034,7 @@ ctm_status corner_spectra(ctm_ctx* c, double* out) {
   PhaseScope ps(c, PH_SPECTRA);
   // unnormalised singular values of all 4 S corners, [label][site][chi]
   CTM_CUDA_OK(jacobi_svd_coop(c->cx, c->chi, c->C, (long)elems_C(c), out, nullptr, nullptr,
-                              false, c->jw, 4 * c->S, 80, c->err, c->num_sms, c->stream,
+                              false, c->jw, 4 * c->S, c->opts.svd_max_sweeps, c->err, c->num_sms, c->stream,
                               &c->launches));
   return CTM_OK;
 }
@@ -997,6 +1055,18 @@ void fill_normal(std::vector<double>& v, uint64_t seed, uint64_t stream_id, doub
     v[i] = rr * std::cos(6.283185307179586 * u2) * scale;
     if (i + 1 < v.size()) v[i + 1] = rr * std::sin(6.283185307179586 * u2) * scale;
   }
+}
+
+// Forget the recycling history (new rangefinders): every cut updates again.
+ctm_status reset_recycling(ctm_ctx* c) {
+  std::fill(c->si_updates.begin(), c->si_updates.end(), 0);
+  std::fill(c->si_skip.begin(), c->si_skip.end(), 0);
+  std::vector<double> one(4 * c->S, 1.0);
+  if (c->dsin2)
+    CTM_CUDA_OK(cudaMemcpyAsync(c->dsin2, one.data(), one.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream));
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  return CTM_OK;
 }
 
 ctm_status upload_default_state(ctm_ctx* c) {
@@ -1029,6 +1099,61 @@ ctm_status upload_default_state(ctm_ctx* c) {
   c->spectra_init = false;
   c->spectra_fresh = false;
   for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
+  return reset_recycling(c);
+}
+
+// Initial environment from the on-site tensors (init_mode CTM_INIT_FROM_A):
+// corner i of a site is the double layer of the site's tensor turned by i
+// quarter turns with its up and left bond pairs traced, as a (d d') x (r r')
+// matrix; edge i the double layer of the turned tensor with its up pair
+// traced, [(l l')][(r r')][d][d']; both embedded in (or cut to) the
+// top-left block of the chi bonds, then normalised like a move's output.
+ctm_status init_env_from_tensors(ctm_ctx* c) {
+  const long chi = c->chi, Dk = c->Dk, Db = c->Db, d = c->d, DD = Dk * Db;
+  const long m = std::min<long>(chi, DD);
+  if ((size_t)(DD * DD * DD) > c->pipe_elems)
+    return fail(c, CTM_EINVAL, "init_mode CTM_INIT_FROM_A needs chi * d >= D (edge buffer)");
+  CTM_CUDA_OK(cudaMemsetAsync(c->C, 0, 4 * c->S * elems_C(c) * c->es, c->stream));
+  CTM_CUDA_OK(cudaMemsetAsync(c->T, 0, 4 * c->S * elems_T(c) * c->es, c->stream));
+  for (int i = 0; i < 4; ++i) {
+    for (int site = 0; site < c->S; ++site) {
+      void* A = KETp(c, i, site);
+      void* B = BRAp(c, i, site);
+      Tn cc = tn(c->pipe[0], {Dk, Db, Dk, Db});
+      CK(ein(c, "sulde,sulDE->dDeE", tn(A, {d, Dk, Dk, Dk, Dk}), false,
+             tn(B, {d, Db, Db, Db, Db}), false, cc));
+      CTM_CUDA_OK(cudaMemcpy2DAsync(Cp(c, i, site), chi * c->es, cc.p, DD * c->es, m * c->es, m,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+      Tn tt = tn(c->pipe[1], {Dk, Db, Dk, Db, Dk, Db});
+      CK(ein(c, "sulde,suLDE->lLeEdD", tn(A, {d, Dk, Dk, Dk, Dk}), false,
+             tn(B, {d, Db, Db, Db, Db}), false, tt));
+      CTM_CUDA_OK(cudaMemcpy2DAsync(Tp(c, i, site), chi * DD * c->es, tt.p, DD * DD * c->es,
+                                    m * DD * c->es, m, cudaMemcpyDeviceToDevice, c->stream));
+    }
+  }
+  const size_t mark = c->scratch_off;
+  void* w = scratch_alloc(c, (size_t)3 * 152 * 4 * c->S * sizeof(double));
+  void* f = scratch_alloc(c, (size_t)4 * c->S * c->es);
+  if (!w || !f) return fail(c, CTM_ENOMEM, "scratch arena too small for the norms");
+  CTM_CUDA_OK(normalize_phase(c->cx, elems_C(c), c->C, elems_C(c), 4 * c->S, f, w, c->stream,
+                              &c->launches));
+  CTM_CUDA_OK(normalize_phase(c->cx, elems_T(c), c->T, elems_T(c), 4 * c->S, f, w, c->stream,
+                              &c->launches));
+  c->scratch_off = mark;
+  return CTM_OK;
+}
+
+// After a synchronisation: fold the mean sin^2 of the last moves into the
+// recycling decisions (a cut recycles without an update round while its
+// angle stays below recycle_sin2, once it had min_si_steps updates).
+ctm_status update_recycling(ctm_ctx* c) {
+  if (!(c->opts.recycle_sin2 > 0.0)) return CTM_OK;
+  std::vector<double> h(4 * c->S);
+  CTM_CUDA_OK(cudaMemcpyAsync(h.data(), c->dsin2, h.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < h.size(); ++i)
+    c->si_skip[i] = (h[i] < c->opts.recycle_sin2 && c->si_updates[i] >= c->opts.min_si_steps) ? 1 : 0;
   return CTM_OK;
 }
 
@@ -1050,10 +1175,14 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   if (opts) c->opts = *opts;
   else ctm_default_opts(&c->opts);
   if (c->opts.p < 0 || c->opts.si_rounds < 0 || c->opts.warmup_iters < 0 ||
-      c->opts.warmup_rounds < 0) {
+      c->opts.warmup_rounds < 0 || c->opts.svd_max_sweeps < 1 || c->opts.min_si_steps < 0 ||
+      !(c->opts.recycle_sin2 >= 0.0) ||
+      (c->opts.init_mode != CTM_INIT_RANDOM && c->opts.init_mode != CTM_INIT_FROM_A)) {
     delete c;
     g_cur = nullptr;
-    return fail(nullptr, CTM_EINVAL, "p and si_rounds must be >= 0");
+    return fail(nullptr, CTM_EINVAL,
+                "p, si_rounds, warm-up counts and min_si_steps must be >= 0, svd_max_sweeps >= 1, "
+                "recycle_sin2 >= 0, init_mode 0 or 1");
   }
   c->N = chi * Dk * Db;
   c->k = std::min(chi + c->opts.p, c->N);
@@ -1141,7 +1270,12 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->chol_work, chol_coop_work_bytes((int)k, 1));
   AL(c->dsc, k * sizeof(double));
   AL(c->fac, Lmax * es);
+  AL(c->dsin2, 4 * S * sizeof(double));
+  AL(c->sinG, Lmax * k * k * es);
 #undef AL
+  c->si_updates.assign(4 * S, 0);
+  c->si_skip.assign(4 * S, 0);
+  c->si_rounds_used.assign(4 * S, 0);
   // every upload goes through the context's stream: a copy on the legacy
   // default stream is not ordered before kernels on a non-blocking stream
   if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess)
@@ -1182,6 +1316,8 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
     }
   }
   if ((st = upload_default_state(c)) != CTM_OK) return bail(st);
+  if (c->opts.init_mode == CTM_INIT_FROM_A && (st = init_env_from_tensors(c)) != CTM_OK)
+    return bail(st);
   if (c->opts.prec == CTM_PREC_SPLIT_BF16) {
     st = split_create(&c->split, cx, (int)N, (int)k, c->err, c->stream);
     if (st != CTM_OK) {
@@ -1403,6 +1539,10 @@ void ctm_default_opts(ctm_opts* o) {
   o->normalize = 1;
   o->sign_fix = 1;
   o->seed = 0;
+  o->svd_max_sweeps = 80;
+  o->init_mode = CTM_INIT_RANDOM;
+  o->recycle_sin2 = 0.0;
+  o->min_si_steps = 3;
   o->stream = nullptr;
 }
 
@@ -1447,7 +1587,7 @@ ctm_status ctm_set_rangefinders(ctm_ctx* c, const void* X, const void* W) {
   CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
   for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
-  return CTM_OK;
+  return reset_recycling(c);
 }
 
 // ------------------------------------------------------------ footprint
@@ -1478,6 +1618,7 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
   b += std::max(Lmax * k, 4 * S * (size_t)chi) * sizeof(double);
   b += Lmax * (2 * eC + eT) * es + 8 * S * chi * sizeof(double);
   b += 2 * (size_t)d * d * d * d * es + 2 * nk * es + ((size_t)1 << 20);
+  b += Lmax * k * k * es + 4 * S * sizeof(double);   // recycling policy
   if (o->prec == CTM_PREC_SPLIT_BF16) {
     const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
     b += 8 * 3 * N * Kp * 2;                       // corner slices, both orientations
@@ -1621,6 +1762,7 @@ ctm_status ctm_move(ctm_ctx* c, ctm_dir dir) {
   CK(move_impl(c, (int)dir));
   CTM_CUDA_OK(cudaEventRecord(c->ev1, c->stream));
   CK(check_err(c));
+  CK(update_recycling(c));
   float ms = 0.f;
   CTM_CUDA_OK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   c->last_ms = ms;
@@ -1652,6 +1794,7 @@ ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, do
     c->spectra_fresh = true;
     CTM_CUDA_OK(cudaMemcpyAsync(&delta, c->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(check_err(c));
+    CK(update_recycling(c));
     if (delta < tol) break;
   }
   CTM_CUDA_OK(cudaEventRecord(c->ev1, c->stream));
@@ -1675,7 +1818,7 @@ ctm_status ctm_spectrum(ctm_ctx* c, int x, int y, int label, double* s_out) {
   Guard gd(c);
   const int site = y * c->Lx + x;
   CTM_CUDA_OK(jacobi_svd_coop(c->cx, c->chi, Cp(c, label - 1, site), 0, c->sv, nullptr,
-                              nullptr, false, c->jw, 1, 80, c->err, c->num_sms, c->stream,
+                              nullptr, false, c->jw, 1, c->opts.svd_max_sweeps, c->err, c->num_sms, c->stream,
                               &c->launches));
   CTM_CUDA_OK(normalize(false, c->chi, c->sv, 0, 1, c->dscal, true, c->scratch, c->stream, &c->launches));
   CTM_CUDA_OK(cudaMemcpyAsync(s_out, c->sv, c->chi * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1839,6 +1982,53 @@ ctm_status ctm_get_projectors(ctm_ctx* c, ctm_dir dir, int x, int y, void* Pl, v
   CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
   return CTM_OK;
 }
+
+ctm_status ctm_corner(ctm_ctx* c, ctm_dir dir, int x, int y, int i, void* Q_out) {
+  if (!c || !Q_out) return fail(c, CTM_EINVAL, "NULL argument");
+  const int r = (int)dir;
+  if (r < 0 || r > 3 || i < 1 || i > 4) return fail(c, CTM_EINVAL, "bad direction or corner");
+  const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
+  if (x < 0 || y < 0 || x >= Lxf || y >= Lyf) return fail(c, CTM_EINVAL, "bad cut");
+  Guard gd(c);
+  use_lane(c, 0);
+  CK(enlarged_corner(c, r, i - 1, x, y, c->Q[i - 1]));
+  CTM_CUDA_OK(cudaMemcpyAsync(Q_out, c->Q[i - 1], (size_t)c->N * c->N * c->es,
+                              cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  return CTM_OK;
+}
+
+ctm_status ctm_corner_apply(ctm_ctx* c, ctm_dir dir, int x, int y, int i, int herm,
+                            const void* Z_in, void* Z_out) {
+  if (!c || !Z_in || !Z_out) return fail(c, CTM_EINVAL, "NULL argument");
+  const int r = (int)dir;
+  if (r < 0 || r > 3 || i < 1 || i > 4) return fail(c, CTM_EINVAL, "bad direction or corner");
+  const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
+  if (x < 0 || y < 0 || x >= Lxf || y >= Lyf) return fail(c, CTM_EINVAL, "bad cut");
+  Guard gd(c);
+  use_lane(c, 0);
+  const size_t Nk = (size_t)c->N * c->k;
+  CK(enlarged_corner(c, r, i - 1, x, y, c->Q[i - 1]));
+  if (c->split) {
+    const ctm_status st = split_prepare_corners(c->split, c->Q, c->N, 1u << (i - 1), c->stream,
+                                                &c->launches);
+    if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+  }
+  CTM_CUDA_OK(cudaMemcpyAsync(c->Z[0], Z_in, Nk * c->es, cudaMemcpyHostToDevice, c->stream));
+  CK(apply_corner(c, c->Q[i - 1], herm != 0, c->Z[0], c->Z[1]));
+  CTM_CUDA_OK(cudaMemcpyAsync(Z_out, c->Z[1], Nk * c->es, cudaMemcpyDeviceToHost, c->stream));
+  CK(check_err(c));
+  return CTM_OK;
+}
+
+ctm_status ctm_si_stats(const ctm_ctx* c, long* updates, long* skipped) {
+  if (!c) return CTM_EINVAL;
+  if (updates) *updates = c->n_updates;
+  if (skipped) *skipped = c->n_skipped;
+  return CTM_OK;
+}
+
+void ctm_debug_fail_alloc(int after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
 
 ctm_status ctm_last_timing(const ctm_ctx* c, double* ms, long* launches) {
   if (!c) return CTM_EINVAL;

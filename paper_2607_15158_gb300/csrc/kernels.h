@@ -170,6 +170,12 @@ cudaError_t normalize(bool cx, long n, void* x, long stride, int batch,
 cudaError_t spectra_delta(int c, int batch, double* snew, double* sold,
                           double* delta, cudaStream_t s, long* launches);
 
+// out = 1 - ||M[:c, :c]||_F^2 / c for a k x k row-major M: the mean sin^2
+// of the principal angles between two c-dimensional subspaces whose
+// orthonormal bases have overlap matrix M[:c, :c].
+cudaError_t mean_sin2(bool cx, int k, int c, const void* M, double* out, cudaStream_t s,
+                      long* launches);
+
 // G += alpha * I for batch k x k matrices
 cudaError_t add_identity(bool cx, int k, void* G, double alpha, int batch,
                          cudaStream_t s, long* launches);

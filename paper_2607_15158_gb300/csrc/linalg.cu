@@ -966,3 +966,37 @@ cudaError_t trace_products(bool cx, int d2, const void* O, const void* R, double
 }
 
 }  // namespace ctm
+
+namespace ctm {
+namespace {
+
+// out = 1 - ||M[:c, :c]||_F^2 / c for a k x k row-major M (one block)
+template <typename T>
+__global__ void mean_sin2_kernel(int k, int c, const T* M, double* out) {
+  __shared__ double part[32];
+  double acc = 0.0;
+  for (long idx = threadIdx.x; idx < (long)c * c; idx += blockDim.x) {
+    const long i = idx / c, j = idx % c;
+    acc += absq(M[i * k + j]);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) *out = 1.0 - v / (double)c;
+  }
+}
+
+}  // namespace
+
+cudaError_t mean_sin2(bool cx, int k, int c, const void* M, double* out, cudaStream_t s,
+                      long* launches) {
+  if (cx) mean_sin2_kernel<cplx><<<1, 256, 0, s>>>(k, c, (const cplx*)M, out);
+  else mean_sin2_kernel<double><<<1, 256, 0, s>>>(k, c, (const double*)M, out);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace ctm

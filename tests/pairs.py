@@ -13,10 +13,12 @@ import paper_2607_15158_gb300 as pkg
 from oracle import ctmrg
 
 
-def make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, seed=0, diag=0.0, **opt_kw):
-    """Context and oracle CTM of one seeded problem: A from seed, C/T from
-    seed 1, rangefinders from seed 2; opt_kw go to ctm_default_opts."""
-    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, seed=seed, diag_weight=diag)
+def make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, seed=0, diag=0.0, decay=1.0, **opt_kw):
+    """Context and oracle CTM of one seeded problem: A from seed (bond weights
+    decaying as decay^(u+l+d+r)), C/T from seed 1, rangefinders from seed 2;
+    opt_kw go to ctm_default_opts."""
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, seed=seed, diag_weight=diag,
+                        bond_decay=decay)
     Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx, seed=1)
     N = chi * D * D
     k = min(chi + p, N)
@@ -29,7 +31,8 @@ def make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, seed=0, diag=0.0, **opt_kw):
                     method="svd" if opts.method == pkg.CTM_PROJ_SVD else "si",
                     p=opts.p, si_rounds=opts.si_rounds, X0=X0, W0=W0,
                     cutoff=opts.svd_rel_cutoff, warmup_iters=opts.warmup_iters,
-                    warmup_rounds=opts.warmup_rounds)
+                    warmup_rounds=opts.warmup_rounds, recycle_sin2=opts.recycle_sin2,
+                    min_si_steps=opts.min_si_steps)
     return ctx, ref
 
 

@@ -109,6 +109,9 @@ def test_single_moves_each_direction():
     # shared memory, so the QR passes take the cooperative Cholesky with an
     # explicit inverse, and the Jacobi SVD nine columns per lane
     (1, 1, 2, 2, 170, 5, True, 1),
+    # the same block size on a 1 x 2 cell: two cuts per column on concurrent
+    # lanes, each with its own cooperative-Cholesky scratch
+    (1, 2, 2, 2, 170, 5, True, 1),
     # D = 7 complex fp64: A, B and the 49 x 49 pair tiles exceed one block's
     # shared memory, so the absorption runs unfused (two GEMMs, permutes)
     (1, 1, 2, 7, 4, 3, True, 1),
@@ -123,10 +126,14 @@ def test_large_block_and_unfused_absorption_track_oracle(case):
         ref.left_move(r)
     spec = ref.spectra()
     for lab in range(4):
-        s = ctx.ctm_spectrum(0, 0, lab + 1)
-        assert np.abs(s - spec[lab][0]).max() < 1e-9, lab
-    Pl, PrH = ctx.ctm_get_projectors(1, 0, 0)
-    assert np.abs(PrH.conj().T @ Pl - np.eye(Pl.shape[1])).max() < 1e-9
+        for i in range(Lx * Ly):
+            s = ctx.ctm_spectrum(i % Lx, i // Lx, lab + 1)
+            assert np.abs(s - spec[lab][i]).max() < 1e-9, (lab, i)
+    f = ctmrg.Frame(Lx, Ly, 1)
+    for y in range(f.Ly):
+        for x in range(f.Lx):
+            Pl, PrH = ctx.ctm_get_projectors(1, x, y)
+            assert np.abs(PrH.conj().T @ Pl - np.eye(Pl.shape[1])).max() < 1e-9
     ctx.ctm_free()
 
 
@@ -179,7 +186,7 @@ def test_ising_onsager_on_gpu():
 
 def test_ising_yang_on_gpu():
     beta = 0.50
-    ctx, ref = _ising_ctx(beta, 12)
+    ctx, ref = _ising_ctx(beta, 16)     # truncation at a gap of the multiplets
     ctx.ctm_converge(1e-11, 300)
     ref.converge(1e-11, 300)
     imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)
@@ -255,4 +262,45 @@ def test_batched_spectra_match_single_corner_calls():
     C, T = ctx.ctm_get_env()
     ctx.ctm_set_env(C, T)
     assert np.abs(ctx.ctm_spectra() - allspec).max() < 1e-13
+    ctx.ctm_free()
+
+
+def test_environment_from_tensors_matches_oracle():
+    """init_mode CTM_INIT_FROM_A: the initial corners and edges equal the
+    oracle's environment built from the tensors (element by element), and the
+    iteration from there converges to the oracle's fixed point."""
+    Lx, Ly, d, D, chi, p = 2, 1, 2, 2, 10, 5
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=True, seed=0)
+    B = [a.conj() for a in A]
+    ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=True,
+                       opts=pkg.ctm_default_opts(p=p, init_mode=pkg.CTM_INIT_FROM_A))
+    C0, T0 = ctmrg.env_from_tensors(Lx, Ly, A, B, chi)
+    C, T = ctx.ctm_get_env()
+    assert np.abs(C - np.array(C0)).max() < 1e-14
+    assert np.abs(T - np.array(T0)).max() < 1e-14
+    N, k = chi * D * D, chi + p
+    X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=True, seed=2)
+    ctx.ctm_set_rangefinders(X0, W0)
+    ref = ctmrg.CTM(Lx, Ly, A, B, C0, T0, chi, method="si", p=p, X0=X0, W0=W0,
+                    warmup_iters=5, warmup_rounds=8)
+    _, _, ok = ctx.ctm_converge(1e-11, 200)
+    _, d_ref = ref.converge(1e-11, 200)
+    assert ok and d_ref < 1e-11
+    _compare(ctx, ref)
+    ctx.ctm_free()
+
+
+def test_recycling_policy_matches_oracle():
+    """Recycling policy of step 4 (updates skipped once the mean sin^2 of the
+    principal angles is below 1e-3, after at least 3 updates): the device
+    takes the same update / skip decisions as the oracle and reaches the same
+    environment."""
+    ctx, ref = make_pair(2, 2, 2, 2, 8, 5, True, 1, recycle_sin2=1e-3, min_si_steps=3)
+    _, _, ok = ctx.ctm_converge(1e-11, 200)
+    _, d_ref = ref.converge(1e-11, 200)
+    assert ok and d_ref < 1e-11
+    upd, skipped = ctx.ctm_si_stats()
+    assert skipped > 0
+    assert (upd, skipped) == (ref.n_updates, ref.n_skipped)
+    _compare(ctx, ref)
     ctx.ctm_free()

@@ -13,6 +13,7 @@ import pytest
 import ctm_synth as S
 import paper_2607_15158_gb300 as pkg
 from oracle import ctmrg
+from pairs import make_pair
 
 pytestmark = pytest.mark.gpu
 HEIS = S.heisenberg_bond()
@@ -87,3 +88,33 @@ def test_converged_split_matches_fp64_and_oracle(case):
                 assert abs(b.ctm_expect(HEIS, x, y, direction) - e_ref) < TOL_SPLIT
     a.ctm_free()
     b.ctm_free()
+
+
+@pytest.mark.parametrize("case", [
+    # Lx, Ly, d, D, chi, p, complex, rounds, bond decay
+    # D = 6: the compile-time D = 6 variant of the fused fp32 absorption (the
+    # one the full-size workload runs), two cuts per column on lanes
+    (2, 2, 2, 6, 8, 5, True, 1, 0.5),
+    # D = 8: the compile-time D = 8 variant (16 x 16 threads, 4 x 4 tiles)
+    (1, 1, 2, 8, 6, 5, True, 1, 0.5),
+])
+def test_converged_split_large_D_matches_oracle(case):
+    """Split precision at D = 6 and D = 8, converged, against the FP64
+    oracle on the same inputs (random states with geometrically decaying bond
+    weights, which converge at small chi). The measured differences of the
+    unit-normalised corner spectra and of the Heisenberg bond energies are
+    printed."""
+    Lx, Ly, d, D, chi, p, cplx, rounds, q = case
+    ctx, ref = make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, decay=q,
+                         prec=pkg.CTM_PREC_SPLIT_BF16)
+    it, delta, _ = ctx.ctm_converge(1e-9, 150)
+    it_ref, d_ref = ref.converge(1e-11, 150)
+    assert d_ref < 1e-11 and delta < 1e-6
+    spec = ref.spectra()
+    es = max(float(np.abs(ctx.ctm_spectrum(x, y, lab + 1) - spec[lab][y * Lx + x]).max())
+             for lab in range(4) for y in range(Ly) for x in range(Lx))
+    ee = max(abs(ctx.ctm_expect(HEIS, x, y, dr) - ref.expect2(HEIS, x, y, dr))
+             for y in range(Ly) for x in range(Lx) for dr in (0, 1))
+    print(f"split D={D}: spectra {es:.2e}, energies {ee:.2e}, delta {delta:.1e}, it {it}")
+    assert es < TOL_SPLIT and ee < TOL_SPLIT
+    ctx.ctm_free()

@@ -85,11 +85,13 @@ def test_ctm_onsager_beta040(method):
 
 @pytest.mark.parametrize("method", ["svd", "si"])
 def test_ctm_yang_beta050(method):
-    """P2: spontaneous magnetisation (Yang) at beta = 0.50. The corner
-    spectrum is effectively of rank ~10 here, so chi = 12 keeps it above the
-    fp64 noise floor (a much larger chi keeps zero directions)."""
+    """P2: spontaneous magnetisation (Yang) at beta = 0.50. Deep in the
+    ordered phase the corner spectrum comes in multiplets with exact zeros;
+    chi = 16 truncates at a gap (reading c10), where both methods converge
+    to 1e-11 (chi = 9 .. 12 cut through a multiplet and the iteration
+    wanders at the 1e-4 .. 1e-7 level)."""
     beta = 0.50
-    ctm = _ising_ctm(beta, 12, method)
+    ctm = _ising_ctm(beta, 16, method)
     ctm.converge(1e-11, 300)
     imp = S.ising_tensor(beta, impurity=True).reshape(1, 2, 2, 2, 2)
     assert abs(abs(ctm.site_ratio(0, 0, imp)) - ising.yang_m(beta)) < 1e-10
@@ -373,3 +375,67 @@ def test_unit_cell_of_identical_tensors_repeats_the_single_site_move():
         for lab in (0, 3):
             assert np.abs(cell.C[lab][y * 2 + 1] - first[lab]).max() < 1e-12
             assert np.abs(cell.C[lab][y * 2 + 0] - one.C[lab][0]).max() < 1e-12
+
+
+# ------------------------------------------- initial environment, recycling
+
+@pytest.mark.parametrize("pad", [0, 3])
+def test_env_from_tensors_is_the_traced_boundary_patch(pad):
+    """The environment built from the tensors (corners and edges of the
+    double layer with their outer bond pairs traced) is the boundary of a
+    finite patch closed by an identity ring: the two-site density matrices of
+    the initial environment equal a brute-force contraction of the 4x3 / 3x4
+    patch whose ring of chi = 1 tensors traces every outer bond pair. Extra
+    bond indices (chi > D^2) are zero and change nothing."""
+    D = 2
+    A = S.ipeps_tensors(1, 1, 2, D, complex_=True, seed=12)
+    B = [a.conj() for a in A]
+    chi = D * D + pad
+    C, T = ctmrg.env_from_tensors(1, 1, A, B, chi)
+    ctm = ctmrg.CTM(1, 1, A, B, C, T, chi, method="svd")
+    ring_C = [np.ones((1, 1))] * 4
+    ring_T = [np.eye(D).reshape(1, 1, D, D)] * 4
+    for direction, (pw, ph), sites in ((0, (4, 3), ((1, 1), (2, 1))),
+                                       (1, (3, 4), ((1, 1), (1, 2)))):
+        R = exact.finite_patch(ring_C, ring_T, A[0], B[0], pw, ph, open_sites=sites)
+        R = R.reshape(4, 4)
+        R = R / np.trace(R)
+        assert np.abs(ctm.rdm2(0, 0, direction) - R).max() < 1e-12
+
+
+def test_recorded_sin2_is_the_mean_principal_angle():
+    """The recycling policy's measure: the mean sin^2 recorded for a cut is
+    that of the principal angles (scipy.linalg.subspace_angles) between the
+    leading chi-subspaces of the bases before and after the move."""
+    from scipy.linalg import subspace_angles
+    ctm = _random_cell("si", Lx=1, Ly=1, D=2, chi=8, cplx=True, seed=4)
+    ctm.iteration()
+    Xb = ctm.rf[(0, 0)][0].copy()
+    ctm.left_move(0)
+    Xa = ctm.rf[(0, 0)][0]
+    th = subspace_angles(Xb[:, :8], Xa[:, :8])
+    assert abs(ctm.last[(0, 0, 0)]["sin2"] - np.mean(np.sin(th) ** 2)) < 1e-12
+
+
+def test_recycling_policy_keeps_the_fixed_point_to_its_accuracy():
+    """Step 4 recycling: skipping the update rounds of cuts whose leading
+    subspace has settled (sin^2 < 1e-3 after at least 3 updates) converges,
+    with fewer updates, to a fixed point within the accuracy the threshold
+    allows: the frozen bases hold the leading subspace only as well as it had
+    settled when updates stopped (the paper's "for the accuracy concerned"),
+    so spectra and energies move by ~1e-6 here, not 1e-12."""
+    res = {}
+    for thr in (0.0, 1e-3):
+        ctm = _random_cell("si", Lx=1, Ly=1, D=2, chi=12, cplx=False, rounds=2, seed=4)
+        ctm.recycle_sin2 = thr
+        it, delta = ctm.converge(1e-12, 400)
+        assert delta < 1e-12
+        res[thr] = ctm
+    a, b = res[0.0], res[1e-3]
+    assert a.n_skipped == 0 and b.n_skipped > 0
+    # every cut made at least min_si_steps updates before it skipped
+    assert min(b.si_updates.values()) >= b.min_si_steps
+    for lab in range(4):
+        assert np.abs(a.spectra()[lab][0] - b.spectra()[lab][0]).max() < 1e-4
+    for direction in (0, 1):
+        assert abs(a.expect2(HEIS, 0, 0, direction) - b.expect2(HEIS, 0, 0, direction)) < 1e-4

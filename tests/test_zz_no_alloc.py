@@ -43,6 +43,25 @@ def _noalloc(mat, cplx):
     return s.cpu().numpy()
 
 
+def test_noalloc_calls_leave_free_device_memory_unchanged():
+    """After a first call on the device (which looks up the scratch address),
+    further calls change the device's free memory by nothing: the call itself
+    allocates no device memory."""
+    rng = np.random.default_rng(7)
+    k = 64
+    m = rng.standard_normal((k, k))
+    a = torch.from_numpy(np.asfortranarray(m).ravel(order="F").copy()).cuda()
+    s = torch.empty(k, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    pkg.ctm_svdvals_noalloc(a.data_ptr(), k, pkg.CTM_F64, s.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        pkg.ctm_svdvals_noalloc(a.data_ptr(), k, pkg.CTM_F64, s.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 def test_noalloc_matches_ctm_spectrum_twice(cplx):
     ctx = _ctx(cplx)
