@@ -101,6 +101,10 @@ typedef struct {
                              recycled, with no subspace-iteration round, until
                              the angle grows above it again; 0 = always update */
   int min_si_steps;       /* see recycle_sin2 (paper: at least 3) */
+  int absorb_tc;          /* split contexts: 1 = the A / conj(A) absorption as
+                             split bf16 tensor-core GEMMs with permutes (the
+                             accuracy of the other products), 0 = one fused
+                             kernel in fp32 arithmetic */
   void* stream;           /* cudaStream_t to run on, NULL = a private stream */
 } ctm_opts;
 
@@ -116,7 +120,7 @@ enum { CTM_INIT_RANDOM = 0, CTM_INIT_FROM_A = 1 };
 /* Defaults: p = 5, si_rounds = 1, warmup_iters = 5, warmup_rounds = 8, SI,
  * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0,
  * svd_max_sweeps = 80, init_mode = CTM_INIT_RANDOM, recycle_sin2 = 0 (always
- * update), min_si_steps = 3, stream = NULL. */
+ * update), min_si_steps = 3, absorb_tc = 0, stream = NULL. */
 void ctm_default_opts(ctm_opts* opts);
 
 /* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz

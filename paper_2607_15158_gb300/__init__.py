@@ -34,7 +34,7 @@ class ctm_opts(C.Structure):
                 ("normalize", C.c_int), ("sign_fix", C.c_int),
                 ("seed", C.c_uint64), ("svd_max_sweeps", C.c_int), ("init_mode", C.c_int),
                 ("recycle_sin2", C.c_double), ("min_si_steps", C.c_int),
-                ("stream", C.c_void_p)]
+                ("absorb_tc", C.c_int), ("stream", C.c_void_p)]
 
 
 class ctm_solve_spec(C.Structure):

@@ -20,160 +20,14 @@
 #include <string>
 #include <vector>
 
-#include "common.cuh"
-#include "ctm.h"
-#include "kernels.h"
-#include "split_gemm.h"
-#include "svd_proj.h"
+#include "ctx.h"
 
 using namespace ctm;
+using namespace ctmi;
 
-namespace {
+namespace ctmi {
 
 thread_local std::string g_create_error;
-
-struct Tn {
-  void* p = nullptr;
-  int r = 0;
-  long d[8] = {0};
-  long size() const {
-    long s = 1;
-    for (int i = 0; i < r; ++i) s *= d[i];
-    return s;
-  }
-};
-
-Tn tn(void* p, std::initializer_list<long> dims) {
-  Tn t;
-  t.p = p;
-  for (long x : dims) t.d[t.r++] = x;
-  return t;
-}
-
-struct StatusError {
-  ctm_status st;
-  std::string msg;
-};
-
-}  // namespace
-
-struct ctm_ctx {
-  int Lx = 0, Ly = 0, S = 0, d = 0, Dk = 0, Db = 0, chi = 0, N = 0, k = 0;
-  bool cx = false;
-  size_t es = 8;
-  ctm_opts opts{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  std::vector<void*> allocs;
-  // tensors
-  void* ket[4] = {nullptr};  // [S][d Dk^4] per rotation
-  void* bra[4] = {nullptr};  // [S][d Db^4]
-  void* C = nullptr;         // [4][S][chi^2]
-  void* T = nullptr;         // [4][S][chi^2 Dk Db]
-  void* X = nullptr;         // [4][S][N k]
-  void* W = nullptr;
-  std::vector<char> rf_ready;
-  // workspace
-  void* Q[4] = {nullptr};
-  void* pipe[2] = {nullptr};
-  size_t pipe_elems = 0;
-  char* scratch = nullptr;
-  size_t scratch_bytes = 0, scratch_off = 0;
-  void* Pl = nullptr;        // [Lmax][N chi] current column
-  void* PrH = nullptr;
-  void* lastPl = nullptr;    // [S][N chi] of the last move
-  void* lastPrH = nullptr;
-  int last_dir = -1;
-  void* Z[4] = {nullptr};    // N x k blocks
-  void* ZR = nullptr;        // [Lmax][N k] Z_R, Z_L of the cuts of a column
-  void* ZL = nullptr;
-  void* Xn = nullptr;
-  void* Wn = nullptr;
-  void* G = nullptr;         // k x k
-  void* Linv = nullptr;
-  void* rho = nullptr;       // [Lmax][k k]
-  void* u = nullptr;         // [Lmax][k k]
-  void* v = nullptr;
-  void* jw = nullptr;        // Jacobi work, max(2 Lmax k^2, 8 S chi^2) elements
-  void* ph = nullptr;
-  void* Vs = nullptr;        // k x chi
-  void* Us = nullptr;
-  double* sv = nullptr;      // max(Lmax k, 4 S chi)
-  void* stC1 = nullptr;      // staging [Lmax][chi^2]
-  void* stC4 = nullptr;
-  void* stT4 = nullptr;      // [Lmax][chi^2 Dk Db]
-  double* spec_old = nullptr;  // [4 S][chi]
-  double* spec_new = nullptr;
-  double* dscal = nullptr;     // small device scalars
-  void* op = nullptr;          // d^4 operator
-  void* rho2 = nullptr;        // d^4 two-site density matrix
-  void* imp[2] = {nullptr};    // impurity kets
-  int* err = nullptr;
-  int* dead = nullptr;         // k flags of the CholeskyQR repair
-  void* chol_work = nullptr;   // cooperative Cholesky scratch
-  double* dsc = nullptr;       // column scales of the Jacobi-scaled Gram
-  void* fac = nullptr;         // per-tensor normalisation factors
-  uint64_t qr_calls = 0;       // counter of the repair directions
-  // recycling policy (opts.recycle_sin2): per direction and cut, the number of
-  // subspace-iteration updates made and whether the next move only recycles
-  std::vector<int> si_updates;
-  std::vector<char> si_skip;
-  std::vector<char> si_rounds_used;   // rounds > 0 in the last move of (r, cut)
-  double* dsin2 = nullptr;     // [4 S] mean sin^2 of the last move of each cut
-  void* sinG = nullptr;        // [Lmax][k k] X_old^H X_upd of the cuts of a column
-  long n_updates = 0, n_skipped = 0;
-  int moves_done[4] = {0, 0, 0, 0};
-  int num_sms = 1;
-  bool spectra_init = false;
-  // spec_old holds the normalised spectra of the current C (set by the
-  // convergence measure, cleared by anything that changes C)
-  bool spectra_fresh = false;
-  // split-precision state
-  SplitCtx* split = nullptr;
-  // lanes: the cuts of a column are independent until their small SVDs, so
-  // they run concurrently, each on its own stream with its own corners and
-  // workspace; use_lane() points the fields above at lane i
-  struct Lane {
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
-    void* Q[4] = {nullptr};
-    void* pipe[2] = {nullptr};
-    char* scratch = nullptr;
-    size_t scratch_bytes = 0;
-    SplitCtx* split = nullptr;
-    void* Z[4] = {nullptr};
-    void* G = nullptr;
-    void* Linv = nullptr;
-    double* dsc = nullptr;
-    int* dead = nullptr;
-    void* chol_work = nullptr;   // cooperative Cholesky scratch (large k)
-  };
-  std::vector<Lane> lanes;   // lane 0 = the context's own buffers and stream
-  int cur_lane = 0;
-  // standard truncated-SVD projectors (CTM_PROJ_SVD)
-  SvdCtx* svd = nullptr;
-  void* svdM = nullptr;      // N x N
-  void* svdUs = nullptr;     // N x chi
-  void* svdVs = nullptr;
-  // phase timing (profiling)
-  bool prof = false;
-  std::vector<cudaEvent_t> pev;
-  std::vector<int> pph;
-  size_t pev_used = 0;
-  double phase_ms[CTM_NPHASES] = {0};
-  // bookkeeping
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  double last_ms = 0.0;
-  long launches = 0, last_launches = 0;
-  std::string msg;
-};
-
-namespace ctm {
-ctm_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line);
-}
-
-namespace {
-
 thread_local ctm_ctx* g_cur = nullptr;
 
 ctm_status fail(ctm_ctx* c, ctm_status st, const std::string& m) {
@@ -182,26 +36,21 @@ ctm_status fail(ctm_ctx* c, ctm_status st, const std::string& m) {
   return st;
 }
 
-}  // namespace
+}  // namespace ctmi
 
 namespace ctm {
 ctm_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line) {
   char buf[512];
   snprintf(buf, sizeof buf, "CUDA error %s (%s) at %s:%d in %s", cudaGetErrorName(e),
            cudaGetErrorString(e), file, line, expr);
-  if (g_cur) g_cur->msg = buf;
-  else g_create_error = buf;
+  if (ctmi::g_cur) ctmi::g_cur->msg = buf;
+  else ctmi::g_create_error = buf;
   return e == cudaErrorMemoryAllocation ? CTM_ENOMEM : CTM_ECUDA;
 }
 }  // namespace ctm
 
-#define CK(expr)                                \
-  do {                                          \
-    ctm_status st__ = (expr);                   \
-    if (st__ != CTM_OK) return st__;            \
-  } while (0)
 
-namespace {
+namespace ctmi {
 
 enum Phase { PH_CORNER = 0, PH_SLICE, PH_PROD, PH_QR, PH_SMALL, PH_ABSORB, PH_NORM, PH_SPECTRA };
 
@@ -352,6 +201,15 @@ ctm_status gemm(ctm_ctx* c, GemmDesc& g) {
   CTM_CUDA_OK(gemm64(g, work, wb, c->stream, &c->launches));
   c->scratch_off = mark;
   return CTM_OK;
+}
+
+// The A / conj(A) absorption runs as one fused kernel (fp32 arithmetic in
+// split contexts) where it fits, unless a split context asks for it on the
+// tensor cores (opts.absorb_tc): then it is two split-precision GEMMs with
+// permutes, as accurate as the other products.
+bool use_fused_absorb(bool cx, bool split, const ctm_opts& o, int Dk, int Db, int d) {
+  if (split && o.absorb_tc) return false;
+  return absorb_ab_supported(cx, split, Dk, Db, d);
 }
 
 // contractions with at least this many multiply-adds go to the split-precision
@@ -513,7 +371,7 @@ ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
   CK(ein(c, "pm,mnuv->pnuv", tn(Cc, {chi, chi}), false, tn(Ta, {chi, chi, Dk, Db}), false, CT));
   Tn CTT = tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db});
   CK(ein(c, "tplw,pnuv->tlwnuv", tn(Tb, {chi, chi, Dk, Db}), false, CT, false, CTT));
-  if (absorb_ab_supported(c->cx, c->split != nullptr, (int)Dk, (int)Db, (int)d)) {
+  if (use_fused_absorb(c->cx, c->split != nullptr, c->opts, (int)Dk, (int)Db, (int)d)) {
     // A and B in one pass over the block (fp32 arithmetic in split contexts)
     CTM_CUDA_OK(absorb_ab(c->cx, c->split != nullptr, (int)chi, (int)Dk, (int)Db, (int)d, CTT.p,
                           A, B, Qout, c->num_sms, c->stream, &c->launches));
@@ -842,7 +700,7 @@ ctm_status absorb_site(ctm_ctx* c, int r, int x, int y, int Lyf) {
   CK(ein(c, "tndD,ndDc->tc", E4, false, tn(Pl_dn, {chi, Dk, Db, chi}), false,
          tn(oC4, {chi, chi})));
   // T4'
-  if (absorb_ab_supported(c->cx, c->split != nullptr, (int)Dk, (int)Db, (int)d)) {
+  if (use_fused_absorb(c->cx, c->split != nullptr, c->opts, (int)Dk, (int)Db, (int)d)) {
     Tn Y1 = tn(c->pipe[0], {chi, Dk, Db, chi, Dk, Db});
     CK(ein(c, "tqlw,quvc->tlwcuv", tn(T4, {chi, chi, Dk, Db}), false,
            tn(Pl_up, {chi, Dk, Db, chi}), false, Y1));
@@ -1356,8 +1214,8 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       // a lane only builds corners and runs the SI round: its pipelines hold
       // N^2 elements (d N^2 for the unfused absorption), not the d^2 N^2 of
       // the two-site observables of lane 0
-      const bool fused = absorb_ab_supported(cx, c->opts.prec == CTM_PREC_SPLIT_BF16, (int)Dk,
-                                             (int)Db, d);
+      const bool fused = use_fused_absorb(cx, c->opts.prec == CTM_PREC_SPLIT_BF16, c->opts,
+                                          (int)Dk, (int)Db, d);
       const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
       M.scratch_bytes = 2 * laneT * es + ((size_t)64 << 20);
       for (int q = 0; q < 4; ++q)
@@ -1398,10 +1256,6 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   return CTM_OK;
 }
 
-struct Guard {
-  explicit Guard(ctm_ctx* c) { g_cur = c; }
-  ~Guard() { g_cur = nullptr; }
-};
 
 // one-site patch with the ket at (x, y) of frame 0 replaced by K (device);
 // result: scalar Z at out (open = false) or rho[s][t] (open = true)
@@ -1522,7 +1376,7 @@ bool valid_site(const ctm_ctx* c, int x, int y) {
   return x >= 0 && y >= 0 && x < c->Lx && y < c->Ly;
 }
 
-}  // namespace
+}  // namespace ctmi
 
 // =============================================================== C ABI
 extern "C" {
@@ -1543,6 +1397,7 @@ void ctm_default_opts(ctm_opts* o) {
   o->init_mode = CTM_INIT_RANDOM;
   o->recycle_sin2 = 0.0;
   o->min_si_steps = 3;
+  o->absorb_tc = 0;
   o->stream = nullptr;
 }
 
@@ -1623,18 +1478,18 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
     const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
     b += 8 * 3 * N * Kp * 2;                       // corner slices, both orientations
     b += 2 * 3 * N * Kp * 2;                       // operand slices of general products
-    b += 32 * N * ((cx ? 2 : 1) * k + 160) * 4;    // split-K partials
+    b += split_partial_splits(N, cx) * N * ((cx ? 2 : 1) * k + 160) * 4;   // split-K partials
   }
   if (o->method == CTM_PROJ_SVD) b += 3 * NN * es + 2 * N * chi * es + (size_t)64 * N * es;
   if (o->method == CTM_PROJ_SI) {
     // lanes 1 .. nl-1: corners, pipes, scratch, N x k blocks, QR work, split state
-    const bool fused = absorb_ab_supported(cx, o->prec == CTM_PREC_SPLIT_BF16, Dk, Db, d);
+    const bool fused = use_fused_absorb(cx, o->prec == CTM_PREC_SPLIT_BF16, *o, Dk, Db, d);
     const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
     size_t lane = 4 * NN * es + 4 * laneT * es + ((size_t)64 << 20) + 4 * N * k * es +
                   2 * k * k * es + 12 * k + chol_coop_work_bytes((int)k, 1);
     if (o->prec == CTM_PREC_SPLIT_BF16) {
       const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
-      lane += 10 * 3 * N * Kp * 2 + 32 * N * ((cx ? 2 : 1) * k + 160) * 4;
+      lane += 10 * 3 * N * Kp * 2 + split_partial_splits(N, cx) * N * ((cx ? 2 : 1) * k + 160) * 4;
     }
     b += (size_t)(lanes_for(Lx, Ly) - 1) * lane;
   }

@@ -6,11 +6,15 @@
 //     (the slices of x rounded to fp32, each the bf16 rounding of the
 //     remainder; |e| <= 2^-24 |x|);
 //   * a product keeps the six slice products of order >= 2^-16
-//     (s0 t0, s0 t1, s1 t0, s0 t2, s1 t1, s2 t0), all accumulated into one
-//     fp32 accumulator in tensor memory;
+//     (s0 t0, s0 t1, s1 t0, s0 t2, s1 t1, s2 t0); the leading s0 t0 is
+//     accumulated in its own fp32 accumulator in tensor memory and the five
+//     smaller ones in a second, so that their additions cost ulps of a
+//     2^-8 smaller running sum, and the two are added once per partial;
 //   * complex data uses the real embedding A_emb = [A_r | A_i] (M x 2K),
 //     B_emb = [[B_r, B_i], [-B_i, B_r]] (2K x 2N), C_emb = [C_r | C_i];
-//   * K is split over CTAs; fp32 partials are reduced in fp64.
+//   * K is split over CTAs, at most KB_SPLIT_MAX K blocks of 64 each (the
+//     error of an fp32 accumulator grows with the number of MMA steps it
+//     takes); fp32 partials are reduced in fp64.
 //
 // Kernel: one CTA = 128 output rows x BNc (<= 160) output columns; A and B
 // slices are K-major, staged by TMA in 64-element (128-byte, 128B-swizzled)
@@ -42,6 +46,10 @@ constexpr int STAGES = 2;
 constexpr int MAX_BNC = 160;     // columns per CTA
 constexpr int A_SLICE_BYTES = BM * BK * 2;   // 16 KB
 constexpr uint64_t WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
+#ifndef CTM_KB_SPLIT_MAX
+#define CTM_KB_SPLIT_MAX 8
+#endif
+constexpr int KB_SPLIT_MAX = CTM_KB_SPLIT_MAX;   // K blocks per fp32 partial
 
 // ---------------------------------------------------------------- PTX
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -157,8 +165,11 @@ __global__ void __launch_bounds__(128, 1)
   const int m_tile = blockIdx.x, chunk = blockIdx.y, ks = blockIdx.z;
   const int kb0 = ks * p.kb_split;
   const int nkb = min(p.kb_split, p.kb_total - kb0);
-  uint32_t ncols = 32;
-  while ((int)ncols < BNc) ncols <<= 1;
+  // two accumulators of BNc columns each: [0, acc1) for s0 t0, [acc1, ..)
+  // for the five smaller slice products
+  uint32_t acc1 = 32;
+  while ((int)acc1 < BNc) acc1 <<= 1;
+  const uint32_t ncols = 2 * acc1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -220,9 +231,11 @@ __global__ void __launch_bounds__(128, 1)
       for (int pr = 0; pr < 6; ++pr) {
         const uint32_t a0 = st + pa[pr] * A_SLICE_BYTES;
         const uint32_t b0 = st + 3 * A_SLICE_BYTES + pb[pr] * b_slice_bytes;
+        const uint32_t d = pr == 0 ? tmem : tmem + acc1;
+        const bool first = kb == 0 && (pr == 0 || pr == 1);
         for (int kk = 0; kk < BK / 16; ++kk) {
-          mma_bf16(tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
-                   (kb > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                   (first && kk == 0) ? 0u : 1u);
         }
       }
       mma_commit(empty0 + 8 * s);
@@ -240,16 +253,20 @@ __global__ void __launch_bounds__(128, 1)
     const int row = m_tile * BM + warp * 32 + lane;
     float* out = p.part + ((size_t)ks * p.M + row) * p.Np + (size_t)chunk * BNc;
     for (int c0 = 0; c0 < BNc; c0 += 16) {
-      uint32_t r[16];
+      uint32_t r[16], q[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + acc1 + (uint32_t)c0, q);
       if (row < p.M) {
         // 64 contiguous bytes of this thread's row (Np, BNc and c0 are
-        // multiples of 16 floats, so the row segment is 64-byte aligned)
+        // multiples of 16 floats, so the row segment is 64-byte aligned);
+        // one rounded addition joins the two accumulators
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __fadd_rn(__uint_as_float(r[i]), __uint_as_float(q[i]));
         float4* o4 = reinterpret_cast<float4*>(out + c0);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          o4[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
-                              __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
+          o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
       }
     }
   }
@@ -564,8 +581,9 @@ void chunking(int Nr, int* nchunks, int* BNc) {
 int choose_splits(int tiles, int kb_total) {
   int best = 1;
   double best_t = 1e30;
-  const int smax = std::max(1, std::min(32, kb_total / 4));
-  for (int s = 1; s <= smax; ++s) {
+  const int smin = (kb_total + KB_SPLIT_MAX - 1) / KB_SPLIT_MAX;
+  const int smax = std::max(smin, std::min(std::max(32, smin), kb_total / 4));
+  for (int s = smin; s <= smax; ++s) {
     const int per = (kb_total + s - 1) / s;
     const int used = (kb_total + per - 1) / per;
     const long ctas = (long)tiles * used;
@@ -780,6 +798,11 @@ ctm_status split_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, c
   st = prep_b(sc, B, ldb, opB, K, N, Kp, Np, sc->bbuf, s, launches);
   if (st != CTM_OK) return st;
   return run_mma(sc, sc->abuf, sc->bbuf, M, Kp, Nr, nchunks, BNc, C, ldc, N, s, launches);
+}
+
+size_t split_partial_splits(size_t N, bool cx) {
+  const size_t kb = ((cx ? 2 : 1) * N + BK - 1) / BK;
+  return std::max<size_t>(32, (kb + KB_SPLIT_MAX - 1) / KB_SPLIT_MAX);
 }
 
 const char* split_last_error(const SplitCtx* sc) {

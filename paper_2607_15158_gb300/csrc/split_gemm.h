@@ -38,6 +38,10 @@ ctm_status split_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, c
 ctm_status split_profile(SplitCtx* sc, int on, double* ms, long* launches, double* flops,
                          double* bytes);
 
+// Largest number of split-K partials a product with inner dimension N (2N
+// for complex) uses: each partial covers a bounded number of K blocks.
+size_t split_partial_splits(size_t N, bool cx);
+
 const char* split_last_error(const SplitCtx* sc);
 
 }  // namespace ctm

@@ -17,7 +17,8 @@ from pairs import make_pair
 
 pytestmark = pytest.mark.gpu
 HEIS = S.heisenberg_bond()
-TOL_SPLIT = 1e-6     # converged spectra and energies, split vs fp64
+TOL_SPLIT = 1e-6          # converged unit-normalised corner spectra, split vs fp64
+TOL_SPLIT_ENERGY = 1e-7   # converged bond energies, split vs fp64
 
 
 def _ctx(case, prec):
@@ -116,5 +117,6 @@ def test_converged_split_large_D_matches_oracle(case):
     ee = max(abs(ctx.ctm_expect(HEIS, x, y, dr) - ref.expect2(HEIS, x, y, dr))
              for y in range(Ly) for x in range(Lx) for dr in (0, 1))
     print(f"split D={D}: spectra {es:.2e}, energies {ee:.2e}, delta {delta:.1e}, it {it}")
-    assert es < TOL_SPLIT and ee < TOL_SPLIT
+    # measured: spectra 4.2e-7 / 2.8e-7, energies 4.9e-8 / 3.1e-8 (D = 6 / 8)
+    assert es < TOL_SPLIT and ee < TOL_SPLIT_ENERGY
     ctx.ctm_free()
