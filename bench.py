@@ -32,7 +32,11 @@ if ROOT not in sys.path:
 
 WORKLOAD = "cfg3_3x3_D6_chi144_c128"
 WARM_ITERS, WARM_ROUNDS = 2, 4
-TRAFFIC_PER_OPERAND_BYTE = 1.00   # profiles/split_mma_small_counters.md
+# DRAM bytes (read + write) per launch of split_mma_kernel over the bf16
+# operand bytes of that launch, from one full-counter ncu capture of the
+# current kernel; None until the kernel has been captured since it changed
+TRAFFIC_PER_OPERAND_BYTE = None
+SLICE_PRODUCTS = 6   # bf16 slice products per algorithmic product
 METRIC = "CTMRG moves/s & tensor TFLOP/s at D=6, chi=144"
 UNIT = "moves/s"
 
@@ -48,9 +52,13 @@ def parse():
                     help="projectors: subspace iteration or the standard truncated SVD")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparisons", action="store_true",
+                    help="skip the plain-FP64 and standard-SVD comparison timings and the "
+                         "split-error measurement")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: Poisson stream of mixed solves, p50/p99 latency")
-    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--requests", type=int, default=128)
+    ap.add_argument("--max-iter", type=int, default=100, help="per solve (serve)")
     ap.add_argument("--rate", type=float, default=1.0, help="arrivals per second (serve)")
     ap.add_argument("--concurrency", type=int, default=8, help="solves in flight (serve)")
     return ap.parse_args()
@@ -316,26 +324,41 @@ def run_ours(args, rank, world, local_rank):
     roofline = None
     if prof is not None and prof[1] > 0:
         mma_ms, mma_n, mma_flops, mma_bytes = prof
-        achieved = mma_flops / (mma_ms * 1e-3) / 1e12
+        # algorithmic flops: the complex (or real) product itself, 8 (2) real
+        # flops per multiply-add = the tensor-pipe flops of the six bf16 slice
+        # products / 6
+        pipe = mma_flops / (mma_ms * 1e-3) / 1e12
+        achieved = pipe / SLICE_PRODUCTS
         peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
-        # DRAM bytes per launch: the full-counter capture of this kernel on the
-        # small workload measured dram read + write = 1.00 x the operand bytes
-        # of the launch; scaled here to the operand bytes of these launches
-        traffic = TRAFFIC_PER_OPERAND_BYTE * mma_bytes / mma_n
+        traffic = (None if TRAFFIC_PER_OPERAND_BYTE is None
+                   else round(TRAFFIC_PER_OPERAND_BYTE * mma_bytes / mma_n))
         roofline = {"bound": "tensor", "kernel": "split_mma_kernel (tcgen05 bf16, fp32 accum)",
                     "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4), "traffic": round(traffic),
-                    "traffic_source": "ncu dram bytes / operand bytes = 1.00 on "
-                                      "small_1x1_D4_chi100_c128, x operand bytes per launch",
-                    "peak_source": f"{src} bf16 sustained",
-                    "launches": mma_n, "kernel_ms": round(mma_ms, 3),
-                    "kernel_share_of_step": round(mma_ms / ms, 4)}
+                    "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "achieved_basis": "algorithmic flops (8 per complex multiply-add) per "
+                                      "launch / CUDA-event duration on the launching stream",
+                    "tensor_pipe_achieved": round(pipe, 2),
+                    "tensor_pipe_frac": round(pipe / peak, 4),
+                    "tensor_pipe_basis": f"{SLICE_PRODUCTS} bf16 slice products of the "
+                                         "real-embedded problem",
+                    "peak_source": f"{src} bf16 sustained (of measured)" if src == "measured"
+                    else "fallback 1.7 PFLOP/s sustained (of fallback)",
+                    "launches": mma_n, "launches_covered": "every launch of the timed steps",
+                    "kernel_ms": round(mma_ms, 3),
+                    "kernel_share_of_step": round(mma_ms / ms, 4),
+                    "overlap": "lanes run the cuts of a column concurrently: a launch's event "
+                               "interval includes time shared with other lanes' kernels"}
     cpu = None
     if not args.no_cpu_baseline:
         per_move, dt, sample = oracle_sample_seconds(w)
         cpu = {"value": 1.0 / per_move, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": sample, "seconds_measured": round(dt, 2)}
     algo_flops_move = move_flops(w, args.method)
+    extra = {}
+    if not args.no_comparisons and args.workload == WORKLOAD and args.prec == "split":
+        ctx.ctm_free()
+        ctx = None
+        extra = comparisons(pkg, S, value)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -343,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "c128" if cplx else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "cell": f"{Lx}x{Ly}", "d": d, "D": D, "chi": chi,
                    "p": p, "N": N, "k": k, "si_rounds": w["si_rounds"],
-                   "precision": "split-bf16x3 (6 slice products), fp32 accum, fp64 QR/SVD"
+                   "precision": "split-bf16x3 (6 slice products; s0 t0 and the rest in separate fp32 accumulators), fp64 QR/SVD"
                    if args.prec == "split" else "fp64",
                    "projectors": "subspace iteration" if args.method == "si"
                    else "standard truncated SVD (dense gesvd)",
@@ -359,8 +382,104 @@ def run_ours(args, rank, world, local_rank):
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"]},
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
+    if ctx is not None:
+        ctx.ctm_free()
+
+
+def _time_moves(pkg, w, prec, method, moves, warm_moves=1):
+    """Seconds per move of a fresh context (no warm-up rounds: every move one
+    SI round, as in steady state), after warm_moves untimed moves."""
+    import torch
+    import ctm_synth as S
+    Lx, Ly, d, D, chi, p = w["Lx"], w["Ly"], w["d"], w["D"], w["chi"], w["p"]
+    cplx = w["complex_"]
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, diag_weight=w["diag_weight"])
+    Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx)
+    N, k = chi * D * D, min(chi + p, chi * D * D)
+    X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx)
+    ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx, opts=pkg.ctm_default_opts(
+        p=p, si_rounds=w["si_rounds"], warmup_iters=0, prec=prec, method=method))
+    ctx.ctm_set_env(Cs, Ts)
+    ctx.ctm_set_rangefinders(X0, W0)
+    for i in range(warm_moves):
+        ctx.ctm_move(i % 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(moves):
+        ctx.ctm_move(i % 4)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / moves
     ctx.ctm_free()
+    return dt
+
+
+def comparisons(pkg, S, split_value):
+    """The metric's comparison lines on the same GPU, in the same run: plain
+    FP64 SI-CTMRG on the bench workload (one timed move), standard truncated-
+    SVD CTMRG and FP64 SI-CTMRG on the 3x3 D = 4 chi = 64 workload (two timed
+    moves each), and the measured error of split precision."""
+    import numpy as np
+    out = {}
+    w3 = S.WORKLOADS[WORKLOAD]
+    w2 = S.WORKLOADS["cfg2_3x3_D4_chi64"]
+    t_fp64 = _time_moves(pkg, w3, pkg.CTM_PREC_FP64, pkg.CTM_PROJ_SI, 1)
+    t_si2 = _time_moves(pkg, w2, pkg.CTM_PREC_FP64, pkg.CTM_PROJ_SI, 2)
+    t_svd2 = _time_moves(pkg, w2, pkg.CTM_PREC_FP64, pkg.CTM_PROJ_SVD, 2)
+    out["comparisons"] = {
+        "fp64_si_same_workload": {"value": 1.0 / t_fp64, "unit": UNIT, "moves_timed": 1,
+                                  "split_over_fp64": split_value * t_fp64},
+        "cfg2_3x3_D4_chi64": {"si_fp64": 1.0 / t_si2, "standard_svd_fp64": 1.0 / t_svd2,
+                              "unit": UNIT, "moves_timed": 2, "si_over_standard": t_svd2 / t_si2},
+        "note": "standard CTMRG on the bench workload (dense 5184 x 5184 complex SVD per cut) "
+                "is not timed: at this GPU's fp64 rate one move takes minutes"}
+    # split error against the fp64 path: (1) one enlarged corner and one
+    # corner x block product at the bench size, (2) a converged D = 6 2x2 cell
+    w = w3
+    Lx, Ly, d, D, chi, p = w["Lx"], w["Ly"], w["d"], w["D"], w["chi"], w["p"]
+    A = S.ipeps_tensors(Lx, Ly, d, D, complex_=True, diag_weight=w["diag_weight"])
+    Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=True)
+
+    def ctx_for(prec, A, Cs, Ts, Lx, Ly, D, chi, **kw):
+        c = pkg.ctm_init(Lx, Ly, A, 2, D, chi, cplx=True,
+                         opts=pkg.ctm_default_opts(p=5, prec=prec, **kw))
+        c.ctm_set_env(Cs, Ts)
+        return c
+    cs = ctx_for(pkg.CTM_PREC_SPLIT_BF16, A, Cs, Ts, Lx, Ly, D, chi)
+    cf = ctx_for(pkg.CTM_PREC_FP64, A, Cs, Ts, Lx, Ly, D, chi)
+    Qs, Qf = cs.ctm_corner(0, 0, 0, 2), cf.ctm_corner(0, 0, 0, 2)
+    e_corner = float(np.abs(Qs - Qf).max() / np.abs(Qf).max())
+    rng = np.random.default_rng(1)
+    Z = rng.standard_normal((cs.N, cs.k)) + 1j * rng.standard_normal((cs.N, cs.k))
+    Y = cs.ctm_corner_apply(0, 0, 0, 2, Z)
+    R = Qs @ Z
+    e_apply = float(np.abs(Y - R).max() / np.abs(R).max())
+    cs.ctm_free()
+    cf.ctm_free()
+    del Qs, Qf, Y, R
+    A6 = S.ipeps_tensors(2, 2, 2, 6, complex_=True, seed=0, bond_decay=0.5)
+    C6, T6 = S.initial_env(2, 2, 8, 6, 6, complex_=True, seed=1)
+    heis = S.heisenberg_bond()
+    res = []
+    for prec in (pkg.CTM_PREC_SPLIT_BF16, pkg.CTM_PREC_FP64):
+        c = ctx_for(prec, A6, C6, T6, 2, 2, 6, 8)
+        c.ctm_converge(1e-11 if prec == pkg.CTM_PREC_FP64 else 1e-9, 150)
+        res.append((c.ctm_spectra(), np.array([c.ctm_expect(heis, x, y, dr)
+                                               for y in range(2) for x in range(2)
+                                               for dr in (0, 1)])))
+        c.ctm_free()
+    out["split_error"] = {
+        "vs": "the fp64 path of this library on the same inputs",
+        "corner_full_size": e_corner, "corner_x_block_full_size": e_apply,
+        "full_size_basis": "max |split - fp64| / max |fp64| over one enlarged corner and one "
+                           "corner x block product of the bench workload",
+        "converged_spectra": float(np.abs(res[0][0] - res[1][0]).max()),
+        "converged_energies": float(np.abs(res[0][1] - res[1][1]).max()),
+        "converged_basis": "2x2 cell, complex D = 6, chi = 8, bond weights decaying as "
+                           "0.5^(u+l+d+r), converged; unit-normalised corner spectra and "
+                           "Heisenberg bond energies"}
+    return out
 
 
 def move_flops(w, method="si"):
@@ -387,18 +506,20 @@ def move_flops(w, method="si"):
 
 
 # ------------------------------------------------------------------ serving
+SERVE_SPLIT_ABOVE_N = 1024   # solves with a larger half-system run in split precision
+
+
 def serve_mix(n, seed=4):
-    """Seeded request stream of the serving workload: cells 1x1 or 2x2, real
-    A[2,D,...] with D in {2, 3, 4}, chi uniform in [D^2, 2 D^2], tol 1e-8
-    (a reduced stand-in for the 1x1..3x3, D = 3..7, chi in [D^2, 4 D^2] mix,
-    whose fp64 solves take minutes each on this GPU)."""
+    """Seeded request stream of the serving workload: each request a random
+    unit cell (1x1, 2x2 or 3x3) of real tensors A[2,D,D,D,D] with D uniform in
+    {3, ..., 7} and chi uniform in [D^2, 4 D^2], tolerance 1e-8."""
     import numpy as np
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
-        L = int(rng.choice([1, 2]))
-        D = int(rng.choice([2, 3, 4]))
-        chi = int(rng.integers(D * D, 2 * D * D + 1))
+        L = int(rng.choice([1, 2, 3]))
+        D = int(rng.integers(3, 8))
+        chi = int(rng.integers(D * D, 4 * D * D + 1))
         out.append((L, L, D, chi, 1000 + i))
     return out
 
@@ -418,27 +539,42 @@ def run_serve(args):
     tensors = [S.ipeps_tensors(Lx, Ly, 2, D, complex_=False, seed=sd) for (Lx, Ly, D, chi, sd) in mix]
     srv = pkg.Server(hbm_budget=0, max_concurrent=args.concurrency)
     t0 = time.perf_counter()
-    tickets = []
+    tickets, precs = [], []
     for (Lx, Ly, D, chi, sd), A, gap in zip(mix, tensors, gaps):
         time.sleep(gap)
-        tickets.append(srv.ctm_server_submit(A, 2, D, chi, 1e-8, 200, op=heis, cplx=False,
-                                             Lx=Lx, Ly=Ly))
+        split = chi * D * D > SERVE_SPLIT_ABOVE_N
+        o = pkg.ctm_default_opts(prec=pkg.CTM_PREC_SPLIT_BF16 if split else pkg.CTM_PREC_FP64,
+                                 recycle_sin2=1e-3, min_si_steps=3)
+        precs.append("split" if split else "fp64")
+        tickets.append(srv.ctm_server_submit(A, 2, D, chi, 1e-8, args.max_iter, op=heis,
+                                             cplx=False, Lx=Lx, Ly=Ly, opts=o))
     res = [srv.ctm_server_result(t) for t in tickets]
     wall = time.perf_counter() - t0
     st = srv.ctm_server_stats()
     srv.ctm_server_free()
+    conv = [r["delta"] < 1e-8 for r in res]
     line = {
         "metric": "serve p50/p99 latency", "value": st["p50_ms"], "unit": "ms",
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "solves_per_s": st["solves_per_s"],
         "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "serve mix: cells 1x1/2x2, D in {2,3,4}, chi in [D^2, 2D^2], "
-                               "tol 1e-8, Poisson arrivals",
+        "config": {"workload": "serve: Poisson arrivals of random cells 1x1/2x2/3x3, real "
+                               "A[2,D,...] with D in {3..7}, chi in [D^2, 4 D^2], tol 1e-8",
                    "requests": len(mix), "rate_per_s": args.rate,
-                   "concurrency": args.concurrency},
+                   "concurrency": args.concurrency, "max_iter": args.max_iter,
+                   "precision": f"fp64 for N = chi D^2 <= {SERVE_SPLIT_ABOVE_N}, split bf16x3 "
+                                "above (fp64 solves of the largest requests take tens of "
+                                "minutes at this GPU's fp64 rate)",
+                   "recycling": "paper step 4 policy: no update round once mean sin^2 < 1e-3 "
+                                "after 3 updates"},
         "wall_s": wall,
         "mean_queue_ms": float(np.mean([r["queue_ms"] for r in res])),
         "mean_run_ms": float(np.mean([r["run_ms"] for r in res])),
-        "converged": int(sum(r["delta"] < 1e-8 for r in res)),
+        "converged_1e-8": {"fp64": int(sum(c for c, p in zip(conv, precs) if p == "fp64")),
+                           "split": int(sum(c for c, p in zip(conv, precs) if p == "split")),
+                           "fp64_requests": precs.count("fp64"),
+                           "split_requests": precs.count("split")},
+        "split_final_delta_median": float(np.median([r["delta"] for r, p in zip(res, precs)
+                                                     if p == "split"] or [0.0])),
     }
     print(json.dumps(line), flush=True)
 

@@ -105,6 +105,14 @@ typedef struct {
                              split bf16 tensor-core GEMMs with permutes (the
                              accuracy of the other products), 0 = one fused
                              kernel in fp32 arithmetic */
+  int si_coupled;         /* 1 = coupled (Halko) rangefinder update: each round
+                             W <- qr(M X), X <- qr(M^H W) (half the corner
+                             products of the paper's independent updates of
+                             Eq. xy_iter); 0 = the paper's form */
+  int warmup_rsvd;        /* 1 = every warm-up move restarts its rounds from
+                             the initial random blocks (a randomized SVD per
+                             move, End Matter: RSVD before SI on larger unit
+                             cells) instead of the recycled bases */
   void* stream;           /* cudaStream_t to run on, NULL = a private stream */
 } ctm_opts;
 
@@ -120,7 +128,8 @@ enum { CTM_INIT_RANDOM = 0, CTM_INIT_FROM_A = 1 };
 /* Defaults: p = 5, si_rounds = 1, warmup_iters = 5, warmup_rounds = 8, SI,
  * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0,
  * svd_max_sweeps = 80, init_mode = CTM_INIT_RANDOM, recycle_sin2 = 0 (always
- * update), min_si_steps = 3, absorb_tc = 0, stream = NULL. */
+ * update), min_si_steps = 3, absorb_tc = 0, si_coupled = 0, warmup_rsvd = 0,
+ * stream = NULL. */
 void ctm_default_opts(ctm_opts* opts);
 
 /* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz
@@ -239,6 +248,50 @@ ctm_status ctm_corner_apply(ctm_ctx* ctx, ctm_dir dir, int x, int y, int i, int 
 /* Subspace-iteration updates made and skipped (recycling policy of
  * opts.recycle_sin2) over all cuts since the context was created. */
 ctm_status ctm_si_stats(const ctm_ctx* ctx, long* updates, long* skipped);
+
+/* ------------------------------------------------------- differentiation
+ * Gradient of the energy E = sum over all sites and both bond directions of
+ * Re <op> (op as in ctm_expect) with respect to the on-site tensors A,
+ * following the paper's section "Variational optimization" (reverse-mode
+ * differentiation of the recorded forward CTMRG, "unrolled") and section
+ * "Differentiable fixed point" (Eq. implicit). The adjoints are hand-written
+ * (contractions, CholeskyQR as the QR with positive diagonal, the small SVD
+ * with Lorentzian-broadened 1/(s_j^2 - s_i^2) = 1/((s_j - s_i)(s_j + s_i)),
+ * the factor 1/(s_j - s_i) replaced by (s_j - s_i) / ((s_j - s_i)^2 + eps),
+ * eps = (1e-12 s_1)^2, the
+ * s^-1/2 scaling, the normalisation) and run on the device in fp64; each
+ * move is recomputed from a checkpoint (its enlarged corners and
+ * half-system products are not stored). Supported for real (CTM_F64)
+ * iPEPS contexts (bra = conj(A)) with CTM_PREC_FP64, SI projectors and
+ * recycle_sin2 = 0; other contexts return CTM_EUNSUPPORTED. dA_out is host
+ * memory of Lx*Ly*d*D^4 doubles laid out like ctm_init's A. */
+
+/* on = 1: forget earlier records and start recording: every following move
+ * (ctm_move, ctm_converge) first saves its input state (C, T and the
+ * rangefinders of its direction, device memory of about
+ * 4 S chi^2 (1 + D^2) + 2 S N k doubles per move). on = 0 stops recording
+ * and keeps the records. */
+ctm_status ctm_record(ctm_ctx* ctx, int on);
+
+/* Unrolled gradient: E of the current environment and dE/dA through every
+ * move recorded since ctm_record(ctx, 1); the environment and rangefinders
+ * at the start of the recording are held constant (the initial raw
+ * rangefinder blocks enter only through their first QR). The records are
+ * kept, so the call can be repeated. E_out may be NULL. */
+ctm_status ctm_grad(ctm_ctx* ctx, const void* op, double* E_out, void* dA_out);
+
+/* Fixed-point gradient (Eq. implicit) at the current, converged
+ * environment: x = (C, T and the recycled rangefinders X, Y of every
+ * direction and cut) is taken as the fixed point of one CTMRG iteration F
+ * (four moves); lambda = dE/dx + (dF/dx)^T lambda is iterated from
+ * lambda = dE/dx until ||lambda_new - lambda|| < tol ||lambda_new|| or
+ * max_iter vector-Jacobian products, then dA = dE/dA + (dF/dA)^T lambda.
+ * Memory: one iteration's tape, independent of the number of forward
+ * iterations. Returns CTM_ENOCONV (dA_out still written) when max_iter is
+ * reached; iters_out, res_out (last relative change) and E_out may be NULL.
+ * Needs the warm-up moves of every direction done. */
+ctm_status ctm_grad_fixed_point(ctm_ctx* ctx, const void* op, double tol, int max_iter,
+                                double* E_out, void* dA_out, int* iters_out, double* res_out);
 
 /* Device milliseconds of the last ctm_move / ctm_converge call and the
  * number of kernels it launched. */

@@ -175,7 +175,7 @@ def apply_Mh(Q1, Q2, Q3, Q4, Z):
 
 
 def projectors_si(Q1, Q2, Q3, Q4, X, W, chi, rounds=1, cutoff=1e-12,
-                  sign_fix=True):
+                  sign_fix=True, coupled=False):
     """SI-CTMRG projectors with recycling (QR-based projector, steps 1-4).
 
     X (N x k, columns in M's column space) and W = Y^dagger (N x k, M's row
@@ -186,9 +186,17 @@ def projectors_si(Q1, Q2, Q3, Q4, X, W, chi, rounds=1, cutoff=1e-12,
     chi; P_l = Z_R v_chi s^-1/2, P_r = s^-1/2 u_chi^H Z_L^H (Eq.
     projectors_diag); recycle X <- X v, W <- W u (Eq. xy_recycle).
     Returns (Pl, Pr, s_chi, X_new, W_new, s_all).
+    With coupled=True each round is the coupled (Halko) form of the
+    subspace iteration, W <- qr(M X), X <- qr(M^H W): the left basis is
+    taken from the current right one instead of being updated on its own
+    (reading c13; half the applications of M per round).
     Pinned by: P_r P_l = I (P5), span invariance (P6), SI -> SVD (P7),
     exact growth with k = N (P3)."""
     for _ in range(rounds):
+        if coupled:
+            W = qr_q(apply_M(Q1, Q2, Q3, Q4, X))
+            X = qr_q(apply_Mh(Q1, Q2, Q3, Q4, W))
+            continue
         # span(M^H M X) taken as qr(M^H qr(M X)): the same span, without
         # squaring the condition number of M before the QR
         X = qr_q(apply_Mh(Q1, Q2, Q3, Q4, qr_q(apply_M(Q1, Q2, Q3, Q4, X))))
@@ -300,12 +308,16 @@ class CTM:
     has had at least min_si_steps updates (paper: at least three), its next
     moves make no update round and only recycle the bases, until the angle
     grows above the threshold again; recycle_sin2 = 0 always updates.
+    coupled: the coupled (Halko) rangefinder update (see projectors_si).
+    warmup_rsvd: each warm-up move starts its rounds from the initial random
+    blocks (a randomized SVD per move, End Matter: RSVD instead of a full SVD
+    before SI) instead of the recycled bases.
     """
 
     def __init__(self, Lx, Ly, kets, bras, C, T, chi, method="si", p=5,
                  si_rounds=1, X0=None, W0=None, cutoff=1e-12, normalize=True,
                  sign_fix=True, warmup_iters=0, warmup_rounds=8, recycle_sin2=0.0,
-                 min_si_steps=3):
+                 min_si_steps=3, coupled=False, warmup_rsvd=False):
         self.Lx, self.Ly = Lx, Ly
         self.kets = [np.asarray(a) for a in kets]
         self.bras = [np.asarray(b) for b in bras]
@@ -327,6 +339,9 @@ class CTM:
         self.moves_done = [0, 0, 0, 0]   # moves per direction
         self.recycle_sin2 = recycle_sin2
         self.min_si_steps = min_si_steps
+        self.coupled = coupled
+        self.warmup_rsvd = warmup_rsvd
+        self.rf_raw = {}                 # (r, cut) -> raw initial blocks
         self.si_updates = {}             # (r, cut) -> update rounds made
         self.si_skip = {}                # (r, cut) -> next move only recycles
         self.n_updates = 0
@@ -377,6 +392,7 @@ class CTM:
                 X = rng.standard_normal((Nc, k))
                 W = rng.standard_normal((Nr, k))
             assert X.shape == (Nc, k) and W.shape == (Nr, k), (X.shape, Nc, k)
+            self.rf_raw[key] = (X.astype(dtype), W.astype(dtype))
             self.rf[key] = (qr_q(X.astype(dtype)), qr_q(W.astype(dtype)))
         return self.rf[key]
 
@@ -395,6 +411,8 @@ class CTM:
         key = (f.r, cut)
         if self.moves_done[f.r] < self.warmup_iters:
             rounds = self.warmup_rounds
+            if self.warmup_rsvd:
+                X, W = (qr_q(b) for b in self.rf_raw[key])
         else:
             rounds = 0 if self.si_skip.get(key, False) else self.si_rounds
         if rounds > 0:
@@ -404,7 +422,7 @@ class CTM:
             self.n_skipped += 1
         Pl, Pr, s, Xn, Wn, s_all = projectors_si(
             Q1, Q2, Q3, Q4, X, W, self.chi, rounds, self.cutoff,
-            self.sign_fix)
+            self.sign_fix, coupled=self.coupled)
         # principal angles between the old and new leading chi-subspaces
         c = min(self.chi, k)
         sv = np.linalg.svd(X[:, :c].conj().T @ Xn[:, :c], compute_uv=False)

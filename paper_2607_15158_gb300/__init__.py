@@ -34,7 +34,8 @@ class ctm_opts(C.Structure):
                 ("normalize", C.c_int), ("sign_fix", C.c_int),
                 ("seed", C.c_uint64), ("svd_max_sweeps", C.c_int), ("init_mode", C.c_int),
                 ("recycle_sin2", C.c_double), ("min_si_steps", C.c_int),
-                ("absorb_tc", C.c_int), ("stream", C.c_void_p)]
+                ("absorb_tc", C.c_int), ("si_coupled", C.c_int), ("warmup_rsvd", C.c_int),
+                ("stream", C.c_void_p)]
 
 
 class ctm_solve_spec(C.Structure):
@@ -90,6 +91,9 @@ def load():
         "ctm_corner_apply": (I, [ctx_p, I, I, I, I, I, VP, VP]),
         "ctm_si_stats": (I, [ctx_p, P(C.c_long), P(C.c_long)]),
         "ctm_debug_fail_alloc": (None, [I]),
+        "ctm_record": (I, [ctx_p, I]),
+        "ctm_grad": (I, [ctx_p, VP, P(D), VP]),
+        "ctm_grad_fixed_point": (I, [ctx_p, VP, D, I, P(D), VP, P(I), P(D)]),
         "ctm_last_timing": (I, [ctx_p, P(D), P(C.c_long)]),
         "ctm_profile_enable": (I, [ctx_p, I]),
         "ctm_profile_read": (I, [ctx_p, P(D), P(C.c_long), P(D), P(D)]),
@@ -272,6 +276,29 @@ class Context:
         _check(self.lib, self.ptr, self.lib.ctm_corner_apply(
             self.ptr, int(direction), x, y, i, 1 if herm else 0, z.ctypes.data, out.ctypes.data))
         return out
+
+    def ctm_record(self, on=True):
+        """Start (on) or stop recording moves for ctm_grad."""
+        _check(self.lib, self.ptr, self.lib.ctm_record(self.ptr, 1 if on else 0))
+
+    def ctm_grad(self, op):
+        """(E, dE/dA) through the recorded moves; dE/dA as [Lx*Ly][d,D,D,D,D]."""
+        o = _host(op, False)
+        dA = np.empty((self.Lx * self.Ly, self.d, self.Dk, self.Dk, self.Dk, self.Dk))
+        E = C.c_double()
+        _check(self.lib, self.ptr, self.lib.ctm_grad(self.ptr, o.ctypes.data, C.byref(E),
+                                                     dA.ctypes.data))
+        return E.value, dA
+
+    def ctm_grad_fixed_point(self, op, tol=1e-10, max_iter=200):
+        """(E, dE/dA, iterations, residual) by fixed-point differentiation."""
+        o = _host(op, False)
+        dA = np.empty((self.Lx * self.Ly, self.d, self.Dk, self.Dk, self.Dk, self.Dk))
+        E, it, res = C.c_double(), C.c_int(), C.c_double()
+        st = self.lib.ctm_grad_fixed_point(self.ptr, o.ctypes.data, float(tol), int(max_iter),
+                                           C.byref(E), dA.ctypes.data, C.byref(it), C.byref(res))
+        _check(self.lib, self.ptr, st, allow=(CTM_ENOCONV,))
+        return E.value, dA, it.value, res.value
 
     def ctm_si_stats(self):
         u, sk = C.c_long(), C.c_long()

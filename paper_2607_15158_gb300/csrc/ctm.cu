@@ -60,6 +60,17 @@ struct PhaseScope {
   int ph;
   bool on;
   PhaseScope(ctm_ctx* c_, int ph_) : c(c_), ph(ph_) {
+    if (c->prof && c->pev_used + 2 > c->pev.size()) {
+      // the whole profiled region is timed: the event pool grows
+      const size_t old = c->pev.size();
+      c->pev.resize(old + 16384);
+      for (size_t i = old; i < c->pev.size(); ++i)
+        if (cudaEventCreate(&c->pev[i]) != cudaSuccess) {
+          c->pev.resize(i);
+          break;
+        }
+      c->pph.resize(c->pev.size() / 2);
+    }
     on = c->prof && c->pev_used + 2 <= c->pev.size();
     if (on) {
       cudaEventRecord(c->pev[c->pev_used], c->stream);
@@ -527,12 +538,21 @@ ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
   void** Q = c->Q;
   void** Z = c->Z;
   char& ready = c->rf_ready[r * c->S + cut];
+  const bool warm = c->moves_done[r] < c->opts.warmup_iters;
+  if (warm && c->opts.warmup_rsvd) {
+    // randomized-SVD warm-up: every warm-up move starts from the initial
+    // random blocks, not from the recycled bases
+    CTM_CUDA_OK(cudaMemcpyAsync(X, at(c->Xraw, (size_t)(r * c->S + cut) * Nk, c), Nk * c->es,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    CTM_CUDA_OK(cudaMemcpyAsync(W, at(c->Wraw, (size_t)(r * c->S + cut) * Nk, c), Nk * c->es,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    ready = 0;
+  }
   if (!ready) {
     CK(qr_inplace(c, X, Z[0], false));
     CK(qr_inplace(c, W, Z[0], false));
     ready = 1;
   }
-  const bool warm = c->moves_done[r] < c->opts.warmup_iters;
   const int rc = r * c->S + cut;
   // recycling policy (paper step 4): a cut whose leading subspace stopped
   // moving only recycles its bases, with no update round
@@ -554,7 +574,20 @@ ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
   // without squaring cond(M)); split: one QR per update on the Jacobi-scaled
   // block (the products themselves carry ~1e-7 errors)
   const bool qr_each = !split_qr;
-  for (int round = 0; round < rounds; ++round) {
+  for (int round = 0; round < rounds && c->opts.si_coupled; ++round) {
+    // coupled (Halko) round: W <- qr(M X), X <- qr(M^H W)
+    CK(apply_corner(c, Q[1], false, X, Z[0]));
+    CK(apply_corner(c, Q[0], false, Z[0], Z[1]));
+    CK(apply_corner(c, Q[3], false, Z[1], Z[0]));
+    CK(apply_corner(c, Q[2], false, Z[0], W));
+    CK(qr_inplace(c, W, Z[0], split_qr));
+    CK(apply_corner(c, Q[2], true, W, Z[0]));
+    CK(apply_corner(c, Q[3], true, Z[0], Z[1]));
+    CK(apply_corner(c, Q[0], true, Z[1], Z[0]));
+    CK(apply_corner(c, Q[1], true, Z[0], X));
+    CK(qr_inplace(c, X, Z[0], split_qr));
+  }
+  for (int round = 0; round < rounds && !c->opts.si_coupled; ++round) {
     // X <- qr(M^H M X)
     CK(apply_corner(c, Q[1], false, X, Z[0]));
     CK(apply_corner(c, Q[0], false, Z[0], Z[1]));
@@ -770,6 +803,7 @@ ctm_status check_err(ctm_ctx* c) {
 }
 
 ctm_status move_impl(ctm_ctx* c, int r) {
+  CK(grad_checkpoint(c, r));
   c->spectra_fresh = false;
   const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
   const size_t NC = (size_t)c->N * c->chi;
@@ -927,6 +961,15 @@ ctm_status reset_recycling(ctm_ctx* c) {
   return CTM_OK;
 }
 
+// the initial raw blocks, kept for the randomized-SVD warm-up
+ctm_status keep_raw_rangefinders(ctm_ctx* c) {
+  if (!c->Xraw) return CTM_OK;
+  const size_t n = (size_t)4 * c->S * c->N * c->k * c->es;
+  CTM_CUDA_OK(cudaMemcpyAsync(c->Xraw, c->X, n, cudaMemcpyDeviceToDevice, c->stream));
+  CTM_CUDA_OK(cudaMemcpyAsync(c->Wraw, c->W, n, cudaMemcpyDeviceToDevice, c->stream));
+  return CTM_OK;
+}
+
 ctm_status upload_default_state(ctm_ctx* c) {
   const size_t per = c->cx ? 2 : 1;
   const double sc = c->cx ? std::sqrt(0.5) : 1.0;
@@ -953,6 +996,7 @@ ctm_status upload_default_state(ctm_ctx* c) {
   fill_normal(h, c->opts.seed, 4, sc);
   CTM_CUDA_OK(cudaMemcpyAsync(c->W, h.data(), nrf * sizeof(double), cudaMemcpyHostToDevice,
                               c->stream));
+  CK(keep_raw_rangefinders(c));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
   c->spectra_init = false;
   c->spectra_fresh = false;
@@ -1029,6 +1073,7 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   g_cur = c;
   c->Lx = Lx; c->Ly = Ly; c->S = Lx * Ly;
   c->d = d; c->Dk = Dk; c->Db = Db; c->chi = chi; c->cx = cx;
+  c->bra_is_conj = !bras && !classical;
   c->es = cx ? 16 : 8;
   if (opts) c->opts = *opts;
   else ctm_default_opts(&c->opts);
@@ -1130,6 +1175,10 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->fac, Lmax * es);
   AL(c->dsin2, 4 * S * sizeof(double));
   AL(c->sinG, Lmax * k * k * es);
+  if (c->opts.warmup_rsvd) {
+    AL(c->Xraw, 4 * S * N * k * es);
+    AL(c->Wraw, 4 * S * N * k * es);
+  }
 #undef AL
   c->si_updates.assign(4 * S, 0);
   c->si_skip.assign(4 * S, 0);
@@ -1398,6 +1447,8 @@ void ctm_default_opts(ctm_opts* o) {
   o->recycle_sin2 = 0.0;
   o->min_si_steps = 3;
   o->absorb_tc = 0;
+  o->si_coupled = 0;
+  o->warmup_rsvd = 0;
   o->stream = nullptr;
 }
 
@@ -1439,6 +1490,7 @@ ctm_status ctm_set_rangefinders(ctm_ctx* c, const void* X, const void* W) {
   const size_t n = (size_t)4 * c->S * c->N * c->k * c->es;
   CTM_CUDA_OK(cudaMemcpyAsync(c->X, X, n, cudaMemcpyHostToDevice, c->stream));
   CTM_CUDA_OK(cudaMemcpyAsync(c->W, W, n, cudaMemcpyHostToDevice, c->stream));
+  CK(keep_raw_rangefinders(c));
   CTM_CUDA_OK(cudaStreamSynchronize(c->stream));
   std::fill(c->rf_ready.begin(), c->rf_ready.end(), 0);
   for (int r = 0; r < 4; ++r) c->moves_done[r] = 0;
@@ -1474,6 +1526,7 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
   b += Lmax * (2 * eC + eT) * es + 8 * S * chi * sizeof(double);
   b += 2 * (size_t)d * d * d * d * es + 2 * nk * es + ((size_t)1 << 20);
   b += Lmax * k * k * es + 4 * S * sizeof(double);   // recycling policy
+  if (o->warmup_rsvd) b += 2 * 4 * S * N * k * es;    // raw blocks
   if (o->prec == CTM_PREC_SPLIT_BF16) {
     const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
     b += 8 * 3 * N * Kp * 2;                       // corner slices, both orientations
@@ -1946,6 +1999,7 @@ ctm_status ctm_profile_phases(ctm_ctx* c, double ms[CTM_NPHASES]) {
 void ctm_free(ctm_ctx* c) {
   if (!c) return;
   use_lane(c, 0);
+  grad_destroy(c);
   for (auto& L : c->lanes)
     if (L.stream) cudaStreamSynchronize(L.stream);
   if (c->stream) cudaStreamSynchronize(c->stream);

@@ -110,6 +110,8 @@ struct ctm_ctx {
   std::vector<char> si_rounds_used;   // rounds > 0 in the last move of (r, cut)
   double* dsin2 = nullptr;     // [4 S] mean sin^2 of the last move of each cut
   void* sinG = nullptr;        // [Lmax][k k] X_old^H X_upd of the cuts of a column
+  void* Xraw = nullptr;        // initial raw blocks (randomized-SVD warm-up)
+  void* Wraw = nullptr;
   long n_updates = 0, n_skipped = 0;
   int moves_done[4] = {0, 0, 0, 0};
   int num_sms = 1;
@@ -157,6 +159,7 @@ struct ctm_ctx {
   std::string msg;
   // reverse-mode differentiation: checkpoints of recorded moves
   ctmi::GradState* grad = nullptr;
+  bool bra_is_conj = false;   // iPEPS context with bra = conj(A)
 };
 
 namespace ctm {

@@ -628,6 +628,16 @@ ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* B
   if (raise_smem((const void*)split_mma_kernel, configured, smem) != cudaSuccess)
     return sfail(sc, CTM_ECUDA, "cannot reserve shared memory for the tensor-core kernel");
   dim3 grid(mt, nchunks, nks);
+  if (sc->prof && sc->ev_used + 2 > sc->ev.size()) {
+    // every launch of the profiled region is timed: the event pool grows
+    const size_t old = sc->ev.size();
+    sc->ev.resize(old + 8192);
+    for (size_t i = old; i < sc->ev.size(); ++i)
+      if (cudaEventCreate(&sc->ev[i]) != cudaSuccess) {
+        sc->ev.resize(i);
+        break;
+      }
+  }
   const bool timed = sc->prof && sc->ev_used + 2 <= sc->ev.size();
   if (timed) cudaEventRecord(sc->ev[sc->ev_used], s);
   split_mma_kernel<<<grid, 128, smem, s>>>(ta, tb, p);

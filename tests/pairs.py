@@ -32,7 +32,8 @@ def make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, seed=0, diag=0.0, decay=1.0, *
                     p=opts.p, si_rounds=opts.si_rounds, X0=X0, W0=W0,
                     cutoff=opts.svd_rel_cutoff, warmup_iters=opts.warmup_iters,
                     warmup_rounds=opts.warmup_rounds, recycle_sin2=opts.recycle_sin2,
-                    min_si_steps=opts.min_si_steps)
+                    min_si_steps=opts.min_si_steps, coupled=bool(opts.si_coupled),
+                    warmup_rsvd=bool(opts.warmup_rsvd))
     return ctx, ref
 
 

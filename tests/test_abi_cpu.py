@@ -43,6 +43,7 @@ def test_default_opts_without_gpu(lib):
             o.normalize, o.sign_fix) == (5, 1, 5, 8, 0, 0, 1, 1)
     assert o.svd_rel_cutoff == 1e-12
     assert (o.svd_max_sweeps, o.init_mode, o.recycle_sin2, o.min_si_steps) == (80, 0, 0.0, 3)
+    assert (o.absorb_tc, o.si_coupled, o.warmup_rsvd) == (0, 0, 0)
 
 
 def test_bad_options_are_rejected_before_device_work(lib):

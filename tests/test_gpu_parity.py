@@ -304,3 +304,20 @@ def test_recycling_policy_matches_oracle():
     assert (upd, skipped) == (ref.n_updates, ref.n_skipped)
     _compare(ctx, ref)
     ctx.ctm_free()
+
+
+@pytest.mark.parametrize("variant", [dict(si_coupled=1), dict(warmup_rsvd=1)])
+def test_si_variants_match_oracle(variant):
+    """The coupled (Halko) rangefinder update and the randomized-SVD warm-up:
+    the first iteration tracks the oracle's same variant (1e-8) and the
+    converged environment matches it (1e-10)."""
+    ctx, ref = make_pair(2, 2, 2, 2, 8, 5, True, 1, **variant)
+    for r in range(4):
+        ctx.ctm_move(r)
+    ref.iteration()
+    _compare(ctx, ref, energies=False, tol=1e-8)
+    _, _, ok = ctx.ctm_converge(1e-11, 200)
+    _, d_ref = ref.converge(1e-11, 200)
+    assert ok and d_ref < 1e-11
+    _compare(ctx, ref)
+    ctx.ctm_free()

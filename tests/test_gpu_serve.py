@@ -21,6 +21,8 @@ MIX = [
     (2, 2, 2, 5, 3),
     (1, 2, 3, 9, 4),
     (1, 1, 2, 4, 5),
+    (3, 3, 2, 4, 6),        # a 3x3 cell
+    (1, 1, 5, 6, 7),        # D = 5
 ]
 TOL, MAXIT = 1e-9, 150
 

@@ -439,3 +439,42 @@ def test_recycling_policy_keeps_the_fixed_point_to_its_accuracy():
         assert np.abs(a.spectra()[lab][0] - b.spectra()[lab][0]).max() < 1e-4
     for direction in (0, 1):
         assert abs(a.expect2(HEIS, 0, 0, direction) - b.expect2(HEIS, 0, 0, direction)) < 1e-4
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_coupled_rounds_reach_svd_projector_on_one_cut(cplx):
+    """Reading c13 (the coupled Halko form W <- qr(M X), X <- qr(M^H W)):
+    its rounds also converge to the leading singular subspaces of M, so the
+    oblique projector equals the truncated-SVD one (as P7 for the paper's
+    independent updates)."""
+    ctm = _random_cell("svd", Lx=1, Ly=1, D=2, chi=6, cplx=cplx, seed=6)
+    for _ in range(3):
+        ctm.iteration()
+    Q = ctm.cut_corners(ctmrg.Frame(1, 1, 0), 0, 0)
+    N, chi = Q[1].shape[1], 6
+    rng = np.random.default_rng(11)
+    X = ctmrg.qr_q(rng.standard_normal((N, chi + 4)) + (1j * rng.standard_normal((N, chi + 4)) if cplx else 0))
+    W = ctmrg.qr_q(rng.standard_normal((N, chi + 4)) + (1j * rng.standard_normal((N, chi + 4)) if cplx else 0))
+    svd = ctmrg.projectors_svd(*Q, chi)
+    si = ctmrg.projectors_si(*Q, X, W, chi, rounds=60, coupled=True)
+    assert np.abs(_oblique(si[0], si[1]) - _oblique(svd[0], svd[1])).max() < 1e-9
+    assert np.abs(si[2] - svd[2]).max() / svd[2][0] < 1e-10
+
+
+@pytest.mark.parametrize("variant", [dict(coupled=True), dict(warmup_rsvd=True)])
+def test_si_variants_reach_the_svd_fixed_point(variant):
+    """The coupled update and the randomized-SVD warm-up change the path,
+    not the fixed point: converged spectra and energies equal the standard
+    method's (P7)."""
+    ref = _random_cell("svd", Lx=1, Ly=1, D=2, chi=12, cplx=False, rounds=2, seed=4)
+    ref.converge(1e-13, 400)
+    ctm = _random_cell("si", Lx=1, Ly=1, D=2, chi=12, cplx=False, rounds=2, seed=4)
+    ctm.coupled = variant.get("coupled", False)
+    ctm.warmup_rsvd = variant.get("warmup_rsvd", False)
+    ctm.warmup_iters, ctm.warmup_rounds = 3, 4
+    it, delta = ctm.converge(1e-13, 400)
+    assert delta < 1e-12
+    for lab in range(4):
+        assert np.abs(ref.spectra()[lab][0] - ctm.spectra()[lab][0]).max() < 1e-10
+    for direction in (0, 1):
+        assert abs(ref.expect2(HEIS, 0, 0, direction) - ctm.expect2(HEIS, 0, 0, direction)) < 1e-10
