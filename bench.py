@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["split", "fp64"], default="split")
+    ap.add_argument("--prec", choices=["split", "tf32", "fp64"], default="split",
+                    help="split: bf16 x3 slices; tf32: 3xTF32 slices; fp64: no slicing")
     ap.add_argument("--method", choices=["si", "svd"], default="si",
                     help="projectors: subspace iteration or the standard truncated SVD")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -248,7 +249,8 @@ def run_ours(args, rank, world, local_rank):
     k = min(chi + p, N)
     X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx)
     stream = torch.cuda.current_stream()
-    prec = pkg.CTM_PREC_SPLIT_BF16 if args.prec == "split" else pkg.CTM_PREC_FP64
+    prec = {"split": pkg.CTM_PREC_SPLIT_BF16, "tf32": pkg.CTM_PREC_SPLIT_TF32,
+            "fp64": pkg.CTM_PREC_FP64}[args.prec]
     # the algorithm's own warm-up (first WARM_ITERS iterations with
     # WARM_ROUNDS subspace-iteration rounds and the fp64 QR schedule) runs in
     # the untimed warm-up steps; timed steps are steady-state SI moves with
@@ -290,7 +292,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    prof = ctx.ctm_profile_read() if prec == pkg.CTM_PREC_SPLIT_BF16 else None
+    prof = ctx.ctm_profile_read() if prec != pkg.CTM_PREC_FP64 else None
     phases = {k_: round(v / args.steps, 2) for k_, v in ctx.ctm_profile_phases().items()}
     ms = max_over_ranks(ms, dist, "cuda")
     value = job_throughput(4 * args.steps, world, ms / 1000.0)
@@ -328,21 +330,27 @@ def run_ours(args, rank, world, local_rank):
         # flops per multiply-add = the tensor-pipe flops of the six bf16 slice
         # products / 6
         pipe = mma_flops / (mma_ms * 1e-3) / 1e12
-        achieved = pipe / SLICE_PRODUCTS
+        nprod = SLICE_PRODUCTS if args.prec == "split" else 3
+        achieved = pipe / nprod
         peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        if args.prec == "tf32":
+            peak = peak / 2.0   # tf32 kind at half the bf16 rate (nominal ratio)
         traffic = (None if TRAFFIC_PER_OPERAND_BYTE is None
                    else round(TRAFFIC_PER_OPERAND_BYTE * mma_bytes / mma_n))
-        roofline = {"bound": "tensor", "kernel": "split_mma_kernel (tcgen05 bf16, fp32 accum)",
+        roofline = {"bound": "tensor",
+                    "kernel": "split_mma_kernel (tcgen05 %s, fp32 accum)"
+                              % ("kind::f16 bf16" if args.prec == "split" else "kind::tf32"),
                     "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
                     "achieved_basis": "algorithmic flops (8 per complex multiply-add) per "
                                       "launch / CUDA-event duration on the launching stream",
                     "tensor_pipe_achieved": round(pipe, 2),
                     "tensor_pipe_frac": round(pipe / peak, 4),
-                    "tensor_pipe_basis": f"{SLICE_PRODUCTS} bf16 slice products of the "
-                                         "real-embedded problem",
-                    "peak_source": f"{src} bf16 sustained (of measured)" if src == "measured"
-                    else "fallback 1.7 PFLOP/s sustained (of fallback)",
+                    "tensor_pipe_basis": f"{nprod} {'bf16' if nprod == 6 else 'tf32'} slice "
+                                         "products of the real-embedded problem",
+                    "peak_source": (f"{src} bf16 sustained (of measured)" if src == "measured"
+                                    else "fallback 1.7 PFLOP/s sustained (of fallback)")
+                    + (" x 1/2 (nominal tf32 / bf16 ratio)" if args.prec == "tf32" else ""),
                     "launches": mma_n, "launches_covered": "every launch of the timed steps",
                     "kernel_ms": round(mma_ms, 3),
                     "kernel_share_of_step": round(mma_ms / ms, 4),
@@ -366,8 +374,10 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "c128" if cplx else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "cell": f"{Lx}x{Ly}", "d": d, "D": D, "chi": chi,
                    "p": p, "N": N, "k": k, "si_rounds": w["si_rounds"],
-                   "precision": "split-bf16x3 (6 slice products; s0 t0 and the rest in separate fp32 accumulators), fp64 QR/SVD"
-                   if args.prec == "split" else "fp64",
+                   "precision": {"split": "split-bf16x3 (6 slice products; s0 t0 and the rest "
+                                          "in separate fp32 accumulators), fp64 QR/SVD",
+                                 "tf32": "split-3xTF32 (3 slice products), fp64 QR/SVD",
+                                 "fp64": "fp64"}[args.prec],
                    "projectors": "subspace iteration" if args.method == "si"
                    else "standard truncated SVD (dense gesvd)",
                    "step": "1 iteration = 4 moves + corner-spectrum scalar",

@@ -63,10 +63,12 @@ typedef enum { CTM_F64 = 0, CTM_C128 = 1 } ctm_dtype;
 /* Arithmetic of the large contractions. FP64: every product in double.
  * SPLIT_BF16: corner x block products and the large GEMMs of the enlarged
  * corners and the absorption as sums of bf16 slice products on the tensor
- * cores with fp32 accumulation and fp64 reduction, the fused A / conj(A)
- * absorption in fp32; QR, small SVD, rho, the projectors and s^-1/2 stay
- * fp64. */
-typedef enum { CTM_PREC_FP64 = 0, CTM_PREC_SPLIT_BF16 = 1 } ctm_prec;
+ * cores (three bf16 slices of each operand's fp32 rounding, six products)
+ * with fp32 accumulation and fp64 reduction, the fused A / conj(A)
+ * absorption in fp32. SPLIT_TF32: the same with 3xTF32 (two tf32 slices,
+ * three products, the tensor cores' tf32 kind at half the bf16 rate). QR,
+ * small SVD, rho, the projectors and s^-1/2 stay fp64 in both. */
+typedef enum { CTM_PREC_FP64 = 0, CTM_PREC_SPLIT_BF16 = 1, CTM_PREC_SPLIT_TF32 = 2 } ctm_prec;
 
 typedef enum { CTM_LEFT = 0, CTM_UP = 1, CTM_RIGHT = 2, CTM_DOWN = 3 } ctm_dir;
 

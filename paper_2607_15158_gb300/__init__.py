@@ -21,7 +21,7 @@ CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENOCONV, CTM_ETIMEOUT, \
 STATUS_NAMES = ["CTM_OK", "CTM_EINVAL", "CTM_ENOMEM", "CTM_ECUDA", "CTM_ENOCONV",
                 "CTM_ETIMEOUT", "CTM_ENUMERIC", "CTM_EUNSUPPORTED"]
 CTM_F64, CTM_C128 = 0, 1
-CTM_PREC_FP64, CTM_PREC_SPLIT_BF16 = 0, 1
+CTM_PREC_FP64, CTM_PREC_SPLIT_BF16, CTM_PREC_SPLIT_TF32 = 0, 1, 2
 CTM_LEFT, CTM_UP, CTM_RIGHT, CTM_DOWN = 0, 1, 2, 3
 CTM_PROJ_SI, CTM_PROJ_SVD = 0, 1
 CTM_INIT_RANDOM, CTM_INIT_FROM_A = 0, 1

@@ -399,7 +399,7 @@ ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
 // Y = op(Q) Z for an N x N corner and an N x k block.
 ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, void* Zout) {
   PhaseScope ps(c, PH_PROD);
-  if (c->opts.prec == CTM_PREC_SPLIT_BF16 && c->split) {
+  if (c->split) {
     const ctm_status st = split_apply(c->split, Qm, herm, Zin, Zout, c->N, c->k, c->stream,
                                       &c->launches);
     if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
@@ -1079,6 +1079,7 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   else ctm_default_opts(&c->opts);
   if (c->opts.p < 0 || c->opts.si_rounds < 0 || c->opts.warmup_iters < 0 ||
       c->opts.warmup_rounds < 0 || c->opts.svd_max_sweeps < 1 || c->opts.min_si_steps < 0 ||
+      c->opts.prec < CTM_PREC_FP64 || c->opts.prec > CTM_PREC_SPLIT_TF32 ||
       !(c->opts.recycle_sin2 >= 0.0) ||
       (c->opts.init_mode != CTM_INIT_RANDOM && c->opts.init_mode != CTM_INIT_FROM_A)) {
     delete c;
@@ -1225,8 +1226,9 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   if ((st = upload_default_state(c)) != CTM_OK) return bail(st);
   if (c->opts.init_mode == CTM_INIT_FROM_A && (st = init_env_from_tensors(c)) != CTM_OK)
     return bail(st);
-  if (c->opts.prec == CTM_PREC_SPLIT_BF16) {
-    st = split_create(&c->split, cx, (int)N, (int)k, c->err, c->stream);
+  if (c->opts.prec != CTM_PREC_FP64) {
+    st = split_create(&c->split, cx, c->opts.prec == CTM_PREC_SPLIT_TF32, (int)N, (int)k, c->err,
+                      c->stream);
     if (st != CTM_OK) {
       c->msg = "split-precision setup failed";
       return bail(st);
@@ -1263,7 +1265,7 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       // a lane only builds corners and runs the SI round: its pipelines hold
       // N^2 elements (d N^2 for the unfused absorption), not the d^2 N^2 of
       // the two-site observables of lane 0
-      const bool fused = use_fused_absorb(cx, c->opts.prec == CTM_PREC_SPLIT_BF16, c->opts,
+      const bool fused = use_fused_absorb(cx, c->opts.prec != CTM_PREC_FP64, c->opts,
                                           (int)Dk, (int)Db, d);
       const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
       M.scratch_bytes = 2 * laneT * es + ((size_t)64 << 20);
@@ -1281,8 +1283,9 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
           (st = dalloc(c, (void**)&M.dead, k * sizeof(int))) != CTM_OK ||
           (st = dalloc(c, &M.chol_work, chol_coop_work_bytes((int)k, 1))) != CTM_OK)
         return bail(st);
-      if (c->opts.prec == CTM_PREC_SPLIT_BF16 &&
-          (st = split_create(&M.split, cx, (int)N, (int)k, c->err, M.stream)) != CTM_OK) {
+      if (c->opts.prec != CTM_PREC_FP64 &&
+          (st = split_create(&M.split, cx, c->opts.prec == CTM_PREC_SPLIT_TF32, (int)N, (int)k,
+                             c->err, M.stream)) != CTM_OK) {
         c->msg = "split-precision setup failed";
         return bail(st);
       }
@@ -1527,22 +1530,25 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
   b += 2 * (size_t)d * d * d * d * es + 2 * nk * es + ((size_t)1 << 20);
   b += Lmax * k * k * es + 4 * S * sizeof(double);   // recycling policy
   if (o->warmup_rsvd) b += 2 * 4 * S * N * k * es;    // raw blocks
-  if (o->prec == CTM_PREC_SPLIT_BF16) {
+  if (o->prec != CTM_PREC_FP64) {
+    // slices: 3 bf16 (6 bytes) or 2 tf32 (8 bytes) per element
     const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
-    b += 8 * 3 * N * Kp * 2;                       // corner slices, both orientations
-    b += 2 * 3 * N * Kp * 2;                       // operand slices of general products
+    const size_t sb = o->prec == CTM_PREC_SPLIT_TF32 ? 8 : 6;
+    b += 8 * N * Kp * sb;                          // corner slices, both orientations
+    b += 2 * N * Kp * sb;                          // operand slices of general products
     b += split_partial_splits(N, cx) * N * ((cx ? 2 : 1) * k + 160) * 4;   // split-K partials
   }
   if (o->method == CTM_PROJ_SVD) b += 3 * NN * es + 2 * N * chi * es + (size_t)64 * N * es;
   if (o->method == CTM_PROJ_SI) {
     // lanes 1 .. nl-1: corners, pipes, scratch, N x k blocks, QR work, split state
-    const bool fused = use_fused_absorb(cx, o->prec == CTM_PREC_SPLIT_BF16, *o, Dk, Db, d);
+    const bool fused = use_fused_absorb(cx, o->prec != CTM_PREC_FP64, *o, Dk, Db, d);
     const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
     size_t lane = 4 * NN * es + 4 * laneT * es + ((size_t)64 << 20) + 4 * N * k * es +
                   2 * k * k * es + 12 * k + chol_coop_work_bytes((int)k, 1);
-    if (o->prec == CTM_PREC_SPLIT_BF16) {
+    if (o->prec != CTM_PREC_FP64) {
       const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
-      lane += 10 * 3 * N * Kp * 2 + split_partial_splits(N, cx) * N * ((cx ? 2 : 1) * k + 160) * 4;
+      const size_t sb = o->prec == CTM_PREC_SPLIT_TF32 ? 8 : 6;
+      lane += 10 * N * Kp * sb + split_partial_splits(N, cx) * N * ((cx ? 2 : 1) * k + 160) * 4;
     }
     b += (size_t)(lanes_for(Lx, Ly) - 1) * lane;
   }

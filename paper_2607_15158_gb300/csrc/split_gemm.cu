@@ -1,7 +1,8 @@
 // Split-precision GEMM on the sm_103a tensor cores (tcgen05 + TMA + TMEM).
 //
 // C = op(A) op(B) for fp64 (or complex fp64) operands, computed as sums of
-// bf16 x bf16 products with fp32 accumulation:
+// low-precision slice products with fp32 accumulation, in one of two
+// formats. bf16 x3 (CTM_PREC_SPLIT_BF16):
 //   * every fp64 value x is split into three bf16 slices x = s0 + s1 + s2 + e
 //     (the slices of x rounded to fp32, each the bf16 rounding of the
 //     remainder; |e| <= 2^-24 |x|);
@@ -10,6 +11,11 @@
 //     accumulated in its own fp32 accumulator in tensor memory and the five
 //     smaller ones in a second, so that their additions cost ulps of a
 //     2^-8 smaller running sum, and the two are added once per partial;
+// 3xTF32 (CTM_PREC_SPLIT_TF32): x = t0 + t1 + e with tf32 slices of the fp32
+// rounding (|e| <= 2^-22 |x|), three products t0 u0 (own accumulator),
+// t0 u1 + t1 u0 (second accumulator), tcgen05 kind::tf32 at half the bf16
+// rate. Both formats stage 128-byte K rows (64 bf16 or 32 tf32 values), so
+// tiles, swizzle and descriptors are shared.
 //   * complex data uses the real embedding A_emb = [A_r | A_i] (M x 2K),
 //     B_emb = [[B_r, B_i], [-B_i, B_r]] (2K x 2N), C_emb = [C_r | C_i];
 //   * K is split over CTAs, at most KB_SPLIT_MAX K blocks of 64 each (the
@@ -41,10 +47,11 @@ namespace ctm {
 namespace {
 
 constexpr int BM = 128;          // rows per CTA (tcgen05 M)
-constexpr int BK = 64;           // K elements per stage (128 bytes of bf16)
+constexpr int BK = 64;           // bf16 K elements per stage (128 bytes)
+constexpr int KROW = 128;        // bytes of one staged K row (either format)
 constexpr int STAGES = 2;
 constexpr int MAX_BNC = 160;     // columns per CTA
-constexpr int A_SLICE_BYTES = BM * BK * 2;   // 16 KB
+constexpr int A_SLICE_BYTES = BM * KROW;     // 16 KB
 constexpr uint64_t WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
 #ifndef CTM_KB_SPLIT_MAX
 #define CTM_KB_SPLIT_MAX 8
@@ -121,6 +128,30 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// instruction descriptor of kind::tf32: tf32 x tf32 -> f32 (format code 2),
+// both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// slice formats: NS slices per operand, NP slice products (the first in its
+// own accumulator), element bytes EB, K elements per 128-byte row KE
+struct FmtBF16 {
+  static constexpr int NS = 3, NP = 6, EB = 2, KE = 64;
+};
+struct FmtTF32 {
+  static constexpr int NS = 2, NP = 3, EB = 4, KE = 32;
+};
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -148,6 +179,7 @@ struct MmaParams {
   int* err;
 };
 
+template <typename F>
 __global__ void __launch_bounds__(128, 1)
     split_mma_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, MmaParams p) {
@@ -155,8 +187,8 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int BNc = p.BNc;
-  const uint32_t b_slice_bytes = (uint32_t)BNc * BK * 2;
-  const uint32_t stage_bytes = 3 * A_SLICE_BYTES + 3 * b_slice_bytes;
+  const uint32_t b_slice_bytes = (uint32_t)BNc * KROW;
+  const uint32_t stage_bytes = F::NS * A_SLICE_BYTES + F::NS * b_slice_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
@@ -206,16 +238,16 @@ __global__ void __launch_bounds__(128, 1)
       const uint32_t full = full0 + 8 * s;
       mbar_expect_tx(full, stage_bytes);
       uint8_t* st = smem + s * stage_bytes;
-      const int kx = (kb0 + kb) * BK;
-      for (int sl = 0; sl < 3; ++sl)
+      const int kx = (kb0 + kb) * F::KE;
+      for (int sl = 0; sl < F::NS; ++sl)
         tma_load_3d(smem_u32(st + sl * A_SLICE_BYTES), &tmA, kx, m_tile * BM, sl, full);
-      for (int sl = 0; sl < 3; ++sl)
-        tma_load_3d(smem_u32(st + 3 * A_SLICE_BYTES + sl * b_slice_bytes), &tmB, kx,
+      for (int sl = 0; sl < F::NS; ++sl)
+        tma_load_3d(smem_u32(st + F::NS * A_SLICE_BYTES + sl * b_slice_bytes), &tmB, kx,
                     chunk * BNc, sl, full);
     }
   } else if (nkb > 0 && warp == 1 && lane == 0) {
-    // MMA issuer: six slice products per K block, four K=16 steps each
-    const uint32_t idesc = idesc_bf16(BM, BNc);
+    // MMA issuer: NP slice products per K block, four 32-byte K steps each
+    const uint32_t idesc = F::EB == 2 ? idesc_bf16(BM, BNc) : idesc_tf32(BM, BNc);
     const int pa[6] = {0, 0, 1, 0, 1, 2};
     const int pb[6] = {0, 1, 0, 2, 1, 0};
     bool ok = true;
@@ -228,14 +260,18 @@ __global__ void __launch_bounds__(128, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = smem_u32(smem + s * stage_bytes);
-      for (int pr = 0; pr < 6; ++pr) {
+      for (int pr = 0; pr < F::NP; ++pr) {
         const uint32_t a0 = st + pa[pr] * A_SLICE_BYTES;
-        const uint32_t b0 = st + 3 * A_SLICE_BYTES + pb[pr] * b_slice_bytes;
+        const uint32_t b0 = st + F::NS * A_SLICE_BYTES + pb[pr] * b_slice_bytes;
         const uint32_t d = pr == 0 ? tmem : tmem + acc1;
         const bool first = kb == 0 && (pr == 0 || pr == 1);
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
-                   (first && kk == 0) ? 0u : 1u);
+        for (int kk = 0; kk < KROW / 32; ++kk) {
+          if (F::EB == 2)
+            mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                     (first && kk == 0) ? 0u : 1u);
+          else
+            mma_tf32(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                     (first && kk == 0) ? 0u : 1u);
         }
       }
       mma_commit(empty0 + 8 * s);
@@ -292,17 +328,38 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat1
   s2 = __float2bfloat16_rn(r2);
 }
 
-__device__ __forceinline__ void put3(__nv_bfloat16* out, long slice, long o, __nv_bfloat16 s0,
-                                     __nv_bfloat16 s1, __nv_bfloat16 s2) {
-  out[o] = s0;
-  out[slice + o] = s1;
-  out[2 * slice + o] = s2;
+// tf32 rounding of an fp32 value (nearest, ties away from zero): the 13 low
+// mantissa bits are dropped after adding half of the last kept bit
+__device__ __forceinline__ float tf32_rn(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 
-__device__ __forceinline__ void emit3(__nv_bfloat16* out, long slice, long o, double x) {
-  __nv_bfloat16 s0, s1, s2;
-  split3(x, s0, s1, s2);
-  put3(out, slice, o, s0, s1, s2);
+// the NS slices of x in format F (bf16: split3; tf32: t0 = tf32(xf),
+// t1 = tf32(xf - t0), the subtraction exact in fp32)
+template <typename F> struct SliceT;
+template <> struct SliceT<FmtBF16> { using T = __nv_bfloat16; };
+template <> struct SliceT<FmtTF32> { using T = float; };
+
+__device__ __forceinline__ void slices_of(FmtBF16, double x, __nv_bfloat16* v) {
+  split3(x, v[0], v[1], v[2]);
+}
+__device__ __forceinline__ void slices_of(FmtTF32, double x, float* v) {
+  const float xf = f32_of(x);
+  v[0] = tf32_rn(xf);
+  v[1] = tf32_rn(xf - v[0]);
+}
+__device__ __forceinline__ __nv_bfloat16 negv(__nv_bfloat16 a) { return __hneg(a); }
+__device__ __forceinline__ float negv(float a) { return -a; }
+template <typename T> __device__ __forceinline__ T zero_slice();
+template <> __device__ __forceinline__ __nv_bfloat16 zero_slice<__nv_bfloat16>() {
+  return __float2bfloat16(0.0f);
+}
+template <> __device__ __forceinline__ float zero_slice<float>() { return 0.0f; }
+
+template <typename F, typename T>
+__device__ __forceinline__ void put_slices(T* out, long slice, long o, const T* v, bool neg) {
+#pragma unroll
+  for (int i = 0; i < F::NS; ++i) out[i * slice + o] = neg ? negv(v[i]) : v[i];
 }
 
 
@@ -310,9 +367,10 @@ __device__ __forceinline__ void emit3(__nv_bfloat16* out, long slice, long o, do
 // (complex); zero up to Kp. A 32 x 32 shared tile of op(A) is read along A's
 // contiguous axis (rows for op N / R, columns for op T / C) and each element
 // is read once and written to both halves.
-template <typename T>
+template <typename T, typename F>
 __global__ void prep_a_kernel(const T* A, long lda, int op, int M, int K, int Kp,
-                               __nv_bfloat16* out) {
+                              typename SliceT<F>::T* out) {
+  using S = typename SliceT<F>::T;
   __shared__ T tile[32][33];
   constexpr bool cx = sizeof(T) == 16;
   const int Kr = cx ? 2 * K : K;
@@ -337,39 +395,38 @@ __global__ void prep_a_kernel(const T* A, long lda, int op, int M, int K, int Kp
       const int m = m0 + yy, kk = k0 + threadIdx.x;
       if (m < M && kk < K) {
         const T v = tile[yy][threadIdx.x];
+        S sv[3];
         if constexpr (cx) {
-          emit3(out, slice, (long)m * Kp + kk, v.x);
-          __nv_bfloat16 i0, i1, i2;
-          split3(v.y, i0, i1, i2);
-          if (cj) { i0 = __hneg(i0); i1 = __hneg(i1); i2 = __hneg(i2); }
-          put3(out, slice, (long)m * Kp + K + kk, i0, i1, i2);
+          slices_of(F(), v.x, sv);
+          put_slices<F>(out, slice, (long)m * Kp + kk, sv, false);
+          slices_of(F(), v.y, sv);
+          put_slices<F>(out, slice, (long)m * Kp + K + kk, sv, cj);
         } else {
-          emit3(out, slice, (long)m * Kp + kk, v);
+          slices_of(F(), v, sv);
+          put_slices<F>(out, slice, (long)m * Kp + kk, sv, false);
         }
       }
     }
     __syncthreads();
   }
   // padding columns kr >= Kr
-  const __nv_bfloat16 z = __float2bfloat16(0.0f);
+  const S z = zero_slice<S>();
+  const S zz[3] = {z, z, z};
   const int pc = Kp - Kr;
   const long tid = (long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x * blockDim.y;
-  for (long idx = tid; idx < (long)M * pc; idx += nth) {
-    const long o = (idx / pc) * Kp + Kr + idx % pc;
-    out[o] = z;
-    out[slice + o] = z;
-    out[2 * slice + o] = z;
-  }
+  for (long idx = tid; idx < (long)M * pc; idx += nth)
+    put_slices<F>(out, slice, (idx / pc) * Kp + Kr + idx % pc, zz, false);
 }
 
 // B slices (K-major rows = output real columns): out[s][j][kr] = B_emb[kr][j]
 // with B_emb = [[B_r, B_i], [-B_i, B_r]] for complex, B for real. A 32 x 32
 // shared tile of op(B) is read along B's contiguous axis and written along
 // kr; the padding rows and columns are zeroed.
-template <typename T>
+template <typename T, typename F>
 __global__ void prep_b_kernel(const T* B, long ldb, int op, int K, int N, int Kp, int Np,
-                              __nv_bfloat16* out) {
+                              typename SliceT<F>::T* out) {
+  using S = typename SliceT<F>::T;
   __shared__ T tile[32][33];
   constexpr bool cx = sizeof(T) == 16;
   const int Kr = cx ? 2 * K : K;
@@ -395,42 +452,35 @@ __global__ void prep_b_kernel(const T* B, long ldb, int op, int K, int N, int Kp
       const int jj = n0 + yy, kk = k0 + threadIdx.x;
       if (jj < N && kk < K) {
         const T v = tile[threadIdx.x][yy];
+        S re[3], im[3];
         if constexpr (cx) {
           // the slices of -x are the negated slices of x: each part is
           // sliced once
-          __nv_bfloat16 r0, r1, r2, i0, i1, i2;
-          split3(v.x, r0, r1, r2);
-          split3(v.y, i0, i1, i2);
-          if (cj) { i0 = __hneg(i0); i1 = __hneg(i1); i2 = __hneg(i2); }
-          put3(out, slice, (long)jj * Kp + kk, r0, r1, r2);
-          put3(out, slice, (long)jj * Kp + K + kk, __hneg(i0), __hneg(i1), __hneg(i2));
-          put3(out, slice, (long)(N + jj) * Kp + kk, i0, i1, i2);
-          put3(out, slice, (long)(N + jj) * Kp + K + kk, r0, r1, r2);
+          slices_of(F(), v.x, re);
+          slices_of(F(), v.y, im);
+          put_slices<F>(out, slice, (long)jj * Kp + kk, re, false);
+          put_slices<F>(out, slice, (long)jj * Kp + K + kk, im, !cj);
+          put_slices<F>(out, slice, (long)(N + jj) * Kp + kk, im, cj);
+          put_slices<F>(out, slice, (long)(N + jj) * Kp + K + kk, re, false);
         } else {
-          emit3(out, slice, (long)jj * Kp + kk, v);
+          slices_of(F(), v, re);
+          put_slices<F>(out, slice, (long)jj * Kp + kk, re, false);
         }
       }
     }
     __syncthreads();
   }
-  const __nv_bfloat16 z = __float2bfloat16(0.0f);
+  const S z = zero_slice<S>();
+  const S zz[3] = {z, z, z};
   const long tid = (long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x * blockDim.y;
   // padding rows j >= Nr
-  for (long idx = tid; idx < (long)(Np - Nr) * Kp; idx += nth) {
-    const long o = (long)Nr * Kp + idx;
-    out[o] = z;
-    out[slice + o] = z;
-    out[2 * slice + o] = z;
-  }
+  for (long idx = tid; idx < (long)(Np - Nr) * Kp; idx += nth)
+    put_slices<F>(out, slice, (long)Nr * Kp + idx, zz, false);
   // padding columns kr >= Kr of the rows j < Nr
   const int pc = Kp - Kr;
-  for (long idx = tid; idx < (long)Nr * pc; idx += nth) {
-    const long o = (idx / pc) * Kp + Kr + idx % pc;
-    out[o] = z;
-    out[slice + o] = z;
-    out[2 * slice + o] = z;
-  }
+  for (long idx = tid; idx < (long)Nr * pc; idx += nth)
+    put_slices<F>(out, slice, (idx / pc) * Kp + Kr + idx % pc, zz, false);
 }
 
 // error-free sum of two fp32 values (Knuth's TwoSum): hi + lo == a + b
@@ -505,15 +555,18 @@ EncodeTiledFn get_encoder() {
   return fn;
 }
 
-// 3-D map over [3][rows][Kp] bf16 with a (64, box_rows, 1) box, 128B swizzle
-bool make_map(CUtensorMap* map, const void* base, int rows, int Kp, int box_rows) {
+// 3-D map over [ns][rows][Kp] slices (bf16 or tf32-in-fp32) with a
+// (128 bytes, box_rows, 1) box, 128B swizzle
+bool make_map(CUtensorMap* map, const void* base, int rows, int Kp, int box_rows, bool tf32) {
   EncodeTiledFn enc = get_encoder();
   if (!enc) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const int eb = tf32 ? 4 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)(tf32 ? 2 : 3)};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * eb, (cuuint64_t)Kp * eb * rows};
+  cuuint32_t box[3] = {(cuuint32_t)(KROW / eb), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+  return enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+             const_cast<void*>(base), dims, strides,
              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
@@ -524,16 +577,17 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int Kp, int box_rows
 // ------------------------------------------------------------ context
 struct SplitCtx {
   bool cx = false;
+  bool tf32 = false;        // 3xTF32 slices instead of bf16 x3
   int N = 0, k = 0;
   std::string msg;
   // cached corner operands: [corner][op N / op H] slices, and their sources
   void* corner_src[4] = {nullptr};
-  __nv_bfloat16* cslices[4][2] = {{nullptr}};
+  void* cslices[4][2] = {{nullptr}};
   int corner_Kp = 0;
   // generic operand buffers (grown on demand)
-  __nv_bfloat16* abuf = nullptr;
+  void* abuf = nullptr;
   size_t abuf_bytes = 0;
-  __nv_bfloat16* bbuf = nullptr;
+  void* bbuf = nullptr;
   size_t bbuf_bytes = 0;
   float* part = nullptr;
   size_t part_bytes = 0;
@@ -578,10 +632,10 @@ void chunking(int Nr, int* nchunks, int* BNc) {
   *BNc = b;
 }
 
-int choose_splits(int tiles, int kb_total) {
+int choose_splits(int tiles, int kb_total, int kb_max) {
   int best = 1;
   double best_t = 1e30;
-  const int smin = (kb_total + KB_SPLIT_MAX - 1) / KB_SPLIT_MAX;
+  const int smin = (kb_total + kb_max - 1) / kb_max;
   const int smax = std::max(smin, std::min(std::max(32, smin), kb_total / 4));
   for (int s = smin; s <= smax; ++s) {
     const int per = (kb_total + s - 1) / s;
@@ -598,21 +652,27 @@ int choose_splits(int tiles, int kb_total) {
 thread_local int g_kr_real = 0;
 inline double Kr_used(int Kp, const SplitCtx*) { return g_kr_real > 0 ? g_kr_real : Kp; }
 
-// run the tensor-core kernel on prepared slices: A [3][M][Kp], B [3][Np][Kp]
-ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* Bs, int M, int Kp,
+// slices per operand, K elements per 128-byte row, bytes per slice element
+inline int ns_of(const SplitCtx* sc) { return sc->tf32 ? 2 : 3; }
+inline int ke_of(const SplitCtx* sc) { return sc->tf32 ? 32 : 64; }
+inline int eb_of(const SplitCtx* sc) { return sc->tf32 ? 4 : 2; }
+
+// run the tensor-core kernel on prepared slices: A [ns][M][Kp], B [ns][Np][Kp]
+ctm_status run_mma(SplitCtx* sc, const void* As, const void* Bs, int M, int Kp,
                    int Nr, int nchunks, int BNc, void* C, long ldc, int Nout, cudaStream_t s,
                    long* launches) {
   const int Np = nchunks * BNc;
-  const int kb_total = Kp / BK;
+  const int kb_total = Kp / ke_of(sc);
   const int mt = (M + BM - 1) / BM;
-  const int nks = choose_splits(mt * nchunks, kb_total);
+  // the same K elements per fp32 partial in both formats
+  const int nks = choose_splits(mt * nchunks, kb_total, KB_SPLIT_MAX * BK / ke_of(sc));
   const int kb_split = (kb_total + nks - 1) / nks;
   {
     ctm_status st = grow(sc, (void**)&sc->part, &sc->part_bytes, (size_t)nks * M * Np * 4);
     if (st != CTM_OK) return st;
   }
   CUtensorMap ta, tb;
-  if (!make_map(&ta, As, M, Kp, BM) || !make_map(&tb, Bs, Np, Kp, BNc))
+  if (!make_map(&ta, As, M, Kp, BM, sc->tf32) || !make_map(&tb, Bs, Np, Kp, BNc, sc->tf32))
     return sfail(sc, CTM_ECUDA, "cuTensorMapEncodeTiled failed");
   MmaParams p;
   p.M = M;
@@ -622,10 +682,13 @@ ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* B
   p.kb_split = kb_split;
   p.part = sc->part;
   p.err = sc->err;
-  const size_t smem = 1024 + (size_t)STAGES * (3 * A_SLICE_BYTES + 3 * (size_t)BNc * BK * 2) +
+  const int ns = ns_of(sc);
+  const size_t smem = 1024 + (size_t)STAGES * (ns * A_SLICE_BYTES + ns * (size_t)BNc * KROW) +
                       (2 * STAGES + 1) * 8 + 16;
-  static size_t configured = 0;
-  if (raise_smem((const void*)split_mma_kernel, configured, smem) != cudaSuccess)
+  static size_t configured_bf16 = 0, configured_tf32 = 0;
+  const void* kfn = sc->tf32 ? (const void*)split_mma_kernel<FmtTF32>
+                             : (const void*)split_mma_kernel<FmtBF16>;
+  if (raise_smem(kfn, sc->tf32 ? configured_tf32 : configured_bf16, smem) != cudaSuccess)
     return sfail(sc, CTM_ECUDA, "cannot reserve shared memory for the tensor-core kernel");
   dim3 grid(mt, nchunks, nks);
   if (sc->prof && sc->ev_used + 2 > sc->ev.size()) {
@@ -640,15 +703,18 @@ ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* B
   }
   const bool timed = sc->prof && sc->ev_used + 2 <= sc->ev.size();
   if (timed) cudaEventRecord(sc->ev[sc->ev_used], s);
-  split_mma_kernel<<<grid, 128, smem, s>>>(ta, tb, p);
+  if (sc->tf32) split_mma_kernel<FmtTF32><<<grid, 128, smem, s>>>(ta, tb, p);
+  else split_mma_kernel<FmtBF16><<<grid, 128, smem, s>>>(ta, tb, p);
   if (timed) {
     cudaEventRecord(sc->ev[sc->ev_used + 1], s);
     sc->ev_used += 2;
-    // tensor-pipe work: six bf16 slice products of the real-embedded
-    // (unpadded) problem; bytes: the three slices of both operands once
+    // tensor-pipe work: the slice products (six bf16 or three tf32) of the
+    // real-embedded (unpadded) problem; bytes: all slices of both operands
+    // once, plus the fp32 partials
     sc->prof_launches += 1;
-    sc->prof_flops += 6.0 * 2.0 * (double)M * (double)Nr * (double)Kr_used(Kp, sc);
-    sc->prof_bytes += 6.0 * ((double)M * Kp + (double)nchunks * BNc * Kp) +
+    const double np = sc->tf32 ? 3.0 : 6.0;
+    sc->prof_flops += np * 2.0 * (double)M * (double)Nr * (double)Kr_used(Kp, sc);
+    sc->prof_bytes += (double)ns * eb_of(sc) * ((double)M * Kp + (double)nchunks * BNc * Kp) +
                       4.0 * (double)nks * M * Np;
   }
   if (launches) ++*launches;
@@ -665,38 +731,52 @@ ctm_status run_mma(SplitCtx* sc, const __nv_bfloat16* As, const __nv_bfloat16* B
 }
 
 ctm_status prep_a(SplitCtx* sc, const void* A, long lda, int op, int M, int K, int Kp,
-                  __nv_bfloat16* out, cudaStream_t s, long* launches) {
+                  void* out, cudaStream_t s, long* launches) {
   const long tiles = (long)((K + 31) / 32) * ((M + 31) / 32);
   const unsigned g = (unsigned)std::max<long>(1, std::min<long>(tiles, 152L * 16));
-  if (sc->cx) prep_a_kernel<cplx><<<g, dim3(32, 8), 0, s>>>((const cplx*)A, lda, op, M, K, Kp, out);
-  else prep_a_kernel<double><<<g, dim3(32, 8), 0, s>>>((const double*)A, lda, op, M, K, Kp, out);
+  const dim3 b(32, 8);
+  if (sc->tf32) {
+    if (sc->cx) prep_a_kernel<cplx, FmtTF32><<<g, b, 0, s>>>((const cplx*)A, lda, op, M, K, Kp, (float*)out);
+    else prep_a_kernel<double, FmtTF32><<<g, b, 0, s>>>((const double*)A, lda, op, M, K, Kp, (float*)out);
+  } else {
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
+    if (sc->cx) prep_a_kernel<cplx, FmtBF16><<<g, b, 0, s>>>((const cplx*)A, lda, op, M, K, Kp, o);
+    else prep_a_kernel<double, FmtBF16><<<g, b, 0, s>>>((const double*)A, lda, op, M, K, Kp, o);
+  }
   if (launches) ++*launches;
   return cudaGetLastError() == cudaSuccess ? CTM_OK : sfail(sc, CTM_ECUDA, "slice launch failed");
 }
 
 ctm_status prep_b(SplitCtx* sc, const void* B, long ldb, int op, int K, int N, int Kp, int Np,
-                  __nv_bfloat16* out, cudaStream_t s, long* launches) {
+                  void* out, cudaStream_t s, long* launches) {
   long tiles = (long)((K + 31) / 32) * ((N + 31) / 32);
   if (tiles > 152L * 8) tiles = 152L * 8;
   if (tiles < 1) tiles = 1;
   const dim3 blk(32, 8);
-  if (sc->cx)
-    prep_b_kernel<cplx><<<(unsigned)tiles, blk, 0, s>>>((const cplx*)B, ldb, op, K, N, Kp, Np, out);
-  else
-    prep_b_kernel<double><<<(unsigned)tiles, blk, 0, s>>>((const double*)B, ldb, op, K, N, Kp, Np,
-                                                          out);
+  const unsigned g = (unsigned)tiles;
+  if (sc->tf32) {
+    float* o = static_cast<float*>(out);
+    if (sc->cx) prep_b_kernel<cplx, FmtTF32><<<g, blk, 0, s>>>((const cplx*)B, ldb, op, K, N, Kp, Np, o);
+    else prep_b_kernel<double, FmtTF32><<<g, blk, 0, s>>>((const double*)B, ldb, op, K, N, Kp, Np, o);
+  } else {
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
+    if (sc->cx) prep_b_kernel<cplx, FmtBF16><<<g, blk, 0, s>>>((const cplx*)B, ldb, op, K, N, Kp, Np, o);
+    else prep_b_kernel<double, FmtBF16><<<g, blk, 0, s>>>((const double*)B, ldb, op, K, N, Kp, Np, o);
+  }
   if (launches) ++*launches;
   return cudaGetLastError() == cudaSuccess ? CTM_OK : sfail(sc, CTM_ECUDA, "slice launch failed");
 }
 
 }  // namespace
 
-ctm_status split_create(SplitCtx** out, bool cx, int N, int k, int* err, cudaStream_t s) {
+ctm_status split_create(SplitCtx** out, bool cx, bool tf32, int N, int k, int* err,
+                        cudaStream_t s) {
   (void)s;
   *out = nullptr;
   if (!get_encoder()) return CTM_EUNSUPPORTED;
   SplitCtx* sc = new SplitCtx();
   sc->cx = cx;
+  sc->tf32 = tf32;
   sc->N = N;
   sc->k = k;
   sc->err = err;
@@ -749,14 +829,14 @@ void split_destroy(SplitCtx* sc) {
 ctm_status split_prepare_corners(SplitCtx* sc, void* const* Q, int N, unsigned mask,
                                  cudaStream_t s, long* launches) {
   const int Kr = sc->cx ? 2 * N : N;
-  const int Kp = pad_to(Kr, BK);
+  const int Kp = pad_to(Kr, ke_of(sc));
   sc->corner_Kp = Kp;
   for (int i = 0; i < 4; ++i) {
     if (!(mask >> i & 1u)) continue;
     sc->corner_src[i] = Q[i];
     for (int o = 0; o < 2; ++o) {
       if (!sc->cslices[i][o]) {
-        if (cudaMalloc(&sc->cslices[i][o], (size_t)3 * N * Kp * 2) != cudaSuccess) {
+        if (cudaMalloc(&sc->cslices[i][o], (size_t)ns_of(sc) * N * Kp * eb_of(sc)) != cudaSuccess) {
           cudaGetLastError();
           return sfail(sc, CTM_ENOMEM, "corner slice allocation failed");
         }
@@ -781,7 +861,8 @@ ctm_status split_apply(SplitCtx* sc, const void* Q, bool herm, const void* Zin, 
   int nchunks, BNc;
   chunking(Nr, &nchunks, &BNc);
   const int Np = nchunks * BNc;
-  ctm_status st = grow(sc, (void**)&sc->bbuf, &sc->bbuf_bytes, (size_t)3 * Np * Kp * 2);
+  ctm_status st = grow(sc, (void**)&sc->bbuf, &sc->bbuf_bytes,
+                       (size_t)ns_of(sc) * Np * Kp * eb_of(sc));
   if (st != CTM_OK) return st;
   st = prep_b(sc, Zin, k, OP_N, N, k, Kp, Np, sc->bbuf, s, launches);
   if (st != CTM_OK) return st;
@@ -793,15 +874,16 @@ ctm_status split_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, c
                       long ldb, int M, int N, int K, void* C, long ldc, cudaStream_t s,
                       long* launches) {
   const int Kr = sc->cx ? 2 * K : K;
-  const int Kp = pad_to(Kr, BK);
+  const int Kp = pad_to(Kr, ke_of(sc));
   const int Nr = sc->cx ? 2 * N : N;
   g_kr_real = Kr;
   int nchunks, BNc;
   chunking(Nr, &nchunks, &BNc);
   const int Np = nchunks * BNc;
-  ctm_status st = grow(sc, (void**)&sc->abuf, &sc->abuf_bytes, (size_t)3 * M * Kp * 2);
+  const size_t per = (size_t)ns_of(sc) * eb_of(sc);
+  ctm_status st = grow(sc, (void**)&sc->abuf, &sc->abuf_bytes, per * M * Kp);
   if (st != CTM_OK) return st;
-  st = grow(sc, (void**)&sc->bbuf, &sc->bbuf_bytes, (size_t)3 * Np * Kp * 2);
+  st = grow(sc, (void**)&sc->bbuf, &sc->bbuf_bytes, per * Np * Kp);
   if (st != CTM_OK) return st;
   st = prep_a(sc, A, lda, opA, M, K, Kp, sc->abuf, s, launches);
   if (st != CTM_OK) return st;

@@ -13,7 +13,10 @@ struct SplitCtx;
 // State for N x N corners and N x k blocks of real (cx = false) or complex
 // data; err is the owner's device error flag (bounded waits report there).
 // Buffers are allocated on first use.
-ctm_status split_create(SplitCtx** out, bool cx, int N, int k, int* err, cudaStream_t s);
+// tf32: 3xTF32 slices (two tf32 slices, three products, kind::tf32) instead
+// of bf16 x3 (three bf16 slices, six products, kind::f16).
+ctm_status split_create(SplitCtx** out, bool cx, bool tf32, int N, int k, int* err,
+                        cudaStream_t s);
 void split_destroy(SplitCtx* sc);
 
 // Slice the fp64 corners Q[i] (N x N) whose bit i is set in mask into bf16

@@ -120,3 +120,40 @@ def test_converged_split_large_D_matches_oracle(case):
     # measured: spectra 4.2e-7 / 2.8e-7, energies 4.9e-8 / 3.1e-8 (D = 6 / 8)
     assert es < TOL_SPLIT and ee < TOL_SPLIT_ENERGY
     ctx.ctm_free()
+
+
+@pytest.mark.parametrize("case", [
+    (2, 1, 2, 3, 10, 5, True, 1),        # N = 90 complex: ragged tiles (32-wide K rows)
+    (1, 1, 2, 4, 12, 5, False, 1),       # real, N = 192
+])
+def test_one_move_tf32_matches_fp64(case):
+    """3xTF32 split mode (two tf32 slices, three kind::tf32 products): one
+    move against the fp64 path; projector identity."""
+    a, _ = _ctx(case, pkg.CTM_PREC_FP64)
+    b, _ = _ctx(case, pkg.CTM_PREC_SPLIT_TF32)
+    a.ctm_move(0)
+    b.ctm_move(0)
+    err = np.abs(_spectra(a) - _spectra(b)).max()
+    print(f"tf32 one move {case[:5]}: spectra vs fp64 {err:.2e}")
+    assert err < 1e-5     # measured 2.8e-7 / 1.6e-7
+    Pl, PrH = b.ctm_get_projectors(0, 0, 0)
+    assert np.abs(PrH.conj().T @ Pl - np.eye(Pl.shape[1])).max() < 1e-9
+    a.ctm_free()
+    b.ctm_free()
+
+
+def test_converged_tf32_matches_oracle():
+    """3xTF32 at D = 6 (the fused absorption's D = 6 variant, lanes),
+    converged, against the FP64 oracle; the measured error is printed."""
+    ctx, ref = make_pair(2, 2, 2, 6, 8, 5, True, 1, decay=0.5, prec=pkg.CTM_PREC_SPLIT_TF32)
+    it, delta, _ = ctx.ctm_converge(1e-9, 150)
+    ref.converge(1e-11, 150)
+    spec = ref.spectra()
+    es = max(float(np.abs(ctx.ctm_spectrum(x, y, lab + 1) - spec[lab][y * 2 + x]).max())
+             for lab in range(4) for y in range(2) for x in range(2))
+    ee = max(abs(ctx.ctm_expect(HEIS, x, y, dr) - ref.expect2(HEIS, x, y, dr))
+             for y in range(2) for x in range(2) for dr in (0, 1))
+    print(f"tf32 D=6: spectra {es:.2e}, energies {ee:.2e}, delta {delta:.1e}, it {it}")
+    # measured: spectra 4.8e-7, energies 8.8e-8
+    assert es < TOL_SPLIT and ee < 2 * TOL_SPLIT_ENERGY
+    ctx.ctm_free()
