@@ -32,10 +32,12 @@ if ROOT not in sys.path:
 
 WORKLOAD = "cfg3_3x3_D6_chi144_c128"
 WARM_ITERS, WARM_ROUNDS = 2, 4
-# DRAM bytes (read + write) per launch of split_mma_kernel over the bf16
-# operand bytes of that launch, from one full-counter ncu capture of the
-# current kernel; None until the kernel has been captured since it changed
-TRAFFIC_PER_OPERAND_BYTE = None
+# DRAM bytes (read + write) per launch of split_mma_kernel<FmtBF16> over the
+# kernel's algorithmic bytes (all slices of both operands + the fp32 split-K
+# partials), from a one-pass ncu capture of a corner x block launch at
+# N = 5184, k = 149 (469.2 MB / 501.7 MB); only valid for the bf16 kernel as
+# captured, so it is set to None whenever that kernel changes
+TRAFFIC_PER_OPERAND_BYTE = 0.935
 SLICE_PRODUCTS = 6   # bf16 slice products per algorithmic product
 METRIC = "CTMRG moves/s & tensor TFLOP/s at D=6, chi=144"
 UNIT = "moves/s"
@@ -335,13 +337,17 @@ def run_ours(args, rank, world, local_rank):
         peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
         if args.prec == "tf32":
             peak = peak / 2.0   # tf32 kind at half the bf16 rate (nominal ratio)
-        traffic = (None if TRAFFIC_PER_OPERAND_BYTE is None
+        traffic = (None if TRAFFIC_PER_OPERAND_BYTE is None or args.prec != "split"
                    else round(TRAFFIC_PER_OPERAND_BYTE * mma_bytes / mma_n))
         roofline = {"bound": "tensor",
                     "kernel": "split_mma_kernel (tcgen05 %s, fp32 accum)"
                               % ("kind::f16 bf16" if args.prec == "split" else "kind::tf32"),
                     "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "traffic_basis": "bytes per launch: ncu dram read + write of one "
+                                     "corner x block launch (N = 5184, k = 149) over its "
+                                     "algorithmic bytes (0.935) x this run's algorithmic "
+                                     "bytes per launch",
                     "achieved_basis": "algorithmic flops (8 per complex multiply-add) per "
                                       "launch / CUDA-event duration on the launching stream",
                     "tensor_pipe_achieved": round(pipe, 2),

@@ -247,6 +247,23 @@ ctm_status ctm_corner(ctm_ctx* ctx, ctm_dir dir, int x, int y, int i, void* Q_ou
 ctm_status ctm_corner_apply(ctm_ctx* ctx, ctm_dir dir, int x, int y, int i, int herm,
                             const void* Z_in, void* Z_out);
 
+/* Correlation length from the converged environment (the paper reports xi
+ * with its states and extrapolates in it; here without the extrapolation):
+ * the leading eigenvalues of the transfer matrix of the boundary formed by
+ * the edges above and below one row, E[(a,d),(b,c)] = sum over u, u' of
+ * T1[a][b][u][u'] T3[c][d][u][u'], multiplied over the Lx sites of the row
+ * period (dir = 0, row = y) or, for dir = 1, over the Ly sites of column
+ * x = row (the edges T2, T4 beside it). nvals (2 .. 24) eigenvalues of
+ * largest modulus, sorted by descending modulus and divided by the modulus
+ * of the first, into lam_out (host, nvals (re, im) pairs); xi_out = -L /
+ * ln|lam_2 / lam_1| in lattice spacings (0 for a rank-one transfer
+ * matrix). Subspace iteration on the device with Rayleigh-Ritz; CTM_ENOCONV
+ * when the leading moduli do not settle (to 1e-13) within 2000
+ * applications. At finite chi this boundary estimate lies below the exact
+ * correlation length (the paper extrapolates it in chi). */
+ctm_status ctm_transfer_spectrum(ctm_ctx* ctx, int dir, int row, int nvals, double* lam_out,
+                                 double* xi_out);
+
 /* Subspace-iteration updates made and skipped (recycling policy of
  * opts.recycle_sin2) over all cuts since the context was created. */
 ctm_status ctm_si_stats(const ctm_ctx* ctx, long* updates, long* skipped);

@@ -617,3 +617,42 @@ class CTM:
         f = Frame(self.Lx, self.Ly, 0)
         i = f.site(x, y)
         return self._one_site(f, x, y, self.kets[i], self.bras[i])
+
+
+# ------------------------------------------------------ correlation length
+
+def transfer_matrix(ctm, direction=0, row=0):
+    """The dense edge transfer matrix of one row period (see
+    transfer_spectrum): prod over x of E_x[(a, d), (b, c)] =
+    sum_{u, u'} T1[a, b, u, u'] T3[c, d, u, u']."""
+    f = Frame(ctm.Lx, ctm.Ly, direction)
+    chi = ctm.chi
+    Etot = None
+    for x in range(f.Lx):
+        T1 = ctm._get(f, "T", 0, x, row)
+        T3 = ctm._get(f, "T", 2, x, row)
+        E = np.einsum("abuv,cduv->adbc", T1, T3).reshape(chi * chi, chi * chi)
+        Etot = E if Etot is None else Etot @ E
+    return Etot
+
+
+def transfer_spectrum(ctm, direction=0, row=0, nvals=4):
+    """Leading eigenvalues of the edge transfer matrix of one period of a row
+    (direction 0: along x, the row at frame-0 position y = row; direction 1:
+    along y, the column x = row, taken as a row of the frame turned once) and
+    the correlation length xi = -L / ln(|lam_2| / |lam_1|) in lattice
+    spacings (L sites per period). Reading of the paper's correlation length
+    from the converged environment: the transfer matrix of the boundary
+    formed by the edges above and below the row,
+    E[(a, d), (b, c)] = sum_{u, u'} T1[a, b, u, u'] T3[c, d, u, u']
+    (T1 runs left -> right, T3 right -> left), multiplied along the period.
+    Built as a dense chi^2 x chi^2 matrix: for small chi only.
+    Pinned by: the exact Ising correlation length above T_c, and D = 1
+    product states (rank-one transfer matrix, xi = 0)."""
+    f = Frame(ctm.Lx, ctm.Ly, direction)
+    lam = np.linalg.eigvals(transfer_matrix(ctm, direction, row))
+    lam = lam[np.argsort(-np.abs(lam), kind="stable")][:nvals]
+    lam = lam / np.abs(lam[0])
+    r = abs(lam[1]) if len(lam) > 1 else 0.0
+    xi = 0.0 if r == 0.0 else -f.Lx / np.log(r)
+    return lam, xi

@@ -90,6 +90,7 @@ def load():
         "ctm_corner": (I, [ctx_p, I, I, I, I, VP]),
         "ctm_corner_apply": (I, [ctx_p, I, I, I, I, I, VP, VP]),
         "ctm_si_stats": (I, [ctx_p, P(C.c_long), P(C.c_long)]),
+        "ctm_transfer_spectrum": (I, [ctx_p, I, I, I, P(D), P(D)]),
         "ctm_debug_fail_alloc": (None, [I]),
         "ctm_record": (I, [ctx_p, I]),
         "ctm_grad": (I, [ctx_p, VP, P(D), VP]),
@@ -299,6 +300,16 @@ class Context:
                                            C.byref(E), dA.ctypes.data, C.byref(it), C.byref(res))
         _check(self.lib, self.ptr, st, allow=(CTM_ENOCONV,))
         return E.value, dA, it.value, res.value
+
+    def ctm_transfer_spectrum(self, direction=0, row=0, nvals=4):
+        """(eigenvalues of largest modulus / |lambda_1|, correlation length) of
+        the edge transfer matrix of one row (direction 0) or column (1)."""
+        lam = np.empty(2 * nvals)
+        xi = C.c_double()
+        _check(self.lib, self.ptr, self.lib.ctm_transfer_spectrum(
+            self.ptr, int(direction), int(row), int(nvals),
+            lam.ctypes.data_as(C.POINTER(C.c_double)), C.byref(xi)))
+        return lam[0::2] + 1j * lam[1::2], xi.value
 
     def ctm_si_stats(self):
         u, sk = C.c_long(), C.c_long()

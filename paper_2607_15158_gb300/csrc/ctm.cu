@@ -1935,6 +1935,109 @@ ctm_status ctm_corner_apply(ctm_ctx* c, ctm_dir dir, int x, int y, int i, int he
   return CTM_OK;
 }
 
+ctm_status ctm_transfer_spectrum(ctm_ctx* c, int dir, int row, int nvals, double* lam_out,
+                                 double* xi_out) {
+  if (!c || !lam_out) return fail(c, CTM_EINVAL, "NULL argument");
+  if (dir < 0 || dir > 1) return fail(c, CTM_EINVAL, "dir must be 0 (along x) or 1 (along y)");
+  const int r = dir;
+  const int Lxf = (r & 1) ? c->Ly : c->Lx, Lyf = (r & 1) ? c->Lx : c->Ly;
+  if (row < 0 || row >= Lyf) return fail(c, CTM_EINVAL, "bad row");
+  const long chi = c->chi, Dk = c->Dk, Db = c->Db, n = chi * chi;
+  if (nvals < 2 || nvals > 24 || nvals > n)
+    return fail(c, CTM_EINVAL, "nvals must be in 2 .. min(24, chi^2)");
+  Guard gd(c);
+  use_lane(c, 0);
+  // subspace iteration with m vectors, Rayleigh-Ritz every 5 applications
+  const int m = (int)std::min<long>(n, std::max(nvals + 4, 8));
+  const size_t es = c->es, mark = c->scratch_off;
+  void* V = scratch_alloc(c, (size_t)n * m * es);
+  void* V2 = scratch_alloc(c, (size_t)n * m * es);
+  void* Ta = scratch_alloc(c, (size_t)n * m * es);
+  void* Tb = scratch_alloc(c, (size_t)n * m * es);
+  void* G = scratch_alloc(c, (size_t)m * m * es);
+  void* Li = scratch_alloc(c, (size_t)m * m * es);
+  void* H = scratch_alloc(c, (size_t)m * m * es);
+  double* ev = static_cast<double*>(scratch_alloc(c, 2 * 32 * sizeof(double)));
+  int* st = static_cast<int*>(scratch_alloc(c, 64 * sizeof(int)));
+  int* dead = st + 16;
+  void* Wb = scratch_alloc(c, (size_t)n * m * Dk * Db * es);
+  if (!V || !V2 || !Ta || !Tb || !G || !Li || !H || !ev || !st || !Wb)
+    return fail(c, CTM_ENOMEM, "scratch arena too small for the transfer vectors");
+  const int opH = c->cx ? OP_C : OP_T;
+  CTM_CUDA_OK(hash_fill((long)(n * m * (c->cx ? 2 : 1)), 7919, static_cast<double*>(V), c->stream,
+                        &c->launches));
+  // Y = E_{Lxf-1}^T ... E_0^T V, the row's edges T1 above and T3 below
+  // (the first contraction of each column reads its input into the
+  // pipeline buffer, so the last column may write over the input block)
+  auto apply = [&](void* X, void* Y) -> ctm_status {
+    void* in = X;
+    for (int x = 0; x < Lxf; ++x) {
+      void* out = (x == Lxf - 1) ? Y : (in == Ta ? Tb : Ta);
+      Tn W = tn(Wb, {chi, m, chi, Dk, Db});
+      CK(ein(c, "adm,abuv->dmbuv", tn(in, {chi, chi, m}), false,
+             tn(fT(c, r, 0, x, row), {chi, chi, Dk, Db}), false, W));
+      CK(ein(c, "dmbuv,cduv->bcm", W, false, tn(fT(c, r, 2, x, row), {chi, chi, Dk, Db}), false,
+             tn(out, {chi, chi, m})));
+      in = out;
+    }
+    return CTM_OK;
+  };
+  // orthonormal columns of X (n x m), twice: Gram, Cholesky, X L^-H
+  auto orth = [&](void* X) -> ctm_status {
+    for (int pass = 0; pass < 2; ++pass) {
+      CK(mm_small(c, opH, OP_N, m, m, n, X, m, X, m, G, m));
+      CTM_CUDA_OK(chol_inv(c->cx, m, n, false, G, Li, 1, dead, c->err, c->stream, &c->launches));
+      CK(mm_small(c, OP_N, opH, n, m, m, X, m, Li, m, V2, m));
+      CTM_CUDA_OK(repair_dead_columns(c->cx, n, m, V2, dead, 104729ull + pass, c->stream,
+                                      &c->launches));
+      CTM_CUDA_OK(cudaMemcpyAsync(X, V2, (size_t)n * m * es, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return CTM_OK;
+  };
+  CTM_CUDA_OK(cudaMemsetAsync(dead, 0, 16 * sizeof(int), c->stream));
+  CK(orth(V));
+  std::vector<double> h(2 * m), prev(2 * nvals, 0.0);
+  double ratio = 0.0;
+  bool conv = false;
+  const int max_apply = 2000;
+  for (int it = 1; it <= max_apply; ++it) {
+    CK(apply(V, V));
+    CK(orth(V));
+    if (it % 5) continue;
+    // Ritz values of the projected transfer matrix H = V^H E V
+    CK(apply(V, V2));
+    CK(mm_small(c, opH, OP_N, m, m, n, V, m, V2, m, H, m));
+    CTM_CUDA_OK(small_eig(c->cx, m, H, ev, st, c->stream, &c->launches));
+    int hst = 0;
+    CTM_CUDA_OK(cudaMemcpyAsync(h.data(), ev, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CTM_CUDA_OK(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(check_err(c));
+    if (hst < 0) return fail(c, CTM_ENOCONV, "small eigenproblem did not converge");
+    const double a0 = std::hypot(h[0], h[1]);
+    if (!(a0 > 0.0)) return fail(c, CTM_ENUMERIC, "zero transfer matrix");
+    double change = 0.0;
+    for (int i = 0; i < nvals; ++i) {
+      const double ai = std::hypot(h[2 * i], h[2 * i + 1]) / a0;
+      change = std::max(change, std::fabs(ai - prev[i]));
+      prev[i] = ai;
+    }
+    ratio = prev[1];
+    if (change < 1e-13) {
+      conv = true;
+      break;
+    }
+  }
+  const double a0 = std::hypot(h[0], h[1]);
+  for (int i = 0; i < nvals; ++i) {
+    lam_out[2 * i] = h[2 * i] / a0;
+    lam_out[2 * i + 1] = h[2 * i + 1] / a0;
+  }
+  if (xi_out) *xi_out = ratio > 0.0 ? -(double)Lxf / std::log(ratio) : 0.0;
+  c->scratch_off = mark;
+  if (!conv) return fail(c, CTM_ENOCONV, "transfer-matrix eigenvalues did not converge");
+  return CTM_OK;
+}
+
 ctm_status ctm_si_stats(const ctm_ctx* c, long* updates, long* skipped) {
   if (!c) return CTM_EINVAL;
   if (updates) *updates = c->n_updates;

@@ -176,6 +176,16 @@ cudaError_t spectra_delta(int c, int batch, double* snew, double* sold,
 cudaError_t mean_sin2(bool cx, int k, int c, const void* M, double* out, cudaStream_t s,
                       long* launches);
 
+// x[i] = uniform [-1, 1) pseudo-random numbers of a counter-based hash of
+// (seed, i) (n doubles).
+cudaError_t hash_fill(long n, uint64_t seed, double* x, cudaStream_t s, long* launches);
+
+// Eigenvalues of one m x m row-major matrix (m <= 32; real or complex), by
+// Hessenberg reduction and shifted QR on one thread, sorted by descending
+// modulus, into ev[2 m] (re, im); status[0] = QR iterations or -1.
+cudaError_t small_eig(bool cx, int m, const void* H, double* ev, int* status, cudaStream_t s,
+                      long* launches);
+
 // G += alpha * I for batch k x k matrices
 cudaError_t add_identity(bool cx, int k, void* G, double alpha, int batch,
                          cudaStream_t s, long* launches);

@@ -1000,3 +1000,71 @@ cudaError_t mean_sin2(bool cx, int k, int c, const void* M, double* out, cudaStr
 }
 
 }  // namespace ctm
+
+#include "small_eig.cuh"
+
+namespace ctm {
+namespace {
+
+// counter-based pseudo-random fill (splitmix64 of seed and index), uniform
+// in [-1, 1): a deterministic start block
+__global__ void hash_fill_kernel(long n, uint64_t seed, double* x) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)i * 0xBF58476D1CE4E5B9ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+// eigenvalues of one m x m (real or complex) row-major matrix, sorted by
+// descending modulus (stable), as (re, im) pairs; status[0] = iterations
+// or -1
+template <typename T>
+__global__ void small_eig_kernel(int m, const T* H, double* ev, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  zc A[32 * 32], e[32];
+  for (int i = 0; i < m * m; ++i) {
+    if constexpr (sizeof(T) == 16) A[i] = zmk(reinterpret_cast<const double2*>(H)[i].x,
+                                              reinterpret_cast<const double2*>(H)[i].y);
+    else A[i] = zmk(reinterpret_cast<const double*>(H)[i], 0.0);
+  }
+  const int it = small_eigvals(m, A, e);
+  for (int i = 1; i < m; ++i) {
+    const zc v = e[i];
+    const double a = zabs(v);
+    int j = i - 1;
+    while (j >= 0 && zabs(e[j]) < a) {
+      e[j + 1] = e[j];
+      --j;
+    }
+    e[j + 1] = v;
+  }
+  for (int i = 0; i < m; ++i) {
+    ev[2 * i] = e[i].re;
+    ev[2 * i + 1] = e[i].im;
+  }
+  status[0] = it;
+}
+
+}  // namespace
+
+cudaError_t hash_fill(long n, uint64_t seed, double* x, cudaStream_t s, long* launches) {
+  long b = (n + 255) / 256;
+  if (b > 152L * 8) b = 152L * 8;
+  hash_fill_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(n, seed, x);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t small_eig(bool cx, int m, const void* H, double* ev, int* status, cudaStream_t s,
+                      long* launches) {
+  if (m < 1 || m > 32) return cudaErrorInvalidValue;
+  if (cx) small_eig_kernel<cplx><<<1, 1, 0, s>>>(m, (const cplx*)H, ev, status);
+  else small_eig_kernel<double><<<1, 1, 0, s>>>(m, (const double*)H, ev, status);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace ctm

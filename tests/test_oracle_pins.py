@@ -478,3 +478,55 @@ def test_si_variants_reach_the_svd_fixed_point(variant):
         assert np.abs(ref.spectra()[lab][0] - ctm.spectra()[lab][0]).max() < 1e-10
     for direction in (0, 1):
         assert abs(ref.expect2(HEIS, 0, 0, direction) - ctm.expect2(HEIS, 0, 0, direction)) < 1e-10
+
+
+# ------------------------------------------------------ correlation length
+
+@pytest.mark.parametrize("beta", [0.30, 0.40])
+def test_transfer_matrix_with_a_row_of_sites_gives_onsager(beta):
+    """The edge transfer matrix of a converged Ising environment, with and
+    without the row of site tensors between its edges: the ratio of their
+    leading eigenvalues is the partition function per site, so its log is
+    Onsager's -beta f. Fixes the orientation of T1 and T3 in the transfer
+    matrix."""
+    chi = 16
+    ctm = _ising_ctm(beta, chi, "svd")
+    ctm.converge(1e-12, 800)
+    ET = ctmrg.transfer_matrix(ctm, 0, 0)
+    f = ctmrg.Frame(1, 1, 0)
+    t1 = ctm._get(f, "T", 0, 0, 0).reshape(chi, chi, -1)
+    t3 = ctm._get(f, "T", 2, 0, 0).reshape(chi, chi, -1)
+    a = exact.double_layer(ctm.kets[0], ctm.bras[0])          # [u, l, d, r]
+    Ef = np.einsum("abu,ulwr,cew->alebrc", t1, a, t3)
+    n = chi * chi * a.shape[1]
+    l_full = np.abs(np.linalg.eigvals(Ef.reshape(n, n))).max()
+    l_T = np.abs(np.linalg.eigvals(ET)).max()
+    assert abs(np.log(l_full / l_T) - ising.onsager_lnz(beta)) < 1e-10
+
+
+def test_product_state_transfer_matrix_has_rank_one():
+    """D = 1, environment built from the tensors (rank-one corners and
+    edges): the edges carry no correlations, the moves keep them rank one,
+    and the transfer matrix has one nonzero eigenvalue, xi = 0."""
+    A = S.product_state_tensors(2, 1, seed=4)
+    B = [a.conj() for a in A]
+    C, T = ctmrg.env_from_tensors(2, 1, A, B, 3)
+    ctm = ctmrg.CTM(2, 1, A, B, C, T, 3, method="svd")
+    for _ in range(3):
+        ctm.iteration()
+    for direction in (0, 1):
+        lam, xi = ctmrg.transfer_spectrum(ctm, direction, 0, 3)
+        assert np.abs(lam[1:]).max() < 1e-12 and xi == 0.0
+
+
+@pytest.mark.parametrize("beta", [0.30, 0.40])
+def test_ising_boundary_correlation_length_below_exact(beta):
+    """At finite chi the boundary estimate lies below the exact correlation
+    length of the disordered Ising model, 1 / (2 (K* - K)) with
+    tanh K* = exp(-2 K) (the paper extrapolates it in chi), within 10 %."""
+    ctm = _ising_ctm(beta, 16, "svd")
+    ctm.converge(1e-12, 800)
+    _, xi = ctmrg.transfer_spectrum(ctm, 0, 0, 2)
+    ks = -0.5 * np.log(np.tanh(beta))
+    xi_exact = 1.0 / (2.0 * (ks - beta))
+    assert 0.9 * xi_exact < xi < xi_exact
