@@ -115,6 +115,11 @@ typedef struct {
                              the initial random blocks (a randomized SVD per
                              move, End Matter: RSVD before SI on larger unit
                              cells) instead of the recycled bases */
+  int svd_presolve;       /* 1 = the small SVDs of rho (k <= 169 complex, 238
+                             real) first run the one-sided Jacobi in fp32,
+                             then the fp64 sweeps on rho V0 from V0 made
+                             unitary in fp64 (same result to fp64 rounding,
+                             fewer fp64 sweeps); 0 = fp64 sweeps only */
   void* stream;           /* cudaStream_t to run on, NULL = a private stream */
 } ctm_opts;
 
@@ -131,7 +136,7 @@ enum { CTM_INIT_RANDOM = 0, CTM_INIT_FROM_A = 1 };
  * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0,
  * svd_max_sweeps = 80, init_mode = CTM_INIT_RANDOM, recycle_sin2 = 0 (always
  * update), min_si_steps = 3, absorb_tc = 0, si_coupled = 0, warmup_rsvd = 0,
- * stream = NULL. */
+ * svd_presolve = 1, stream = NULL. */
 void ctm_default_opts(ctm_opts* opts);
 
 /* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz

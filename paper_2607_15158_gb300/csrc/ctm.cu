@@ -632,12 +632,64 @@ ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
   return CTM_OK;
 }
 
-// rho = u s v^H for the slots 0 .. n-1 in one cooperative launch.
+// Batched m x m products C[i] = alpha op(A[i]) B[i] in fp64 (A[i] at stride
+// sA elements, B and C contiguous).
+ctm_status mm_batched(ctm_ctx* c, int m, int opA, int n, const void* A, long sA, const void* B,
+                      void* Cm, double alpha) {
+  GemmDesc g;
+  g.opA = opA;
+  g.opB = OP_N;
+  g.M = m; g.N = m; g.K = m;
+  g.A = A; g.lda = m; g.strideA = sA;
+  g.B = B; g.ldb = m; g.strideB = (long)m * m;
+  g.C = Cm; g.ldc = m; g.strideC = (long)m * m;
+  g.alpha[0] = alpha;
+  g.batch = n;
+  return gemm(c, g);
+}
+
+// fp32 pre-solve of n m x m matrices A (stride sA): the one-sided Jacobi in
+// fp32 (jacobi32.cu) gives the right rotations V0, two Newton-Schulz steps
+// V <- V (3 I - V^H V) / 2 make them unitary in fp64 (each squares the
+// distance from unitarity: ~1e-6 -> ~1e-12 -> rounding), and B = A V0
+// (into c->jB) has columns that are already nearly orthogonal. The fp64
+// one-sided Jacobi of B from V0 is then the SVD of A.
+ctm_status svd_presolve(ctm_ctx* c, int m, int n, const void* A, long sA, const void** V0) {
+  CTM_CUDA_OK(jacobi32_presolve(c->cx, m, A, sA, c->jv0, n, 40, nullptr, c->stream,
+                                &c->launches));
+  void* V = c->jv0;
+  void* Vn = c->jv1;
+  const int opH = c->cx ? OP_C : OP_T;
+  const long mm = (long)m * m;
+  for (int it = 0; it < 2; ++it) {
+    CK(mm_batched(c, m, opH, n, V, mm, V, c->jT, -0.5));
+    CTM_CUDA_OK(add_identity(c->cx, m, c->jT, 1.5, n, c->stream, &c->launches));
+    CK(mm_batched(c, m, OP_N, n, V, mm, c->jT, Vn, 1.0));
+    std::swap(V, Vn);
+  }
+  CK(mm_batched(c, m, OP_N, n, A, sA, V, c->jB, 1.0));
+  *V0 = V;
+  return CTM_OK;
+}
+
+bool use_presolve(const ctm_ctx* c, int m) {
+  return c->opts.svd_presolve && jacobi32_supported(c->cx, m);
+}
+
+// rho = u s v^H for the slots 0 .. n-1 in one cooperative launch (after the
+// fp32 pre-solve with opts.svd_presolve).
 ctm_status si_small_svd(ctm_ctx* c, int n) {
   PhaseScope ps(c, PH_SMALL);
   const int k = c->k;
-  CTM_CUDA_OK(jacobi_svd_coop(c->cx, k, c->rho, (long)k * k, c->sv, c->u, c->v, true, c->jw, n,
-                              c->opts.svd_max_sweeps, c->err, c->num_sms, c->stream, &c->launches));
+  const void* A = c->rho;
+  const void* Vinit = nullptr;
+  if (use_presolve(c, k)) {
+    CK(svd_presolve(c, k, n, c->rho, (long)k * k, &Vinit));
+    A = c->jB;
+  }
+  CTM_CUDA_OK(jacobi_svd_coop(c->cx, k, A, (long)k * k, c->sv, c->u, c->v, true, c->jw, n,
+                              c->opts.svd_max_sweeps, c->err, c->num_sms, c->stream, &c->launches,
+                              Vinit));
   return CTM_OK;
 }
 
@@ -925,7 +977,15 @@ ctm_status move_impl(ctm_ctx* c, int r) {
 ctm_status corner_spectra(ctm_ctx* c, double* out) {
   PhaseScope ps(c, PH_SPECTRA);
   // unnormalised singular values of all 4 S corners, [label][site][chi]
-  CTM_CUDA_OK(jacobi_svd_coop(c->cx, c->chi, c->C, (long)elems_C(c), out, nullptr, nullptr,
+  const void* A = c->C;
+  long sA = (long)elems_C(c);
+  if (use_presolve(c, c->chi)) {
+    const void* V0 = nullptr;
+    CK(svd_presolve(c, c->chi, 4 * (int)c->S, c->C, sA, &V0));
+    A = c->jB;
+    sA = (long)c->chi * c->chi;
+  }
+  CTM_CUDA_OK(jacobi_svd_coop(c->cx, c->chi, A, sA, out, nullptr, nullptr,
                               false, c->jw, 4 * c->S, c->opts.svd_max_sweeps, c->err, c->num_sms, c->stream,
                               &c->launches));
   return CTM_OK;
@@ -1081,12 +1141,13 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       c->opts.warmup_rounds < 0 || c->opts.svd_max_sweeps < 1 || c->opts.min_si_steps < 0 ||
       c->opts.prec < CTM_PREC_FP64 || c->opts.prec > CTM_PREC_SPLIT_TF32 ||
       !(c->opts.recycle_sin2 >= 0.0) ||
-      (c->opts.init_mode != CTM_INIT_RANDOM && c->opts.init_mode != CTM_INIT_FROM_A)) {
+      (c->opts.init_mode != CTM_INIT_RANDOM && c->opts.init_mode != CTM_INIT_FROM_A) ||
+      (c->opts.svd_presolve != 0 && c->opts.svd_presolve != 1)) {
     delete c;
     g_cur = nullptr;
     return fail(nullptr, CTM_EINVAL,
                 "p, si_rounds, warm-up counts and min_si_steps must be >= 0, svd_max_sweeps >= 1, "
-                "recycle_sin2 >= 0, init_mode 0 or 1");
+                "recycle_sin2 >= 0, init_mode and svd_presolve 0 or 1");
   }
   c->N = chi * Dk * Db;
   c->k = std::min(chi + c->opts.p, c->N);
@@ -1153,6 +1214,13 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
   AL(c->rho, Lmax * k * k * es);
   AL(c->u, Lmax * k * k * es);
   AL(c->v, Lmax * k * k * es);
+  {
+    const size_t jn = std::max(Lmax * k * k, 4 * S * (size_t)chi * chi) * es;
+    AL(c->jv0, jn);
+    AL(c->jv1, jn);
+    AL(c->jT, jn);
+    AL(c->jB, jn);
+  }
   AL(c->jw, std::max(jacobi_coop_work_bytes(cx, (int)k, Lmax),
                      jacobi_coop_work_bytes(cx, chi, 4 * (int)S)));
   AL(c->ph, std::max(k, (size_t)chi) * es);
@@ -1452,6 +1520,7 @@ void ctm_default_opts(ctm_opts* o) {
   o->absorb_tc = 0;
   o->si_coupled = 0;
   o->warmup_rsvd = 0;
+  o->svd_presolve = 1;
   o->stream = nullptr;
 }
 
@@ -1522,6 +1591,7 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
   b += 2 * Lmax * N * chi * es + 2 * S * N * chi * es;   // Pl, PrH, last*
   b += 6 * N * k * es + 2 * k * k * es;            // Z, Xn, Wn, G, Linv
   b += 2 * Lmax * N * k * es + 3 * Lmax * k * k * es;    // ZR, ZL, rho, u, v
+  b += 4 * std::max(Lmax * k * k, 4 * S * (size_t)chi * chi) * es;   // pre-solve
   b += std::max(jacobi_coop_work_bytes(cx, (int)k, (int)Lmax),
                 jacobi_coop_work_bytes(cx, chi, 4 * (int)S));
   b += (std::max(k, (size_t)chi) + 2 * k * chi) * es;

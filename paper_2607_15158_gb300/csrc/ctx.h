@@ -83,6 +83,10 @@ struct ctm_ctx {
   void* rho = nullptr;       // [Lmax][k k]
   void* u = nullptr;         // [Lmax][k k]
   void* v = nullptr;
+  void* jv0 = nullptr;       // fp32 pre-solve of the small SVDs: V0 (two buffers),
+  void* jv1 = nullptr;       // Newton-Schulz temporary and A V0, each
+  void* jT = nullptr;        // max(Lmax k^2, 4 S chi^2) elements
+  void* jB = nullptr;
   void* jw = nullptr;        // Jacobi work, max(2 Lmax k^2, 8 S chi^2) elements
   void* ph = nullptr;
   void* Vs = nullptr;        // k x chi

@@ -35,8 +35,10 @@ struct JacobiArgs {
   double* s_out;
   void* U;
   void* V;
+  const void* Vinit;     // row-major k x k per matrix (V starts here), or null (identity)
   void* work;            // per matrix: 2 k^2 elements (A and V, column-major)
-  double* off;           // per matrix: 2 sweep slots (bits of a double)
+  double* off;           // per matrix: 2 sweep slots (largest rotated ratio
+                         // |gamma| / sqrt(alpha beta) of the sweep) and a check slot
   double* norms;         // per matrix: k
   unsigned* ver;         // per matrix: k column versions (rounds applied)
   unsigned* bar;         // [count, generation, abort]
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
   T* wv = wa + (size_t)k * k;
   double* nsq = a.norms + (size_t)b * k;
   const T* Ab = static_cast<const T*>(a.A) + (size_t)b * a.strideA;
+  const T* Vi = a.Vinit ? static_cast<const T*>(a.Vinit) + (size_t)b * k * k : nullptr;
   const T one = [] {
     if constexpr (sizeof(T) == 8) return T(1.0);
     else return make_double2(1.0, 0.0);
@@ -177,13 +180,15 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
   for (long idx = (long)g * JT + threadIdx.x; idx < (long)k * k; idx += (long)G * JT) {
     const int r = (int)(idx / k), c = (int)(idx % k);
     stcg(wa + (size_t)c * k + r, Ab[idx]);
-    if (a.want_uv) stcg(wv + (size_t)c * k + r, (r == c) ? one : zero_of(T()));
+    if (a.want_uv)
+      stcg(wv + (size_t)c * k + r, Vi ? Vi[idx] : ((r == c) ? one : zero_of(T())));
   }
   unsigned* ver = a.ver + (size_t)b * k;
   for (int c = g * JT + threadIdx.x; c < k; c += G * JT) ver[c] = 0u;
   if (g == 0 && threadIdx.x == 0) {
-    a.off[2 * b] = 0.0;
-    a.off[2 * b + 1] = 0.0;
+    a.off[3 * b] = 0.0;
+    a.off[3 * b + 1] = 0.0;
+    a.off[3 * b + 2] = 0.0;
   }
   if (!grid_barrier(a.bar, nblocks, a.err)) return;
   const double tol = fmax(1.0, (double)k) * DBL_EPSILON;
@@ -203,8 +208,14 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
     if (!grid_barrier(a.bar, nblocks, a.err)) return;
     // every block read the previous sweep's flag before this barrier: clear
     // the slot of the next sweep
-    if (g == 0 && threadIdx.x == 0) a.off[2 * b + ((sweep + 1) & 1)] = 0.0;
-    double* offb = a.off + 2 * b + (sweep & 1);   // set to 1 when a pair rotates
+    if (g == 0 && threadIdx.x == 0) {
+      a.off[3 * b + ((sweep + 1) & 1)] = 0.0;
+      a.off[3 * b + 2] = 0.0;
+    }
+    // the largest ratio |gamma| / sqrt(alpha beta) of the pairs rotated in
+    // this sweep (non-negative doubles order like their bit patterns)
+    unsigned long long* offb =
+        reinterpret_cast<unsigned long long*>(a.off + 3 * b + (sweep & 1));
     // rounds without grid barriers: a pair waits only for the two pairs of
     // the previous round that wrote its columns (column versions), so the
     // rotations are the same as with a barrier per round
@@ -250,7 +261,9 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
           const double nrm = sqrt(al) * sqrt(be);
           // rotate when |gamma| > tol sqrt(alpha beta)
           if (gm > tol * nrm && gm != 0.0) {
-            if (lane == 0) __stcg(offb, 1.0);   // this sweep rotated
+            if (lane == 0)   // this sweep rotated
+              atomicMax(offb, (unsigned long long)__double_as_longlong(
+                                  nrm > 0.0 ? fmin(gm / nrm, 1.0) : 1.0));
             const double zeta = (be - al) / (2.0 * gm);
             const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
             const double c = 1.0 / hypot(1.0, tt), s = c * tt;
@@ -302,8 +315,64 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
     if (!grid_barrier(a.bar, nblocks, a.err)) return;
     // convergence of the whole batch: every block reads every flag
     bool all = true;
-    for (int bb = 0; bb < a.batch; ++bb)
-      all = all && (__ldcg(a.off + 2 * bb + (sweep & 1)) <= tol);
+    double mxr = 0.0;
+    for (int bb = 0; bb < a.batch; ++bb) {
+      const double r = __ldcg(a.off + 3 * bb + (sweep & 1));
+      all = all && (r <= tol);
+      mxr = fmax(mxr, r);
+    }
+    if (!all && mxr < 1e-6 && sweep + 1 < a.max_sweeps) {
+      // quadratic regime: the next sweep most likely rotates nothing. Its
+      // decision is taken here at once, from every pair's exact ratio on the
+      // current columns (the dot products such a sweep would compute before
+      // any rotation), in parallel instead of round by round
+      for (int c = gw; c < k; c += nw) {
+        double acc = 0.0;
+        for (int r = lane; r < k; r += 32) acc += absq(ldcg(wa + (size_t)c * k + r));
+        acc = warp_sum(acc);
+        if (lane == 0) __stcg(nsq + c, acc);
+      }
+      if (!grid_barrier(a.bar, nblocks, a.err)) return;
+      double* chk = a.off + 3 * b + 2;
+      // fold f holds the columns f and k - 2 - f: k - 1 pairs (p, q > p) each
+      for (int f = gw; 2 * f <= k - 2; f += nw) {
+        for (int side = 0; side < 2; ++side) {
+          const int p = side == 0 ? f : k - 2 - f;
+          if (side == 1 && p == f) break;
+          T xr[R];
+#pragma unroll
+          for (int e = 0; e < R; ++e) {
+            const int r = lane + 32 * e;
+            xr[e] = r < k ? ldcg(wa + (size_t)p * k + r) : zero_of(T());
+          }
+          const double np_ = __ldcg(nsq + p);
+          bool bad = false;
+          for (int q = p + 1; q < k && !bad; ++q) {
+            const T* aq = wa + (size_t)q * k;
+            T ga = zero_of(T());
+#pragma unroll
+            for (int e = 0; e < R; ++e) {
+              const int r = lane + 32 * e;
+              if (r < k) fmacv(ga, xr[e], ldcg(aq + r));
+            }
+            ga = warp_sum(ga);
+            bad = absq(ga) > tol * tol * np_ * __ldcg(nsq + q) && absq(ga) != 0.0;
+          }
+          if (bad) {
+            if (lane == 0) __stcg(chk, 1.0);
+            break;
+          }
+        }
+      }
+      if (!grid_barrier(a.bar, nblocks, a.err)) return;
+      bool pass = true;
+      for (int bb = 0; bb < a.batch; ++bb) pass = pass && __ldcg(a.off + 3 * bb + 2) == 0.0;
+      if (pass) {
+        converged = true;
+        ++sweep;
+        break;
+      }
+    }
     if (all) {
       converged = true;
       ++sweep;
@@ -601,13 +670,14 @@ cudaError_t chol_inv_coop(bool cx, int k, long n, bool shift, bool scale, void* 
 
 size_t jacobi_coop_work_bytes(bool cx, int k, int batch) {
   const size_t es = cx ? 16 : 8;
-  return (size_t)batch * 2 * k * k * es + (size_t)batch * (2 + k) * sizeof(double) +
+  return (size_t)batch * 2 * k * k * es + (size_t)batch * (3 + k) * sizeof(double) +
          (size_t)batch * k * sizeof(unsigned) + 16 + 65 * sizeof(unsigned);
 }
 
 cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double* sv, void* U,
                             void* V, bool want_uv, void* work, int batch, int max_sweeps,
-                            int* err, int max_blocks, cudaStream_t s, long* launches) {
+                            int* err, int max_blocks, cudaStream_t s, long* launches,
+                            const void* Vinit) {
   const size_t es = cx ? 16 : 8;
   const int kk = k + (k & 1);
   const int npairs = kk / 2;
@@ -646,8 +716,9 @@ cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double*
   char* w = static_cast<char*>(work);
   a.work = w;
   w += (size_t)batch * 2 * k * k * es;
+  a.Vinit = want_uv ? Vinit : nullptr;
   a.off = reinterpret_cast<double*>(w);
-  w += (size_t)batch * 2 * sizeof(double);
+  w += (size_t)batch * 3 * sizeof(double);
   a.norms = reinterpret_cast<double*>(w);
   w += (size_t)batch * k * sizeof(double);
   a.ver = reinterpret_cast<unsigned*>(w);

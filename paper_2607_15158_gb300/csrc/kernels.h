@@ -127,10 +127,26 @@ cudaError_t jacobi_svd(bool cx, int k, const void* A, long strideA,
 
 // The same SVD with each matrix spread over several blocks of one
 // cooperative grid (jacobi.cu); max_blocks caps the grid (SM count). work:
-// jacobi_coop_work_bytes(cx, k, batch).
+// jacobi_coop_work_bytes(cx, k, batch). With Vinit (row-major k x k per
+// matrix, unitary) the accumulated V starts from Vinit instead of the
+// identity: the SVD of A Vinit then returns V = Vinit J, the right singular
+// vectors of A (used after the fp32 pre-solve, jacobi32_presolve). Vinit may
+// alias V and A may alias U (both are read before anything is written).
 cudaError_t jacobi_svd_coop(bool cx, int k, const void* A, long strideA, double* s, void* U,
                             void* V, bool want_uv, void* work, int batch, int max_sweeps,
-                            int* err, int max_blocks, cudaStream_t s_, long* launches);
+                            int* err, int max_blocks, cudaStream_t s_, long* launches,
+                            const void* Vinit = nullptr);
+
+// ------------------------------------------------------------ jacobi32.cu
+// fp32 one-sided Jacobi of a batch of k x k matrices (fp64 in, row-major,
+// stride strideA elements) on clusters of two CTAs, to the fp32 threshold or
+// max_sweeps: V0 receives the accumulated right rotations in fp64 (row-major
+// k x k per matrix; unitary to ~1e-6), sweeps (optional) the sweeps used.
+// Supported when jacobi32_supported(cx, k) (A and V each fit one CTA's
+// shared memory in fp32: k <= 169 complex, 238 real).
+bool jacobi32_supported(bool cx, int k);
+cudaError_t jacobi32_presolve(bool cx, int k, const void* A, long strideA, void* V0, int batch,
+                              int max_sweeps, int* sweeps, cudaStream_t s, long* launches);
 size_t jacobi_coop_work_bytes(bool cx, int k, int batch);
 
 // chol_inv on a cooperative grid (blocked, jacobi.cu); with scale the Gram

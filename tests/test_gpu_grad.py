@@ -166,3 +166,43 @@ def test_gradient_at_the_differentiation_shape():
     print(f"cfg5 shape, two moves: E {E:.12f} vs {float(e.detach()):.12f}, "
           f"gradient device vs oracle {err:.2e}, |g| {np.abs(g).max():.2e}")
     assert abs(E - float(e.detach())) < 1e-9 * max(1.0, abs(E)) and err < 1e-6
+
+
+def test_autograd_function_matches_the_reverse_pass():
+    """paper_2607_15158_gb300.autograd.ctm_energy: torch.autograd through the
+    library's forward and its hand-written backward gives exactly the
+    gradient of ctm_grad on the same inputs, scaled by the chain rule, and
+    central differences of its forward."""
+    from paper_2607_15158_gb300.autograd import ctm_energy
+
+    Lx, Ly, D, chi, p, iters = 2, 1, 2, 6, 4, 2
+    A, C, T, X0, W0 = _inputs(Lx, Ly, D, chi, p, 0.3)
+    opts = pkg.ctm_default_opts(p=p, warmup_iters=1, warmup_rounds=3)
+    At = torch.tensor(np.stack(A), dtype=torch.float64, requires_grad=True)
+    E = ctm_energy(At, HEIS, Lx, Ly, chi, iters, opts=opts, env=(C, T), rangefinders=(X0, W0))
+    (3.0 * E).backward()
+    ctx = _ctx(Lx, Ly, D, chi, p, A, C, T, X0, W0, warmup_iters=1, warmup_rounds=3)
+    ctx.ctm_record(True)
+    for _ in range(iters):
+        for r in range(4):
+            ctx.ctm_move(r)
+    E_ref, dA = ctx.ctm_grad(HEIS)
+    ctx.ctm_free()
+    assert abs(float(E) - E_ref) < 1e-13 * max(1.0, abs(E_ref))
+    g = At.grad.numpy()
+    assert np.abs(g - 3.0 * dA.reshape(g.shape)).max() <= 1e-14 * np.abs(dA).max()
+    rng = np.random.default_rng(6)
+    h = 1e-7
+    for _ in range(3):
+        V = torch.tensor(rng.standard_normal(At.shape))
+
+        def e_at(s):
+            with torch.no_grad():
+                return float(ctm_energy(At.detach() + s * V, HEIS, Lx, Ly, chi, iters, opts=opts,
+                                        env=(C, T), rangefinders=(X0, W0)))
+
+        c1 = (e_at(h) - e_at(-h)) / (2 * h)
+        c2 = (e_at(h / 2) - e_at(-h / 2)) / h
+        fd = (4 * c2 - c1) / 3
+        an = float((At.grad * V).sum()) / 3.0
+        assert abs(fd - an) < 1e-5 * max(1.0, abs(fd)), (fd, an)

@@ -321,3 +321,34 @@ def test_si_variants_match_oracle(variant):
     assert ok and d_ref < 1e-11
     _compare(ctx, ref)
     ctx.ctm_free()
+
+
+@pytest.mark.parametrize("case", [
+    (2, 2, 2, 3, 24, 5, True, 1),     # k = 29, four cuts per column batch
+    (1, 1, 2, 4, 64, 5, True, 1),     # k = 69
+    (2, 1, 2, 3, 30, 5, False, 1),    # real, k = 35
+])
+def test_fp32_presolve_matches_oracle_and_fp64_sweeps(case):
+    """Small SVD with the fp32 pre-solve (default) against the oracle and
+    against the fp64 sweeps alone (svd_presolve = 0) on the same inputs: the
+    first iteration agrees to the transient bar (1e-8), the converged
+    environments to 1e-10."""
+    Lx, Ly, d, D, chi, p, cplx, rounds = case
+    ctx, ref = make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, decay=0.7)
+    ctx0, _ = make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, decay=0.7, svd_presolve=0)
+    for c in (ctx, ctx0):
+        for r in range(4):
+            c.ctm_move(r)
+    ref.iteration()
+    _compare(ctx, ref, energies=False, tol=1e-8)
+    for lab in range(4):
+        for y in range(Ly):
+            for x in range(Lx):
+                s1, s0 = ctx.ctm_spectrum(x, y, lab + 1), ctx0.ctm_spectrum(x, y, lab + 1)
+                assert np.abs(s1 - s0).max() < 1e-8
+    _, _, ok = ctx.ctm_converge(1e-11, 300)
+    _, d_ref = ref.converge(1e-11, 300)
+    assert ok and d_ref < 1e-11
+    _compare(ctx, ref)
+    ctx.ctm_free()
+    ctx0.ctm_free()
