@@ -29,9 +29,7 @@ namespace {
 namespace cg = cooperative_groups;
 
 constexpr int J32T = 1024;   // threads per CTA (32 warps)
-// rows per lane held in registers: k <= 32 R (complex 192, real 256)
-template <bool CX>
-__host__ __device__ constexpr int j32r() { return CX ? 6 : 8; }
+constexpr int J32G = J32T / 8;   // 8-lane groups per CTA (one column pair each)
 
 struct J32Args {
   int k, max_sweeps;
@@ -95,9 +93,31 @@ struct F32<false> {
   }
 };
 
-__device__ __forceinline__ float wsum(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// V <- V J for the rotations of round t (CTA 1): group gi takes pair gi
+template <bool CX>
+__device__ __forceinline__ void apply_round(typename F32<CX>::T* M, const float4* prm, int k,
+                                            int kk, int m, int npairs, int t, int gi, int l8) {
+  typedef F32<CX> E;
+  typedef typename E::T T;
+  for (int pr = gi; pr < npairs; pr += J32G) {
+    int p = player32(pr, t, m), q = player32(kk - 1 - pr, t, m);
+    if (p > q) {
+      const int tmp = p;
+      p = q;
+      q = tmp;
+    }
+    const float4 rp = prm[pr];
+    if (q >= k || rp.y == 0.f) continue;
+    T* x = M + (size_t)p * k;
+    T* y = M + (size_t)q * k;
+    const float2 e = make_float2(rp.z, rp.w);
+    for (int r = l8; r < k; r += 8) {
+      T xv = x[r], yv = y[r];
+      E::rot(xv, yv, rp.x, rp.y, e);
+      x[r] = xv;
+      y[r] = yv;
+    }
+  }
 }
 
 template <bool CX>
@@ -114,10 +134,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
   T* M = reinterpret_cast<T*>(smem);   // A (rank 0) or V (rank 1), column c at M[c k]
   const size_t mbytes = ((size_t)k * k * sizeof(T) + 15) & ~(size_t)15;
   float4* prm = reinterpret_cast<float4*>(smem + mbytes);   // [2][npairs] (c, s, e)
+  float* nsq = reinterpret_cast<float*>(prm + 2 * npairs);   // [k] squared column norms
   __shared__ int rotated, stop;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = J32T / 32;
-  const void* Ab = static_cast<const char*>(a.A) + (size_t)b * a.strideA * (CX ? 16 : 8);
   __shared__ unsigned long long amax;   // bits of max |a_ij| (non-negative doubles order as integers)
+  const int lane = threadIdx.x & 31;
+  // groups of 8 lanes, one column pair each: the 4 groups of a warp share its
+  // instruction stream (scalar rotation math, reductions)
+  const int gi = threadIdx.x >> 3, l8 = threadIdx.x & 7;
+  const unsigned m8 = 0xffu << (lane & ~7);   // the lanes of this group (shuffle mask)
+  const void* Ab = static_cast<const char*>(a.A) + (size_t)b * a.strideA * (CX ? 16 : 8);
   if (threadIdx.x == 0) {
     rotated = 0;
     stop = 0;
@@ -157,9 +182,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
   int sweep = 0;
   long g = 0;   // rounds done (all sweeps)
   for (; sweep < a.max_sweeps; ++sweep) {
+    if (rank == 0) {
+      // exact squared norms at the start of the sweep, updated by
+      // alpha' = alpha - t |gamma|, beta' = beta + t |gamma| within it
+      for (int c = gi; c < k; c += J32G) {
+        const T* x = M + (size_t)c * k;
+        float acc = 0.f;
+        for (int r = l8; r < k; r += 8) acc += E::nrm2(x[r]);
+        acc += __shfl_xor_sync(m8, acc, 4);
+        acc += __shfl_xor_sync(m8, acc, 2);
+        acc += __shfl_xor_sync(m8, acc, 1);
+        if (l8 == 0) nsq[c] = acc;
+      }
+      __syncthreads();
+    }
     for (int t = 0; t < m; ++t, ++g) {
       if (rank == 0) {
-        for (int pr = wp; pr < npairs; pr += nw) {
+        for (int pr = gi; pr < npairs; pr += J32G) {
           int p = player32(pr, t, m), q = player32(kk - 1 - pr, t, m);
           if (p > q) {
             const int tmp = p;
@@ -170,68 +209,43 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
           if (q < k) {
             T* x = M + (size_t)p * k;
             T* y = M + (size_t)q * k;
-            constexpr int J32R = j32r<CX>();
-            T xr[J32R], yr[J32R];
-            float al = 0.f, be = 0.f;
             float2 ga = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int e = 0; e < J32R; ++e) {
-              const int r = lane + 32 * e;
-              if (r < k) {
-                xr[e] = x[r];
-                yr[e] = y[r];
-                al += E::nrm2(xr[e]);
-                be += E::nrm2(yr[e]);
-                E::dotc(ga, xr[e], yr[e]);
-              }
+            for (int r = l8; r < k; r += 8) E::dotc(ga, x[r], y[r]);
+            ga.x += __shfl_xor_sync(m8, ga.x, 4);
+            ga.x += __shfl_xor_sync(m8, ga.x, 2);
+            ga.x += __shfl_xor_sync(m8, ga.x, 1);
+            if (CX) {
+              ga.y += __shfl_xor_sync(m8, ga.y, 4);
+              ga.y += __shfl_xor_sync(m8, ga.y, 2);
+              ga.y += __shfl_xor_sync(m8, ga.y, 1);
             }
-            al = wsum(al);
-            be = wsum(be);
-            ga.x = wsum(ga.x);
-            if (CX) ga.y = wsum(ga.y);
+            const float al = nsq[p], be = nsq[q];
             const float gm = sqrtf(ga.x * ga.x + ga.y * ga.y);
-            if (gm > tol * sqrtf(al) * sqrtf(be) && gm > 0.f) {
+            if (gm > tol * sqrtf(fmaxf(al, 0.f)) * sqrtf(fmaxf(be, 0.f)) && gm > 0.f) {
               const float zeta = (be - al) / (2.f * gm);
               const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
               const float c = 1.f / sqrtf(1.f + tt * tt), s = c * tt;
               const float2 e = make_float2(ga.x / gm, -ga.y / gm);   // conj(gamma) / |gamma|
-#pragma unroll
-              for (int q2 = 0; q2 < J32R; ++q2) {
-                const int r = lane + 32 * q2;
-                if (r < k) {
-                  E::rot(xr[q2], yr[q2], c, s, e);
-                  x[r] = xr[q2];
-                  y[r] = yr[q2];
-                }
+              for (int r = l8; r < k; r += 8) {
+                T xv = x[r], yv = y[r];
+                E::rot(xv, yv, c, s, e);
+                x[r] = xv;
+                y[r] = yv;
               }
               rp = make_float4(c, s, e.x, e.y);
-              if (lane == 0) rotated = 1;
+              if (l8 == 0) {
+                nsq[p] = al - tt * gm;
+                nsq[q] = be + tt * gm;
+                rotated = 1;
+              }
             }
           }
-          if (lane == 0) prm1[(g & 1) * npairs + pr] = rp;
+          if (l8 == 0) prm1[(g & 1) * npairs + pr] = rp;
         }
       } else if (g > 0) {
         // V <- V J for the rotations of the previous round
         const long g1 = g - 1;
-        const int t1 = (int)(g1 % m);
-        for (int pr = wp; pr < npairs; pr += nw) {
-          int p = player32(pr, t1, m), q = player32(kk - 1 - pr, t1, m);
-          if (p > q) {
-            const int tmp = p;
-            p = q;
-            q = tmp;
-          }
-          const float4 rp = prm[(g1 & 1) * npairs + pr];
-          if (q >= k || rp.y == 0.f) continue;
-          T* x = M + (size_t)p * k;
-          T* y = M + (size_t)q * k;
-          for (int r = lane; r < k; r += 32) {
-            T xv = x[r], yv = y[r];
-            E::rot(xv, yv, rp.x, rp.y, make_float2(rp.z, rp.w));
-            x[r] = xv;
-            y[r] = yv;
-          }
-        }
+        apply_round<CX>(M, prm + (g1 & 1) * npairs, k, kk, m, npairs, (int)(g1 % m), gi, l8);
       }
       cl.sync();
     }
@@ -251,25 +265,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
   if (rank == 1) {
     if (g > 0) {
       const long g1 = g - 1;
-      const int t1 = (int)(g1 % m);
-      for (int pr = wp; pr < npairs; pr += nw) {
-        int p = player32(pr, t1, m), q = player32(kk - 1 - pr, t1, m);
-        if (p > q) {
-          const int tmp = p;
-          p = q;
-          q = tmp;
-        }
-        const float4 rp = prm[(g1 & 1) * npairs + pr];
-        if (q >= k || rp.y == 0.f) continue;
-        T* x = M + (size_t)p * k;
-        T* y = M + (size_t)q * k;
-        for (int r = lane; r < k; r += 32) {
-          T xv = x[r], yv = y[r];
-          E::rot(xv, yv, rp.x, rp.y, make_float2(rp.z, rp.w));
-          x[r] = xv;
-          y[r] = yv;
-        }
-      }
+      apply_round<CX>(M, prm + (g1 & 1) * npairs, k, kk, m, npairs, (int)(g1 % m), gi, l8);
     }
     __syncthreads();
     for (long idx = threadIdx.x; idx < (long)k * k; idx += J32T) {
@@ -284,14 +280,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
 
 size_t j32_smem(bool cx, int k) {
   const int npairs = (k + (k & 1)) / 2;
-  return (((size_t)k * k * (cx ? 8 : 4) + 15) & ~(size_t)15) + 2 * (size_t)npairs * 16;
+  return (((size_t)k * k * (cx ? 8 : 4) + 15) & ~(size_t)15) + 2 * (size_t)npairs * 16 +
+         (size_t)k * 4;
 }
 
 }  // namespace
 
 bool jacobi32_supported(bool cx, int k) {
-  return k >= 2 && k <= 32 * (cx ? j32r<true>() : j32r<false>()) &&
-         j32_smem(cx, k) <= (size_t)227 * 1024;
+  return k >= 2 && (k + 1) / 2 <= J32G && j32_smem(cx, k) <= (size_t)227 * 1024;
 }
 
 cudaError_t jacobi32_presolve(bool cx, int k, const void* A, long strideA, void* V0, int batch,
