@@ -55,6 +55,10 @@ def parse():
                     help="projectors: subspace iteration or the standard truncated SVD")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-svd-presolve", action="store_true",
+                    help="small SVDs in fp64 sweeps only (no fp32 one-sided Jacobi first)")
+    ap.add_argument("--no-fp64-tc", action="store_true",
+                    help="split modes: Grams, rho and projectors as fp64 GEMMs on the CUDA cores")
     ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the plain-FP64 and standard-SVD comparison timings and the "
                          "split-error measurement")
@@ -260,6 +264,8 @@ def run_ours(args, rank, world, local_rank):
     method = pkg.CTM_PROJ_SVD if args.method == "svd" else pkg.CTM_PROJ_SI
     opts = pkg.ctm_default_opts(p=p, si_rounds=w["si_rounds"], warmup_iters=WARM_ITERS,
                                 warmup_rounds=WARM_ROUNDS, prec=prec, method=method,
+                                svd_presolve=0 if args.no_svd_presolve else 1,
+                                fp64_tc=0 if args.no_fp64_tc else 1,
                                 stream=stream.cuda_stream)
     ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx, opts=opts)
     ctx.ctm_set_env(Cs, Ts)
@@ -386,6 +392,11 @@ def run_ours(args, rank, world, local_rank):
                                  "fp64": "fp64"}[args.prec],
                    "projectors": "subspace iteration" if args.method == "si"
                    else "standard truncated SVD (dense gesvd)",
+                   "small_svd": "fp64 one-sided Jacobi" if args.no_svd_presolve
+                   else "fp32 one-sided Jacobi pre-solve, then fp64 sweeps",
+                   "fp64_products": "fp64 GEMMs (CUDA cores)" if (args.no_fp64_tc or args.prec == "fp64")
+                   else "Grams, rho, projectors: exact 8-digit fixed-point bf16 products on the "
+                        "tensor cores (fp64-accurate)",
                    "step": "1 iteration = 4 moves + corner-spectrum scalar",
                    "l2": "working set >> L2 (no flush)", "replicas": world},
         "algorithmic_tflops": round(algo_flops_move * value / 1e12, 3),

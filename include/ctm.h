@@ -115,6 +115,11 @@ typedef struct {
                              the initial random blocks (a randomized SVD per
                              move, End Matter: RSVD before SI on larger unit
                              cells) instead of the recycled bases */
+  int fp64_tc;           /* split contexts: 1 = the products that stay fp64
+                             (CholeskyQR Grams, rho, the projectors
+                             Z v s^-1/2) run as exact fixed-point digit
+                             products on the tensor cores (ctm_gemm_fp64tc),
+                             0 = fp64 GEMMs on the CUDA cores */
   int svd_presolve;       /* 1 = the small SVDs of rho (k <= 169 complex, 238
                              real) first run the one-sided Jacobi in fp32,
                              then the fp64 sweeps on rho V0 from V0 made
@@ -136,7 +141,7 @@ enum { CTM_INIT_RANDOM = 0, CTM_INIT_FROM_A = 1 };
  * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0,
  * svd_max_sweeps = 80, init_mode = CTM_INIT_RANDOM, recycle_sin2 = 0 (always
  * update), min_si_steps = 3, absorb_tc = 0, si_coupled = 0, warmup_rsvd = 0,
- * svd_presolve = 1, stream = NULL. */
+ * fp64_tc = 1, svd_presolve = 1, stream = NULL. */
 void ctm_default_opts(ctm_opts* opts);
 
 /* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz
@@ -272,6 +277,21 @@ ctm_status ctm_transfer_spectrum(ctm_ctx* ctx, int dir, int row, int nvals, doub
 /* Subspace-iteration updates made and skipped (recycling policy of
  * opts.recycle_sin2) over all cuts since the context was created. */
 ctm_status ctm_si_stats(const ctm_ctx* ctx, long* updates, long* skipped);
+
+/* C = op(A) B (M x N, inner K) to fp64 accuracy on the bf16 tensor cores,
+ * as split contexts run their fp64 products (opts.fp64_tc): every row of
+ * op(A) and column of B is written as a 56-bit fixed-point number against
+ * the exponent of its largest entry and cut into eight 7-bit digits (an
+ * error-free splitting after Ozaki et al.); the digit products of weight
+ * <= 7 are exact in the fp32 tensor-memory accumulators and are combined as
+ * unevaluated fp32 pairs. The error is about 2^-48 of |op(A)| |B|
+ * (elementwise products of the row and column maxima), the order of an fp64
+ * product. Host buffers, row-major: A is M x K (opA = 0) or K x M (opA = 1
+ * transpose, 2 conjugate transpose), B is K x N, C is M x N; leading
+ * dimensions lda, ldb, ldc; dtype CTM_F64 or CTM_C128. Verification entry
+ * point of the library's product (allocates, synchronises). */
+ctm_status ctm_gemm_fp64tc(ctm_dtype dtype, int opA, const void* A, long lda, const void* B,
+                           long ldb, int M, int N, int K, void* C, long ldc);
 
 /* ------------------------------------------------------- differentiation
  * Gradient of the energy E = sum over all sites and both bond directions of

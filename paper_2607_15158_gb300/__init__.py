@@ -35,7 +35,7 @@ class ctm_opts(C.Structure):
                 ("seed", C.c_uint64), ("svd_max_sweeps", C.c_int), ("init_mode", C.c_int),
                 ("recycle_sin2", C.c_double), ("min_si_steps", C.c_int),
                 ("absorb_tc", C.c_int), ("si_coupled", C.c_int), ("warmup_rsvd", C.c_int),
-                ("svd_presolve", C.c_int), ("stream", C.c_void_p)]
+                ("fp64_tc", C.c_int), ("svd_presolve", C.c_int), ("stream", C.c_void_p)]
 
 
 class ctm_solve_spec(C.Structure):
@@ -436,6 +436,24 @@ def ctm_svdvals_noalloc(A_dev, k, dtype, s_dev, stream=0):
     if st != CTM_OK:
         raise CTMError(st, (lib.ctm_noalloc_last_error() or b"").decode())
     return st
+
+
+def ctm_gemm_fp64tc(A, B, opA=0):
+    """op(A) @ B through the library's fp64-accurate tensor-core product
+    (host arrays; opA 0 = A, 1 = A^T, 2 = A^H)."""
+    lib = load()
+    cx = np.iscomplexobj(A) or np.iscomplexobj(B)
+    a = _host(A, cx)
+    b = _host(B, cx)
+    M = a.shape[1] if opA else a.shape[0]
+    K = a.shape[0] if opA else a.shape[1]
+    if b.shape[0] != K:
+        raise ValueError("inner dimensions differ")
+    N = b.shape[1]
+    c = np.empty((M, N), np.complex128 if cx else np.float64)
+    _check(lib, None, lib.ctm_gemm_fp64tc(CTM_C128 if cx else CTM_F64, int(opA), a.ctypes.data,
+                                          a.shape[1], b.ctypes.data, N, M, N, K, c.ctypes.data, N))
+    return c
 
 
 def ctm_debug_fail_alloc(after):

@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libctm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ctm.cu", "permute.cu", "gemm64.cu", "linalg.cu", "jacobi.cu", "split_gemm.cu",
-           "noalloc.cu", "cholqr_mixed.cu", "jacobi32.cu",
+           "noalloc.cu", "cholqr_mixed.cu", "jacobi32.cu", "chol_cluster.cu",
            "absorb.cu", "svd_proj.cu", "serve.cu", "grad.cu"]
 
 

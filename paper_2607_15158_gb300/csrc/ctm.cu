@@ -214,6 +214,22 @@ ctm_status gemm(ctm_ctx* c, GemmDesc& g) {
   return CTM_OK;
 }
 
+// Products whose result must stay fp64-accurate (CholeskyQR Grams, rho, the
+// projectors): in split contexts with opts.fp64_tc as exact fixed-point
+// digit products on the tensor cores (oz_gemm), else the fp64 GEMM.
+constexpr double FP64TC_MIN_MNK = 1 << 16;
+ctm_status gemm_exact(ctm_ctx* c, GemmDesc& g) {
+  if (c->split && c->opts.fp64_tc && g.batch == 1 && g.opB == OP_N && g.alpha[0] == 1.0 &&
+      g.alpha[1] == 0.0 && g.beta[0] == 0.0 && g.beta[1] == 0.0 &&
+      (double)g.M * g.N * g.K >= FP64TC_MIN_MNK) {
+    const ctm_status st = oz_gemm(c->split, g.opA, g.A, g.lda, g.opB, g.B, g.ldb, (int)g.M,
+                                  (int)g.N, (int)g.K, g.C, g.ldc, c->stream, &c->launches);
+    if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+    return CTM_OK;
+  }
+  return gemm(c, g);
+}
+
 // The A / conj(A) absorption runs as one fused kernel (fp32 arithmetic in
 // split contexts) where it fits, unless a split context asks for it on the
 // tensor cores (opts.absorb_tc): then it is two split-precision GEMMs with
@@ -448,7 +464,7 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
       g.B = Zm; g.ldb = c->k;
       g.C = c->G; g.ldc = c->k;
       g.lower_only = true;
-      CK(gemm(c, g));
+      CK(gemm_exact(c, g));
       CTM_CUDA_OK(orth_correction(c->cx, c->k, c->G, c->Linv, c->stream, &c->launches));
       const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, OP_N, c->Linv, c->k, c->N, c->k,
                                        c->k, tmp, c->k, c->stream, &c->launches);
@@ -467,23 +483,37 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
       g.B = Zm; g.ldb = c->k;
       g.C = c->G; g.ldc = c->k;
       g.lower_only = smem_chol;
-      CK(gemm(c, g));
+      CK(gemm_exact(c, g));
     }
     int* dead = c->dead;   // every pass finds and refills dependent columns
+    // the k x k factor on a cluster of eight SMs where it fits (chol_cluster.cu),
+    // else on one SM (the fp64 pipe of one SM bounds it)
+    const bool cl_chol = chol_cluster_supported(c->cx, c->k);
     if (split && smem_chol && pass == 1) {
       // second pass of a split context: the block is already conditioned by
       // the shifted pass, so Q = Z D^-1 L^-H runs on the tensor cores (the
       // explicit k x k inverse replaces the fp64 row solve; its ~1e-7 error
       // is removed by the correction pass that follows)
-      CTM_CUDA_OK(chol_factor_inv(c->cx, c->k, c->N, false, true, c->G, c->Linv, c->dsc, dead,
-                                  c->G, c->err, c->stream, &c->launches));
+      if (cl_chol)
+        CTM_CUDA_OK(chol_cluster(c->cx, c->k, c->N, false, true, c->G, c->Linv, c->dsc, dead,
+                                 c->G, c->err, c->stream, &c->launches));
+      else
+        CTM_CUDA_OK(chol_factor_inv(c->cx, c->k, c->N, false, true, c->G, c->Linv, c->dsc, dead,
+                                    c->G, c->err, c->stream, &c->launches));
       const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, OP_N, c->G, c->k, c->N, c->k,
                                        c->k, tmp, c->k, c->stream, &c->launches);
       if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
     } else if (smem_chol) {
       // L = chol(D^-1 G D^-1) in shared memory, Q = Z D^-1 L^-H row by row
-      CTM_CUDA_OK(chol_qr_pass(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
-                               Zm, tmp, c->err, c->num_sms, c->stream, &c->launches));
+      if (cl_chol) {
+        CTM_CUDA_OK(chol_cluster(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
+                                 nullptr, c->err, c->stream, &c->launches));
+        CTM_CUDA_OK(trsm_rows(c->cx, c->k, c->N, c->Linv, c->dsc, Zm, tmp, c->num_sms, c->stream,
+                              &c->launches));
+      } else {
+        CTM_CUDA_OK(chol_qr_pass(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
+                                 Zm, tmp, c->err, c->num_sms, c->stream, &c->launches));
+      }
     } else {
       CTM_CUDA_OK(chol_inv_coop(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, 1, dead,
                                 c->chol_work, c->err, c->num_sms, c->stream, &c->launches));
@@ -523,6 +553,17 @@ ctm_status mm_small(ctm_ctx* c, int opA, int opB, long M, long Nn, long K, const
   g.B = B; g.ldb = ldb;
   g.C = Cm; g.ldc = ldc;
   return gemm(c, g);
+}
+
+ctm_status mm_exact(ctm_ctx* c, int opA, int opB, long M, long Nn, long K, const void* A,
+                    long lda, const void* B, long ldb, void* Cm, long ldc) {
+  GemmDesc g;
+  g.opA = opA; g.opB = opB;
+  g.M = M; g.N = Nn; g.K = K;
+  g.A = A; g.lda = lda;
+  g.B = B; g.ldb = ldb;
+  g.C = Cm; g.ldc = ldc;
+  return gemm_exact(c, g);
 }
 
 // SI projectors of one cut (paper "QR-based projector", steps 1-4), first
@@ -628,7 +669,7 @@ ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
   const int k = c->k;
   const int opH = c->cx ? OP_C : OP_T;
   PhaseScope ps(c, PH_SMALL);
-  CK(mm_small(c, opH, OP_N, k, k, c->N, ZL, k, ZR, k, at(c->rho, (size_t)y * k * k, c), k));
+  CK(mm_exact(c, opH, OP_N, k, k, c->N, ZL, k, ZR, k, at(c->rho, (size_t)y * k * k, c), k));
   return CTM_OK;
 }
 
@@ -744,8 +785,8 @@ ctm_status si_finish(ctm_ctx* c, int r, int cut, int y, void* Pl, void* PrH) {
                                 c->stream, &c->launches));
   CTM_CUDA_OK(scale_by_inv_sqrt(c->cx, k, chi, u, sv, c->opts.svd_rel_cutoff, c->Us,
                                 c->stream, &c->launches));
-  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, ZR, k, c->Vs, chi, Pl, chi));
-  CK(mm_small(c, OP_N, OP_N, c->N, chi, k, ZL, k, c->Us, chi, PrH, chi));
+  CK(mm_exact(c, OP_N, OP_N, c->N, chi, k, ZR, k, c->Vs, chi, Pl, chi));
+  CK(mm_exact(c, OP_N, OP_N, c->N, chi, k, ZL, k, c->Us, chi, PrH, chi));
   CTM_CUDA_OK(cudaMemcpyAsync(X, c->Xn, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
   CTM_CUDA_OK(cudaMemcpyAsync(W, c->Wn, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
   return CTM_OK;
@@ -1142,12 +1183,13 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       c->opts.prec < CTM_PREC_FP64 || c->opts.prec > CTM_PREC_SPLIT_TF32 ||
       !(c->opts.recycle_sin2 >= 0.0) ||
       (c->opts.init_mode != CTM_INIT_RANDOM && c->opts.init_mode != CTM_INIT_FROM_A) ||
-      (c->opts.svd_presolve != 0 && c->opts.svd_presolve != 1)) {
+      (c->opts.svd_presolve != 0 && c->opts.svd_presolve != 1) ||
+      (c->opts.fp64_tc != 0 && c->opts.fp64_tc != 1)) {
     delete c;
     g_cur = nullptr;
     return fail(nullptr, CTM_EINVAL,
                 "p, si_rounds, warm-up counts and min_si_steps must be >= 0, svd_max_sweeps >= 1, "
-                "recycle_sin2 >= 0, init_mode and svd_presolve 0 or 1");
+                "recycle_sin2 >= 0, init_mode, fp64_tc and svd_presolve 0 or 1");
   }
   c->N = chi * Dk * Db;
   c->k = std::min(chi + c->opts.p, c->N);
@@ -1520,6 +1562,7 @@ void ctm_default_opts(ctm_opts* o) {
   o->absorb_tc = 0;
   o->si_coupled = 0;
   o->warmup_rsvd = 0;
+  o->fp64_tc = 1;
   o->svd_presolve = 1;
   o->stream = nullptr;
 }
@@ -2113,6 +2156,51 @@ ctm_status ctm_si_stats(const ctm_ctx* c, long* updates, long* skipped) {
   if (updates) *updates = c->n_updates;
   if (skipped) *skipped = c->n_skipped;
   return CTM_OK;
+}
+
+ctm_status ctm_gemm_fp64tc(ctm_dtype dtype, int opA, const void* A, long lda, const void* B,
+                           long ldb, int M, int N, int K, void* C, long ldc) {
+  if ((dtype != CTM_F64 && dtype != CTM_C128) || opA < OP_N || opA > OP_C || !A || !B || !C ||
+      M < 1 || N < 1 || K < 1 || ldb < N || ldc < N || lda < (opA == OP_N ? K : M))
+    return fail(nullptr, CTM_EINVAL, "bad arguments of ctm_gemm_fp64tc");
+  const bool cx = dtype == CTM_C128;
+  const size_t es = cx ? 16 : 8;
+  const size_t na = (size_t)(opA == OP_N ? M : K) * lda, nb = (size_t)K * ldb, nc = (size_t)M * ldc;
+  void *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  int* err = nullptr;
+  SplitCtx* sc = nullptr;
+  cudaStream_t s = nullptr;
+  ctm_status st = CTM_OK;
+  auto done = [&](ctm_status r, const char* m) {
+    if (sc) split_destroy(sc);
+    if (dA) cudaFree(dA);
+    if (dB) cudaFree(dB);
+    if (dC) cudaFree(dC);
+    if (err) cudaFree(err);
+    if (s) cudaStreamDestroy(s);
+    return r == CTM_OK ? CTM_OK : fail(nullptr, r, m);
+  };
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&dA, na * es) != cudaSuccess || cudaMalloc(&dB, nb * es) != cudaSuccess ||
+      cudaMalloc(&dC, nc * es) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return done(CTM_ENOMEM, "device allocation failed");
+  }
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemcpyAsync(dA, A, na * es, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dB, B, nb * es, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return done(CTM_ECUDA, "host to device copy failed");
+  st = split_create(&sc, cx, false, 1, 1, err, s);
+  if (st != CTM_OK) return done(st, "tensor-core product unavailable");
+  st = oz_gemm(sc, opA, dA, lda, OP_N, dB, ldb, M, N, K, dC, ldc, s, nullptr);
+  if (st != CTM_OK) return done(st, split_last_error(sc));
+  int herr = 0;
+  if (cudaMemcpyAsync(C, dC, nc * es, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return done(CTM_ECUDA, "device to host copy failed");
+  if (herr) return done(CTM_ECUDA, "a bounded wait of the tensor-core product gave up");
+  return done(CTM_OK, "");
 }
 
 void ctm_debug_fail_alloc(int after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }

@@ -134,7 +134,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
   T* M = reinterpret_cast<T*>(smem);   // A (rank 0) or V (rank 1), column c at M[c k]
   const size_t mbytes = ((size_t)k * k * sizeof(T) + 15) & ~(size_t)15;
   float4* prm = reinterpret_cast<float4*>(smem + mbytes);   // [2][npairs] (c, s, e)
-  float* nsq = reinterpret_cast<float*>(prm + 2 * npairs);   // [k] squared column norms
   __shared__ int rotated, stop;
   __shared__ unsigned long long amax;   // bits of max |a_ij| (non-negative doubles order as integers)
   const int lane = threadIdx.x & 31;
@@ -182,20 +181,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
   int sweep = 0;
   long g = 0;   // rounds done (all sweeps)
   for (; sweep < a.max_sweeps; ++sweep) {
-    if (rank == 0) {
-      // exact squared norms at the start of the sweep, updated by
-      // alpha' = alpha - t |gamma|, beta' = beta + t |gamma| within it
-      for (int c = gi; c < k; c += J32G) {
-        const T* x = M + (size_t)c * k;
-        float acc = 0.f;
-        for (int r = l8; r < k; r += 8) acc += E::nrm2(x[r]);
-        acc += __shfl_xor_sync(m8, acc, 4);
-        acc += __shfl_xor_sync(m8, acc, 2);
-        acc += __shfl_xor_sync(m8, acc, 1);
-        if (l8 == 0) nsq[c] = acc;
-      }
-      __syncthreads();
-    }
     for (int t = 0; t < m; ++t, ++g) {
       if (rank == 0) {
         for (int pr = gi; pr < npairs; pr += J32G) {
@@ -209,19 +194,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
           if (q < k) {
             T* x = M + (size_t)p * k;
             T* y = M + (size_t)q * k;
+            // exact squared norms and the overlap of the pair, every round
             float2 ga = make_float2(0.f, 0.f);
-            for (int r = l8; r < k; r += 8) E::dotc(ga, x[r], y[r]);
-            ga.x += __shfl_xor_sync(m8, ga.x, 4);
-            ga.x += __shfl_xor_sync(m8, ga.x, 2);
-            ga.x += __shfl_xor_sync(m8, ga.x, 1);
-            if (CX) {
-              ga.y += __shfl_xor_sync(m8, ga.y, 4);
-              ga.y += __shfl_xor_sync(m8, ga.y, 2);
-              ga.y += __shfl_xor_sync(m8, ga.y, 1);
+            float al = 0.f, be = 0.f;
+            for (int r = l8; r < k; r += 8) {
+              const T xv = x[r], yv = y[r];
+              al += E::nrm2(xv);
+              be += E::nrm2(yv);
+              E::dotc(ga, xv, yv);
             }
-            const float al = nsq[p], be = nsq[q];
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+              al += __shfl_xor_sync(m8, al, o);
+              be += __shfl_xor_sync(m8, be, o);
+              ga.x += __shfl_xor_sync(m8, ga.x, o);
+              if (CX) ga.y += __shfl_xor_sync(m8, ga.y, o);
+            }
             const float gm = sqrtf(ga.x * ga.x + ga.y * ga.y);
-            if (gm > tol * sqrtf(fmaxf(al, 0.f)) * sqrtf(fmaxf(be, 0.f)) && gm > 0.f) {
+            if (gm > tol * sqrtf(al) * sqrtf(be) && gm > 0.f) {
               const float zeta = (be - al) / (2.f * gm);
               const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
               const float c = 1.f / sqrtf(1.f + tt * tt), s = c * tt;
@@ -233,11 +223,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
                 y[r] = yv;
               }
               rp = make_float4(c, s, e.x, e.y);
-              if (l8 == 0) {
-                nsq[p] = al - tt * gm;
-                nsq[q] = be + tt * gm;
-                rotated = 1;
-              }
+              if (l8 == 0) rotated = 1;
             }
           }
           if (l8 == 0) prm1[(g & 1) * npairs + pr] = rp;
@@ -280,8 +266,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
 
 size_t j32_smem(bool cx, int k) {
   const int npairs = (k + (k & 1)) / 2;
-  return (((size_t)k * k * (cx ? 8 : 4) + 15) & ~(size_t)15) + 2 * (size_t)npairs * 16 +
-         (size_t)k * 4;
+  return (((size_t)k * k * (cx ? 8 : 4) + 15) & ~(size_t)15) + 2 * (size_t)npairs * 16;
 }
 
 }  // namespace

@@ -106,6 +106,22 @@ cudaError_t chol_factor_inv(bool cx, int k, long rows, bool shift, bool scale, c
                             void* L, double* dsc, int* dead, void* W, int* err, cudaStream_t s,
                             long* launches);
 
+// The row solve of chol_qr_pass alone: Q = Z D^-1 L^-H for a factor L and
+// scales D already computed (chol_cluster).
+cudaError_t trsm_rows(bool cx, int k, long rows, const void* L, const double* dsc, const void* Z,
+                      void* Q, int num_sms, cudaStream_t s, long* launches);
+
+// ------------------------------------------------------- chol_cluster.cu
+// The factor of chol_qr_pass / chol_factor_inv (same options and outputs:
+// L, dsc, dead; with W != null also W = D^-1 L^-H) computed by a cluster of
+// eight CTAs (rows dealt cyclically, one cluster barrier per column). W may
+// alias G. Supported when chol_cluster_supported(cx, k) (the packed factor
+// fits one CTA's shared memory: k <= 156 complex, 225 real).
+bool chol_cluster_supported(bool cx, int k);
+cudaError_t chol_cluster(bool cx, int k, long rows, bool shift, bool scale, const void* G,
+                         void* L, double* dsc, int* dead, void* W, int* err, cudaStream_t s,
+                         long* launches);
+
 // Overwrite the dead columns of a rows x k matrix with deterministic
 // pseudo-random entries (a counter-based hash of seed, column, row).
 cudaError_t repair_dead_columns(bool cx, long rows, int k, void* Q, const int* dead,

@@ -805,6 +805,24 @@ cudaError_t chol_qr_pass(bool cx, int k, long rows, bool shift, bool scale, cons
   return cudaGetLastError();
 }
 
+cudaError_t trsm_rows(bool cx, int k, long rows, const void* L, const double* dsc, const void* Z,
+                      void* Q, int num_sms, cudaStream_t s, long* launches) {
+  const size_t shm = chol_smem_bytes(cx, k);
+  static size_t configured_trsm[2][5] = {{0}};
+  {
+    const cudaError_t e = cx ? trsm_set_smem<cplx>(configured_trsm[1], shm)
+                             : trsm_set_smem<double>(configured_trsm[0], shm);
+    if (e != cudaSuccess) return e;
+  }
+  long g = (rows + 31) / 32;
+  if (g > num_sms) g = num_sms;
+  if (g < 1) g = 1;
+  if (cx) CTM_TRSM_LAUNCH(cplx);
+  else CTM_TRSM_LAUNCH(double);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
 // W = D^-1 L^-H from the factor of chol_smem_kernel: block c solves the
 // column c of X = L^-1 by forward substitution (one warp, x in shared
 // memory) and writes row c of W, W[c][i] = conj(X[i][c]) / D_c (i >= c).

@@ -363,6 +363,12 @@ __device__ __forceinline__ void put_slices(T* out, long slice, long o, const T* 
 }
 
 
+__device__ __forceinline__ void put_digits(__nv_bfloat16* out, long slice, long o,
+                                           const __nv_bfloat16* d, bool neg) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) out[i * slice + o] = neg ? __hneg(d[i]) : d[i];
+}
+
 // A slices: out[s][m][kr], kr < K: Re op(A)(m, kr); K <= kr < 2K: Im
 // (complex); zero up to Kp. A 32 x 32 shared tile of op(A) is read along A's
 // contiguous axis (rows for op N / R, columns for op T / C) and each element
@@ -530,6 +536,444 @@ __global__ void reduce_kernel(const float* part, int nks, int M, int N, int Np, 
   }
 }
 
+// ------------------------------------------- fp64-accurate products (Ozaki)
+// C = op(A) op(B) to fp64 accuracy on the bf16 tensor cores, for the
+// products whose result must be fp64-accurate in split contexts (the Gram
+// matrices of the CholeskyQR passes, rho = Z_L^H Z_R and the projectors
+// Z_R v s^-1/2): an error-free splitting of the operands in the manner of
+// Ozaki et al. (2012), "Error-free transformations of matrix multiplication
+// by using fast routines of matrix multiplication and its applications".
+//   * every row m of op(A) (every column n of op(B)) gets the exponent E of
+//     its largest entry, |x| < 2^E; each entry is written as the 56-bit
+//     fixed-point integer F = trunc(|x| 2^(56 - E)) and cut into eight 7-bit
+//     digits d_0 .. d_7 (most significant first), stored with the sign of x
+//     as bf16 (integers below 128 are exact in bf16);
+//   * a digit product d_s e_t is an integer below 2^14, exact in fp32; the
+//     products of equal weight w = s + t (w <= 7; the dropped ones are below
+//     2^-53 of the row / column maxima) are accumulated in tensor memory,
+//     one fp32 accumulator per weight, over at most OZ_KB_DRAIN K blocks of
+//     64: at most 8 * 128 * 127^2 < 2^24, so every partial sum is an exact
+//     integer;
+//   * each accumulator is drained after OZ_KB_DRAIN K blocks and added,
+//     scaled by 2^-7w, into an unevaluated fp32 pair (TwoSum) per output;
+//     the pairs of the K splits are summed the same way and the result is
+//     hi + lo scaled by 2^(E_m + E_n - 14), to about 2^-48 relative.
+// The operand digits stage through shared memory in three quarter stages
+// per K block (digits 0-3 of A with 0-3 of B, 0-3 with 4-7, 4-7 with 0-3),
+// which cover every product of weight <= 7.
+constexpr int OZ_NS = 8;          // digits per operand
+constexpr int OZ_BITS = 7;        // bits per digit
+constexpr int OZ_BN = 64;         // output columns per CTA (one accumulator width)
+constexpr int OZ_KB_DRAIN = 2;    // K blocks per exact accumulation
+constexpr int OZ_Q_BYTES = 4 * A_SLICE_BYTES + 4 * OZ_BN * KROW;   // 96 KB per quarter stage
+
+struct OzParams {
+  int M;          // output rows (real-embedded)
+  int Np;         // padded output columns
+  int kb_total;   // K blocks of 64
+  int kb_split;   // K blocks per CTA
+  float2* part;   // [nks][M][Np] (hi, lo)
+  int* err;
+};
+
+__global__ void __launch_bounds__(192, 1)
+    oz_mma_kernel(const __grid_constant__ CUtensorMap tmA,
+                  const __grid_constant__ CUtensorMap tmB, OzParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * OZ_Q_BYTES);
+  // full[2], empty[2], chunk done, drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 cdone = smem_u32(bars + 2 * STAGES), drained = smem_u32(bars + 2 * STAGES + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m_tile = blockIdx.x, chunk = blockIdx.y, ks = blockIdx.z;
+  const int kb0 = ks * p.kb_split;
+  const int nkb = min(p.kb_split, p.kb_total - kb0);
+  const int nchunks = (nkb + OZ_KB_DRAIN - 1) / OZ_KB_DRAIN;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(cdone, 1);
+    mbar_init(drained, 4);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  __shared__ int failed;
+  if (threadIdx.x == 0) failed = 0;
+  __syncthreads();
+  // quarter q: A digits from a_off, B digits from b_off
+  const int q_a[3] = {0, 0, 4}, q_b[3] = {0, 4, 0};
+
+  if (nkb > 0 && warp == 0 && lane == 0) {
+    // TMA producer: three quarter stages per K block
+    for (int kb = 0; kb < nkb; ++kb) {
+      for (int q = 0; q < 3; ++q) {
+        const int it = 3 * kb + q, s = it % STAGES;
+        if (it >= STAGES && !mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, p.err)) {
+          failed = 1;
+          break;
+        }
+        const uint32_t full = full0 + 8 * s;
+        mbar_expect_tx(full, OZ_Q_BYTES);
+        uint8_t* st = smem + s * OZ_Q_BYTES;
+        const int kx = (kb0 + kb) * BK;
+        for (int i = 0; i < 4; ++i)
+          tma_load_3d(smem_u32(st + i * A_SLICE_BYTES), &tmA, kx, m_tile * BM, q_a[q] + i, full);
+        for (int i = 0; i < 4; ++i)
+          tma_load_3d(smem_u32(st + 4 * A_SLICE_BYTES + i * OZ_BN * KROW), &tmB, kx,
+                      chunk * OZ_BN, q_b[q] + i, full);
+      }
+      if (failed) break;
+    }
+  } else if (nkb > 0 && warp == 1 && lane == 0) {
+    // MMA issuer: the products of weight <= 7 of each quarter, into the
+    // accumulator of their weight; a chunk of OZ_KB_DRAIN K blocks starts
+    // each accumulator afresh once the epilogue has drained the last one
+    const uint32_t idesc = idesc_bf16(BM, OZ_BN);
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      if (c > 0) {
+        if (!mbar_wait(drained, (c - 1) & 1, p.err)) {
+          ok = false;
+          failed = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+      unsigned used = 0;   // accumulators written in this chunk
+      const int kbe = min(nkb, (c + 1) * OZ_KB_DRAIN);
+      for (int kb = c * OZ_KB_DRAIN; kb < kbe && ok; ++kb) {
+        for (int q = 0; q < 3; ++q) {
+          const int it = 3 * kb + q, s = it % STAGES;
+          if (!mbar_wait(full0 + 8 * s, (it / STAGES) & 1, p.err)) {
+            ok = false;
+            failed = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + s * OZ_Q_BYTES);
+          for (int i = 0; i < 4; ++i) {
+            for (int j = 0; j < 4; ++j) {
+              const int w = q_a[q] + i + q_b[q] + j;
+              if (w >= OZ_NS) continue;
+              const uint32_t a0 = st + i * A_SLICE_BYTES;
+              const uint32_t b0 = st + 4 * A_SLICE_BYTES + j * OZ_BN * KROW;
+              const uint32_t d = tmem + (uint32_t)(w * OZ_BN);
+              const bool fresh = !(used >> w & 1u);
+              used |= 1u << w;
+              for (int kk = 0; kk < KROW / 32; ++kk)
+                mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                         (fresh && kk == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+      }
+      if (ok) mma_commit(cdone);
+    }
+  } else if (warp >= 2 && nkb > 0) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its quarter)
+    const int quarter = warp & 3;
+    float hi[OZ_BN], lo[OZ_BN];
+#pragma unroll
+    for (int i = 0; i < OZ_BN; ++i) hi[i] = lo[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      if (!mbar_wait(cdone, c & 1, p.err)) {
+        ok = false;
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+        float scale = 1.f;
+#pragma unroll 1
+        for (int w = 0; w < OZ_NS; ++w) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(w * OZ_BN + c0), r);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) two_sum_acc(hi[c0 + i], lo[c0 + i], __uint_as_float(r[i]) * scale);
+          scale *= 0.0078125f;   // 2^-7
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained) : "memory");
+    }
+    const int row = m_tile * BM + quarter * 32 + lane;
+    if (ok && row < p.M) {
+      float2* out = p.part + ((size_t)ks * p.M + row) * p.Np + (size_t)chunk * OZ_BN;
+#pragma unroll
+      for (int i = 0; i < OZ_BN; ++i) out[i] = make_float2(hi[i], lo[i]);
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+}
+
+// biased exponent field of |x| (0 for zero and subnormals)
+__device__ __forceinline__ int bexp(double x) {
+  return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
+}
+
+// the eight signed 7-bit digits of x against the exponent field eb of its
+// row / column maximum: F = trunc(|x| 2^(56 - E)), E = eb - 1022
+__device__ __forceinline__ void oz_digits(double x, int eb, __nv_bfloat16* d) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  unsigned long long m = ((unsigned long long)(hi & 0xfffffu) << 32) | lo;
+  unsigned long long F = 0;
+  if (ex > 0) {
+    m |= 1ull << 52;
+    const int sh = ex - eb + 3;   // <= 3 since ex <= eb
+    F = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+  }
+  const bool neg = (hi >> 31) != 0;
+#pragma unroll
+  for (int s = 0; s < OZ_NS; ++s) {
+    const int v = (int)((F >> (OZ_BITS * (OZ_NS - 1 - s))) & 127ull);
+    d[s] = __float2bfloat16_rn((float)(neg ? -v : v));
+  }
+}
+
+// exponent fields of the rows of op(A) (M x K): ea[m] = max over k; 32 x 32
+// tiles, one atomicMax per row and tile
+template <typename T>
+__global__ void oz_rowexp_kernel(const T* A, long lda, int op, int M, int K, int* ea) {
+  __shared__ int tile[32][33];
+  const int tiles_k = (K + 31) / 32, tiles_m = (M + 31) / 32;
+  const bool trans = (op == OP_T || op == OP_C);
+  for (int t = blockIdx.x; t < tiles_k * tiles_m; t += gridDim.x) {
+    const int k0 = (t % tiles_k) * 32, m0 = (t / tiles_k) * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      int e = 0;
+      if (!trans) {
+        const int m = m0 + yy, kk = k0 + threadIdx.x;
+        if (m < M && kk < K) {
+          const T v = A[(long)m * lda + kk];
+          if constexpr (sizeof(T) == 16) e = max(bexp(v.x), bexp(v.y));
+          else e = bexp(v);
+        }
+        tile[yy][threadIdx.x] = e;
+      } else {
+        const int kk = k0 + yy, m = m0 + threadIdx.x;
+        if (m < M && kk < K) {
+          const T v = A[(long)kk * lda + m];
+          if constexpr (sizeof(T) == 16) e = max(bexp(v.x), bexp(v.y));
+          else e = bexp(v);
+        }
+        tile[threadIdx.x][yy] = e;
+      }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      int e = tile[yy][threadIdx.x];
+      for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+      if (threadIdx.x == 0 && m0 + yy < M && e > 0) atomicMax(ea + m0 + yy, e);
+    }
+    __syncthreads();
+  }
+}
+
+// A digits: out[s][m][kr] as prep_a_kernel (real embedding [Re | Im]), with
+// the fixed-point digits of each row against ea[m]
+template <typename T>
+__global__ void oz_prep_a_kernel(const T* A, long lda, int op, int M, int K, int Kp,
+                                 const int* ea, __nv_bfloat16* out) {
+  __shared__ T tile[32][33];
+  constexpr bool cx = sizeof(T) == 16;
+  const int Kr = cx ? 2 * K : K;
+  const long slice = (long)M * Kp;
+  const int tiles_k = (K + 31) / 32, tiles_m = (M + 31) / 32;
+  const bool trans = (op == OP_T || op == OP_C);
+  const bool cj = (op == OP_C || op == OP_R);
+  for (int t = blockIdx.x; t < tiles_k * tiles_m; t += gridDim.x) {
+    const int k0 = (t % tiles_k) * 32, m0 = (t / tiles_k) * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      if (!trans) {
+        const int m = m0 + yy, kk = k0 + threadIdx.x;
+        tile[yy][threadIdx.x] = (m < M && kk < K) ? A[(long)m * lda + kk] : zero_of(T());
+      } else {
+        const int kk = k0 + yy, m = m0 + threadIdx.x;
+        tile[threadIdx.x][yy] = (m < M && kk < K) ? A[(long)kk * lda + m] : zero_of(T());
+      }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      const int m = m0 + yy, kk = k0 + threadIdx.x;
+      if (m < M && kk < K) {
+        const T v = tile[yy][threadIdx.x];
+        const int eb = ea[m];
+        __nv_bfloat16 d[OZ_NS];
+        if constexpr (cx) {
+          oz_digits(v.x, eb, d);
+          put_digits(out, slice, (long)m * Kp + kk, d, false);
+          oz_digits(v.y, eb, d);
+          put_digits(out, slice, (long)m * Kp + K + kk, d, cj);
+        } else {
+          oz_digits(v, eb, d);
+          put_digits(out, slice, (long)m * Kp + kk, d, false);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int pc = Kp - Kr;
+  const long tid = (long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x * blockDim.y;
+  const __nv_bfloat16 z = __float2bfloat16(0.0f);
+  for (long idx = tid; idx < (long)M * pc; idx += nth)
+    for (int s = 0; s < OZ_NS; ++s) out[s * slice + (idx / pc) * Kp + Kr + idx % pc] = z;
+}
+
+// exponent fields of the columns of op(B) (K x N): eb[n] = max over k
+template <typename T>
+__global__ void oz_colexp_kernel(const T* B, long ldb, int op, int K, int N, int* eb) {
+  __shared__ int tile[32][33];
+  const int tk = (K + 31) / 32, tn = (N + 31) / 32;
+  const bool trans = (op == OP_T || op == OP_C);
+  for (int t = blockIdx.x; t < tk * tn; t += gridDim.x) {
+    const int k0 = (t % tk) * 32, n0 = (t / tk) * 32;
+    // tile[jj - n0][kk - k0]
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      int e = 0;
+      if (!trans) {
+        const int kk = k0 + yy, jj = n0 + threadIdx.x;
+        if (kk < K && jj < N) {
+          const T v = B[(long)kk * ldb + jj];
+          if constexpr (sizeof(T) == 16) e = max(bexp(v.x), bexp(v.y));
+          else e = bexp(v);
+        }
+        tile[threadIdx.x][yy] = e;
+      } else {
+        const int jj = n0 + yy, kk = k0 + threadIdx.x;
+        if (kk < K && jj < N) {
+          const T v = B[(long)jj * ldb + kk];
+          if constexpr (sizeof(T) == 16) e = max(bexp(v.x), bexp(v.y));
+          else e = bexp(v);
+        }
+        tile[yy][threadIdx.x] = e;
+      }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      int e = tile[yy][threadIdx.x];
+      for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+      if (threadIdx.x == 0 && n0 + yy < N && e > 0) atomicMax(eb + n0 + yy, e);
+    }
+    __syncthreads();
+  }
+}
+
+// B digits: out[s][j][kr] as prep_b_kernel (B_emb = [[B_r, B_i], [-B_i, B_r]])
+template <typename T>
+__global__ void oz_prep_b_kernel(const T* B, long ldb, int op, int K, int N, int Kp, int Np,
+                                 const int* ebx, __nv_bfloat16* out) {
+  __shared__ T tile[32][33];
+  constexpr bool cx = sizeof(T) == 16;
+  const int Kr = cx ? 2 * K : K;
+  const int Nr = cx ? 2 * N : N;
+  const long slice = (long)Np * Kp;
+  const int tk = (K + 31) / 32, tn = (N + 31) / 32;
+  const bool trans = (op == OP_T || op == OP_C);
+  const bool cj = (op == OP_C || op == OP_R);
+  for (int t = blockIdx.x; t < tk * tn; t += gridDim.x) {
+    const int k0 = (t % tk) * 32, n0 = (t / tk) * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      if (!trans) {
+        const int kk = k0 + yy, jj = n0 + threadIdx.x;
+        tile[yy][threadIdx.x] = (kk < K && jj < N) ? B[(long)kk * ldb + jj] : zero_of(T());
+      } else {
+        const int jj = n0 + yy, kk = k0 + threadIdx.x;
+        tile[threadIdx.x][yy] = (kk < K && jj < N) ? B[(long)jj * ldb + kk] : zero_of(T());
+      }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+      const int jj = n0 + yy, kk = k0 + threadIdx.x;
+      if (jj < N && kk < K) {
+        const T v = tile[threadIdx.x][yy];
+        const int e = ebx[jj];
+        __nv_bfloat16 re[OZ_NS], im[OZ_NS];
+        if constexpr (cx) {
+          oz_digits(v.x, e, re);
+          oz_digits(v.y, e, im);
+          put_digits(out, slice, (long)jj * Kp + kk, re, false);
+          put_digits(out, slice, (long)jj * Kp + K + kk, im, !cj);
+          put_digits(out, slice, (long)(N + jj) * Kp + kk, im, cj);
+          put_digits(out, slice, (long)(N + jj) * Kp + K + kk, re, false);
+        } else {
+          oz_digits(v, e, re);
+          put_digits(out, slice, (long)jj * Kp + kk, re, false);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const __nv_bfloat16 z = __float2bfloat16(0.0f);
+  const long tid = (long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x * blockDim.y;
+  for (long idx = tid; idx < (long)(Np - Nr) * Kp; idx += nth)
+    for (int s = 0; s < OZ_NS; ++s) out[s * slice + (long)Nr * Kp + idx] = z;
+  const int pc = Kp - Kr;
+  for (long idx = tid; idx < (long)Nr * pc; idx += nth)
+    for (int s = 0; s < OZ_NS; ++s) out[s * slice + (idx / pc) * Kp + Kr + idx % pc] = z;
+}
+
+// C[m][j] = (sum over K splits of the pairs) 2^(E_m + E_j - 14), complex
+// from [C_r | C_i]; the pairs are summed with TwoSum and converted to fp64
+// once, and the power of two is applied to the exponent field
+template <typename T>
+__global__ void oz_reduce_kernel(const float2* part, int nks, int M, int N, int Np,
+                                 const int* ea, const int* ebx, T* C, long ldc) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)M * N;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int m = (int)(idx / N), j = (int)(idx % N);
+    const size_t sstep = (size_t)M * Np;
+    const float2* row = part + (size_t)m * Np + j;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int s = 0; s < nks; ++s) {
+      const float2 a = row[s * sstep];
+      two_sum_acc(rh, rl, a.x);
+      two_sum_acc(rh, rl, a.y);
+      if constexpr (sizeof(T) == 16) {
+        const float2 b = row[s * sstep + N];
+        two_sum_acc(ih, il, b.x);
+        two_sum_acc(ih, il, b.y);
+      }
+    }
+    const int e1 = ea[m], e2 = ebx[j];
+    // 2^(E_m + E_j - 14) with E = field - 1022
+    const int sc = (e1 > 0 && e2 > 0) ? e1 + e2 - 2044 - 14 : -2000;
+    const double f = sc > -1022 && sc < 1023 ? __hiloint2double((sc + 1023) << 20, 0) : 0.0;
+    const double re = (f64_of(rh) + f64_of(rl)) * f;
+    if constexpr (sizeof(T) == 16)
+      C[(long)m * ldc + j] = make_double2(re, (f64_of(ih) + f64_of(il)) * f);
+    else
+      C[(long)m * ldc + j] = re;
+  }
+}
+
 unsigned grid_cap(long n, long cap = 152L * 8) {
   long g = (n + 255) / 256;
   if (g < 1) g = 1;
@@ -556,12 +1000,14 @@ EncodeTiledFn get_encoder() {
 }
 
 // 3-D map over [ns][rows][Kp] slices (bf16 or tf32-in-fp32) with a
-// (128 bytes, box_rows, 1) box, 128B swizzle
-bool make_map(CUtensorMap* map, const void* base, int rows, int Kp, int box_rows, bool tf32) {
+// (128 bytes, box_rows, 1) box, 128B swizzle; ns = 0: the format's count
+bool make_map(CUtensorMap* map, const void* base, int rows, int Kp, int box_rows, bool tf32,
+              int ns = 0) {
   EncodeTiledFn enc = get_encoder();
   if (!enc) return false;
   const int eb = tf32 ? 4 : 2;
-  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)(tf32 ? 2 : 3)};
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows,
+                        (cuuint64_t)(ns > 0 ? ns : (tf32 ? 2 : 3))};
   cuuint64_t strides[2] = {(cuuint64_t)Kp * eb, (cuuint64_t)Kp * eb * rows};
   cuuint32_t box[3] = {(cuuint32_t)(KROW / eb), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
@@ -591,6 +1037,16 @@ struct SplitCtx {
   size_t bbuf_bytes = 0;
   float* part = nullptr;
   size_t part_bytes = 0;
+  // fp64-accurate products: digits of both operands, exponent fields, partials
+  void* oz_a = nullptr;
+  size_t oz_a_bytes = 0;
+  void* oz_b = nullptr;
+  size_t oz_b_bytes = 0;
+  int* oz_e = nullptr;
+  size_t oz_e_bytes = 0;
+  void* oz_part = nullptr;
+  size_t oz_part_bytes = 0;
+  long oz_launches = 0;
   int* err = nullptr;       // device error flag of the owning context
   // per-launch CUDA events around the tensor-core kernel (profiling)
   bool prof = false;
@@ -823,6 +1279,10 @@ void split_destroy(SplitCtx* sc) {
   if (sc->abuf) cudaFree(sc->abuf);
   if (sc->bbuf) cudaFree(sc->bbuf);
   if (sc->part) cudaFree(sc->part);
+  if (sc->oz_a) cudaFree(sc->oz_a);
+  if (sc->oz_b) cudaFree(sc->oz_b);
+  if (sc->oz_e) cudaFree(sc->oz_e);
+  if (sc->oz_part) cudaFree(sc->oz_part);
   delete sc;
 }
 
@@ -890,6 +1350,78 @@ ctm_status split_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, c
   st = prep_b(sc, B, ldb, opB, K, N, Kp, Np, sc->bbuf, s, launches);
   if (st != CTM_OK) return st;
   return run_mma(sc, sc->abuf, sc->bbuf, M, Kp, Nr, nchunks, BNc, C, ldc, N, s, launches);
+}
+
+ctm_status oz_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, const void* B,
+                   long ldb, int M, int N, int K, void* C, long ldc, cudaStream_t s,
+                   long* launches) {
+  if (M <= 0 || N <= 0 || K <= 0) return sfail(sc, CTM_EINVAL, "empty fp64-accurate product");
+  const bool cx = sc->cx;
+  const int Kr = cx ? 2 * K : K;
+  const int Kp = pad_to(Kr, BK);
+  const int Nr = cx ? 2 * N : N;
+  const int Np = pad_to(Nr, OZ_BN);
+  const int nchunks = Np / OZ_BN;
+  const int mt = (M + BM - 1) / BM;
+  const int kb_total = Kp / BK;
+  // about two waves of CTAs, at least OZ_KB_DRAIN K blocks each
+  const long tiles = (long)mt * nchunks;
+  int nks = (int)std::max<long>(1, std::min<long>((2 * 152 + tiles - 1) / tiles,
+                                                  (kb_total + OZ_KB_DRAIN - 1) / OZ_KB_DRAIN));
+  const int kb_split = (kb_total + nks - 1) / nks;
+  nks = (kb_total + kb_split - 1) / kb_split;
+  ctm_status st = grow(sc, &sc->oz_a, &sc->oz_a_bytes, (size_t)OZ_NS * M * Kp * 2);
+  if (st == CTM_OK) st = grow(sc, &sc->oz_b, &sc->oz_b_bytes, (size_t)OZ_NS * Np * Kp * 2);
+  if (st == CTM_OK) st = grow(sc, (void**)&sc->oz_e, &sc->oz_e_bytes, (size_t)(M + N) * sizeof(int));
+  if (st == CTM_OK) st = grow(sc, &sc->oz_part, &sc->oz_part_bytes, (size_t)nks * M * Np * 8);
+  if (st != CTM_OK) return st;
+  int* ea = sc->oz_e;
+  int* ebx = sc->oz_e + M;
+  if (cudaMemsetAsync(sc->oz_e, 0, (size_t)(M + N) * sizeof(int), s) != cudaSuccess)
+    return sfail(sc, CTM_ECUDA, "exponent reset failed");
+  const dim3 blk(32, 8);
+  const unsigned ga = (unsigned)std::max<long>(1, std::min<long>((long)((K + 31) / 32) * ((M + 31) / 32), 152L * 16));
+  const unsigned gb = (unsigned)std::max<long>(1, std::min<long>((long)((K + 31) / 32) * ((N + 31) / 32), 152L * 16));
+  __nv_bfloat16* da = static_cast<__nv_bfloat16*>(sc->oz_a);
+  __nv_bfloat16* db = static_cast<__nv_bfloat16*>(sc->oz_b);
+  if (cx) {
+    oz_rowexp_kernel<cplx><<<ga, blk, 0, s>>>((const cplx*)A, lda, opA, M, K, ea);
+    oz_colexp_kernel<cplx><<<gb, blk, 0, s>>>((const cplx*)B, ldb, opB, K, N, ebx);
+    oz_prep_a_kernel<cplx><<<ga, blk, 0, s>>>((const cplx*)A, lda, opA, M, K, Kp, ea, da);
+    oz_prep_b_kernel<cplx><<<gb, blk, 0, s>>>((const cplx*)B, ldb, opB, K, N, Kp, Np, ebx, db);
+  } else {
+    oz_rowexp_kernel<double><<<ga, blk, 0, s>>>((const double*)A, lda, opA, M, K, ea);
+    oz_colexp_kernel<double><<<gb, blk, 0, s>>>((const double*)B, ldb, opB, K, N, ebx);
+    oz_prep_a_kernel<double><<<ga, blk, 0, s>>>((const double*)A, lda, opA, M, K, Kp, ea, da);
+    oz_prep_b_kernel<double><<<gb, blk, 0, s>>>((const double*)B, ldb, opB, K, N, Kp, Np, ebx, db);
+  }
+  if (launches) *launches += 4;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, sc->oz_a, M, Kp, BM, false, OZ_NS) ||
+      !make_map(&tb, sc->oz_b, Np, Kp, OZ_BN, false, OZ_NS))
+    return sfail(sc, CTM_ECUDA, "cuTensorMapEncodeTiled failed");
+  OzParams p;
+  p.M = M;
+  p.Np = Np;
+  p.kb_total = kb_total;
+  p.kb_split = kb_split;
+  p.part = static_cast<float2*>(sc->oz_part);
+  p.err = sc->err;
+  const size_t smem = 1024 + (size_t)STAGES * OZ_Q_BYTES + (2 * STAGES + 2) * 8 + 16;
+  static size_t configured = 0;
+  if (raise_smem((const void*)oz_mma_kernel, configured, smem) != cudaSuccess)
+    return sfail(sc, CTM_ECUDA, "cannot reserve shared memory for the fp64-accurate product");
+  oz_mma_kernel<<<dim3(mt, nchunks, nks), 192, smem, s>>>(ta, tb, p);
+  ++sc->oz_launches;
+  if (cx)
+    oz_reduce_kernel<cplx><<<grid_cap((long)M * N), 256, 0, s>>>(
+        p.part, nks, M, N, Np, ea, ebx, (cplx*)C, ldc);
+  else
+    oz_reduce_kernel<double><<<grid_cap((long)M * N), 256, 0, s>>>(
+        p.part, nks, M, N, Np, ea, ebx, (double*)C, ldc);
+  if (launches) *launches += 2;
+  if (cudaGetLastError() != cudaSuccess) return sfail(sc, CTM_ECUDA, "fp64-accurate product launch failed");
+  return CTM_OK;
 }
 
 size_t split_partial_splits(size_t N, bool cx) {

@@ -35,6 +35,17 @@ ctm_status split_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, c
                       long ldb, int M, int N, int K, void* C, long ldc, cudaStream_t s,
                       long* launches);
 
+// C = op(A) op(B) to fp64 accuracy on the bf16 tensor cores: every operand
+// row / column is written as a 56-bit fixed-point number against the
+// exponent of its largest entry and cut into eight 7-bit digits; the digit
+// products of weight <= 7 are accumulated exactly in fp32 tensor memory and
+// combined as unevaluated fp32 pairs (about 2^-48 relative to the products
+// of the row and column maxima, the bound of an fp64 product). Ops and
+// layouts as in split_gemm.
+ctm_status oz_gemm(SplitCtx* sc, int opA, const void* A, long lda, int opB, const void* B,
+                   long ldb, int M, int N, int K, void* C, long ldc, cudaStream_t s,
+                   long* launches);
+
 // Profiling of the tensor-core kernel: on = 1 / 0 starts / stops recording
 // CUDA events around every launch (and clears the totals); on = -1 reads the
 // accumulated device time, launches, tensor-pipe flops and operand bytes.

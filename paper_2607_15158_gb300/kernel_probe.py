@@ -1,6 +1,6 @@
 """Run one kernel class of the library in isolation, for profilers.
 
-    python -m paper_2607_15158_gb300.kernel_probe --workload NAME --op apply|corner \
+    python -m paper_2607_15158_gb300.kernel_probe --workload NAME --op apply|corner|move \
         [--prec split|tf32|fp64] [--repeat R]
 
 Builds a context of the named synthetic workload (ctm_synth.WORKLOADS) with
@@ -12,7 +12,9 @@ started with --profile-from-start off sees only them):
   op(Q2) Z for a Gaussian N x k block (ctm_corner_apply: the corner is built
   and sliced, then the tensor-core product runs);
 * corner: one enlarged corner Q1 (ctm_corner: the contractions of C, T and
-  the fused absorption of A and conj(A)).
+  the fused absorption of A and conj(A));
+* move: one left move (ctm_move: every kernel of the move, including the
+  batched small SVDs with their fp32 pre-solve).
 
 Prints the mean wall time per call. All work runs in the library's kernels.
 """
@@ -31,7 +33,7 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="small_1x1_D6_chi80_c128")
-    ap.add_argument("--op", choices=["apply", "corner"], default="apply")
+    ap.add_argument("--op", choices=["apply", "corner", "move"], default="apply")
     ap.add_argument("--prec", choices=["split", "tf32", "fp64"], default="split")
     ap.add_argument("--repeat", type=int, default=2)
     args = ap.parse_args()
@@ -51,7 +53,7 @@ def main():
     A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, diag_weight=w["diag_weight"])
     Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx)
     ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx,
-                       opts=pkg.ctm_default_opts(p=p, prec=prec))
+                       opts=pkg.ctm_default_opts(p=p, prec=prec, warmup_iters=0))
     ctx.ctm_set_env(Cs, Ts)
     rng = np.random.default_rng(1)
     Z = rng.standard_normal((ctx.N, ctx.k))
@@ -61,8 +63,10 @@ def main():
     def call():
         if args.op == "apply":
             ctx.ctm_corner_apply(0, 0, 0, 2, Z)
-        else:
+        elif args.op == "corner":
             ctx.ctm_corner(0, 0, 0, 1)
+        else:
+            ctx.ctm_move(0)
 
     call()
     torch.cuda.synchronize()

@@ -43,14 +43,14 @@ def test_default_opts_without_gpu(lib):
             o.normalize, o.sign_fix) == (5, 1, 5, 8, 0, 0, 1, 1)
     assert o.svd_rel_cutoff == 1e-12
     assert (o.svd_max_sweeps, o.init_mode, o.recycle_sin2, o.min_si_steps) == (80, 0, 0.0, 3)
-    assert (o.absorb_tc, o.si_coupled, o.warmup_rsvd, o.svd_presolve) == (0, 0, 0, 1)
+    assert (o.absorb_tc, o.si_coupled, o.warmup_rsvd, o.svd_presolve, o.fp64_tc) == (0, 0, 0, 1, 1)
 
 
 def test_bad_options_are_rejected_before_device_work(lib):
     pkg.load()
     A = (ctypes.c_void_p * 1)(ctypes.c_void_p(16))
     for kw in (dict(svd_max_sweeps=0), dict(init_mode=2), dict(recycle_sin2=-1.0),
-               dict(min_si_steps=-1), dict(svd_presolve=2)):
+               dict(min_si_steps=-1), dict(svd_presolve=2), dict(fp64_tc=-1)):
         o = pkg.ctm_default_opts(**kw)
         ptr = ctypes.c_void_p()
         st = pkg._lib.ctm_init(ctypes.byref(ptr), 1, 1, A, None, 0, 2, 2, 4, ctypes.byref(o))

@@ -157,3 +157,34 @@ def test_converged_tf32_matches_oracle():
     # measured: spectra 4.8e-7, energies 8.8e-8
     assert es < TOL_SPLIT and ee < 2 * TOL_SPLIT_ENERGY
     ctx.ctm_free()
+
+
+@pytest.mark.parametrize("case", [
+    # M, N, K, opA, complex, grading (decades across rows / columns)
+    (149, 149, 5184, 2, True, 0),     # CholeskyQR Gram / rho shape at the bench size
+    (5184, 144, 149, 0, True, 6),     # projector Z v s^-1/2 at the bench size
+    (130, 70, 1000, 1, False, 8),     # real, ragged tiles
+    (37, 5, 64, 0, True, 0),          # one K block, one column chunk
+])
+def test_fp64_tensor_core_product_matches_fp64(case):
+    """The exact-digit tensor-core product (ctm_gemm_fp64tc, used for the
+    fp64 products of split contexts) against numpy's fp64 product: every
+    element within 1e-13 of sum_k |op(A)_mk| |B_kn| (an fp64 product's own
+    error is ~sqrt(K) 1.1e-16 of that), also with rows and columns graded
+    over several decades (per-row and per-column exponents)."""
+    M, N, K, op, cx, dec = case
+    rng = np.random.default_rng(11)
+
+    def rnd(*shape):
+        x = rng.standard_normal(shape)
+        return x + 1j * rng.standard_normal(shape) if cx else x
+
+    opA = rnd(M, K) * (10.0 ** (-dec * np.arange(M) / M))[:, None]
+    B = rnd(K, N) * (10.0 ** (-dec * np.arange(N) / N))[None, :]
+    A = {0: opA, 1: opA.T, 2: opA.conj().T}[op].copy()
+    C = pkg.ctm_gemm_fp64tc(A, B, op)
+    ref = opA @ B
+    bound = np.abs(opA) @ np.abs(B)
+    rel = np.abs(C - ref) / bound
+    print(f"fp64 tensor-core product {M}x{N}x{K} op {op}: max error / (|A||B|) {rel.max():.2e}")
+    assert rel.max() < 1e-13
