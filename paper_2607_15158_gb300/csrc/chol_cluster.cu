@@ -153,8 +153,10 @@ __global__ void __cluster_dims__(CC, 1, 1) __launch_bounds__(CT, 1)
       if (!pv.dead) {
         const T* cb = colbuf + slot * k;
         T* Si = S + tri(i, 0);
-        // S(i, l) -= L(i, j) conj(L(l, j)), j < l <= i
-        for (int l = j + 1 + lane; l <= i; l += 32) Si[l] = subv(Si[l], mulv(lij, scalev(cb[l], inv)));
+        // S(i, l) -= L(i, j) conj(L(l, j)) = (L(i, j) / piv) conj(G(l, j)),
+        // j < l <= i: one complex multiply-add per entry
+        const T a = scalev(lij, inv);
+        for (int l = j + 1 + lane; l <= i; l += 32) fnmav(Si[l], a, cb[l]);
       }
     }
     __syncthreads();
@@ -174,26 +176,36 @@ __global__ void __cluster_dims__(CC, 1, 1) __launch_bounds__(CT, 1)
       T* dst = S + tri(i, 0);
       for (int l = lane; l <= i; l += 32) dst[l] = src[l];
     }
+    // every CTA has its copy before any CTA rescales its own rows below
+    cl.sync();
+    // L' = L diag(1 / L_ll) (rinv kept in orig), so that the substitution
+    // below needs no division per step
+    double* rinv = orig;
+    for (int i = threadIdx.x; i < k; i += CT) rinv[i] = 1.0 / realv(S[tri(i, i)]);
     __syncthreads();
-    // columns c = rank, rank + 8, ... of X = L^-1 by forward substitution
-    // (one warp per column, x in shared memory), written as
+    for (int i = wp; i < k; i += nw) {
+      T* Si = S + tri(i, 0);
+      for (int l = lane; l <= i; l += 32) Si[l] = scalev(Si[l], rinv[l]);
+    }
+    __syncthreads();
+    // columns c = rank, rank + 8, ... of X = L^-1, right-looking: acc_i =
+    // delta_ic - sum_{l < i} L'(i, l) acc_l, x_i = acc_i / L_ii (one warp per
+    // column, lanes along i, acc in shared memory), written as
     // W[c][i] = conj(X[i][c]) / D_c
     T* Wm = static_cast<T*>(a.W);
     T* x = xs + (size_t)wp * k;
     for (int c = rank + CC * wp; c < k; c += CC * nw) {
-      if (lane == 0) x[c] = scalev(one_of<T>(), 1.0 / realv(S[tri(c, c)]));
+      for (int i = c + lane; i < k; i += 32) x[i] = i == c ? one_of<T>() : zero_of(T());
       __syncwarp();
-      for (int i = c + 1; i < k; ++i) {
-        T acc = zero_of(T());
-        const T* Li = S + tri(i, 0);
-        for (int l = c + lane; l < i; l += 32) fmav(acc, Li[l], x[l]);
-        acc = warp_sum(acc);
-        if (lane == 0) x[i] = scalev(acc, -1.0 / realv(Li[i]));
+      for (int l = c; l + 1 < k; ++l) {
+        const T al = x[l];
+        for (int i = l + 1 + lane; i < k; i += 32) fnmav(x[i], S[tri(i, l)], al);
         __syncwarp();
       }
       const double id = 1.0 / dsc[c];
       T* wrow = Wm + (size_t)c * k;
-      for (int i = lane; i < k; i += 32) wrow[i] = i >= c ? scalev(conjv(x[i]), id) : zero_of(T());
+      for (int i = lane; i < k; i += 32)
+        wrow[i] = i >= c ? scalev(conjv(x[i]), rinv[i] * id) : zero_of(T());
       __syncwarp();
     }
   }

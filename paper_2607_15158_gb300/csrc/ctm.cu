@@ -431,6 +431,9 @@ ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, 
   return gemm(c, g);
 }
 
+ctm_status mm_exact(ctm_ctx* c, int opA, int opB, long M, long Nn, long K, const void* A,
+                    long lda, const void* B, long ldb, void* Cm, long ldc);
+
 // Orthonormal basis of span(Z) in place (N x k): shifted CholeskyQR followed
 // by two CholeskyQR passes (CholeskyQR3, Fukaya et al. 2020). Only the span
 // enters the projectors (paper step 1), so R is not kept.
@@ -505,7 +508,14 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
       if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
     } else if (smem_chol) {
       // L = chol(D^-1 G D^-1) in shared memory, Q = Z D^-1 L^-H row by row
-      if (cl_chol) {
+      if (cl_chol && c->split && c->opts.fp64_tc) {
+        // split contexts: the explicit W = D^-1 L^-H (its norm is at most
+        // ~shift^-1/2 in the shifted pass) and Q = Z W as an fp64-accurate
+        // tensor-core product instead of the fp64 row solve
+        CTM_CUDA_OK(chol_cluster(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
+                                 c->G, c->err, c->stream, &c->launches));
+        CK(mm_exact(c, OP_N, OP_N, c->N, c->k, c->k, Zm, c->k, c->G, c->k, tmp, c->k));
+      } else if (cl_chol) {
         CTM_CUDA_OK(chol_cluster(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
                                  nullptr, c->err, c->stream, &c->launches));
         CTM_CUDA_OK(trsm_rows(c->cx, c->k, c->N, c->Linv, c->dsc, Zm, tmp, c->num_sms, c->stream,
