@@ -35,7 +35,7 @@ constexpr int CT = 256;   // threads per CTA
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }   // i >= j
 
 struct Pivot {
-  double piv;
+  double piv, inv;   // pivot and its reciprocal (formed once, by the owner)
   int dead;
   int pad;
 };
@@ -133,13 +133,16 @@ __global__ void __cluster_dims__(CC, 1, 1) __launch_bounds__(CT, 1)
         } else {
           pv.piv = sqrt(d);
         }
+        // one division per column: on this GPU's narrow fp64 pipe a division
+        // by every warp would cost more than the column's update
+        pv.inv = 1.0 / pv.piv;
         for (int dst = 0; dst < CC; ++dst) cl.map_shared_rank(pivbuf, dst)[slot] = pv;
       }
     }
     cl.sync();
     // phase B: scale own entries of column j, update own rows
     const Pivot pv = pivbuf[slot];
-    const double inv = 1.0 / pv.piv;
+    const double inv = pv.inv;
     if (j % CC == rank && threadIdx.x == 0) {
       T dv = one_of<T>();
       if (!pv.dead) dv = scalev(one_of<T>(), pv.piv);

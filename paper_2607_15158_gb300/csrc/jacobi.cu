@@ -257,19 +257,44 @@ __global__ void __launch_bounds__(JT) jacobi_coop(JacobiArgs a) {
             if (lane + 32 * e < k) fmacv(ga, xr[e], yr[e]);
           ga = warp_sum(ga);
           const double al = __ldcg(nsq + p), be = __ldcg(nsq + q);
-          const double gm = sqrt(absq(ga));
-          const double nrm = sqrt(al) * sqrt(be);
-          // rotate when |gamma| > tol sqrt(alpha beta)
-          if (gm > tol * nrm && gm != 0.0) {
-            if (lane == 0)   // this sweep rotated
+          // the rotation's scalars on lane 0 only, then broadcast: every
+          // fp64 instruction a whole warp executes costs the SM's narrow fp64
+          // pipe its full width
+          double gm = 0.0, tt = 0.0, c = 1.0, s = 0.0, ex = 0.0, ey = 0.0;
+          int rot = 0;
+          if (lane == 0) {
+            gm = sqrt(absq(ga));
+            const double nrm = sqrt(al) * sqrt(be);
+            // rotate when |gamma| > tol sqrt(alpha beta)
+            rot = gm > tol * nrm && gm != 0.0;
+            if (rot) {
               atomicMax(offb, (unsigned long long)__double_as_longlong(
-                                  nrm > 0.0 ? fmin(gm / nrm, 1.0) : 1.0));
-            const double zeta = (be - al) / (2.0 * gm);
-            const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-            const double c = 1.0 / hypot(1.0, tt), s = c * tt;
-            T eph;   // conj(gamma) / |gamma|
-            if constexpr (sizeof(T) == 8) eph = ga / gm;
-            else eph = make_double2(ga.x / gm, -ga.y / gm);
+                                  nrm > 0.0 ? fmin(gm / nrm, 1.0) : 1.0));   // this sweep rotated
+              const double zeta = (be - al) / (2.0 * gm);
+              tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+              c = 1.0 / hypot(1.0, tt);
+              s = c * tt;
+              // conj(gamma) / |gamma|
+              const double ig = 1.0 / gm;
+              if constexpr (sizeof(T) == 8) {
+                ex = ga * ig;
+              } else {
+                ex = ga.x * ig;
+                ey = -ga.y * ig;
+              }
+            }
+          }
+          rot = __shfl_sync(0xffffffffu, rot, 0);
+          if (rot) {
+            gm = __shfl_sync(0xffffffffu, gm, 0);
+            tt = __shfl_sync(0xffffffffu, tt, 0);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            ex = __shfl_sync(0xffffffffu, ex, 0);
+            if constexpr (sizeof(T) == 16) ey = __shfl_sync(0xffffffffu, ey, 0);
+            T eph;
+            if constexpr (sizeof(T) == 8) eph = ex;
+            else eph = make_double2(ex, ey);
             const T se = scalev(eph, s), ce = scalev(eph, c);
 #pragma unroll
             for (int e = 0; e < R; ++e) {
