@@ -184,6 +184,11 @@ void use_lane(ctm_ctx* c, int i) {
   c->dsc = L.dsc;
   c->dead = L.dead;
   c->chol_work = L.chol_work;
+  c->Xn = L.Xn;
+  c->Wn = L.Wn;
+  c->Vs = L.Vs;
+  c->Us = L.Us;
+  c->ph = L.ph;
   c->cur_lane = i;
 }
 
@@ -986,14 +991,28 @@ ctm_status move_impl(ctm_ctx* c, int r) {
     // the cuts of a column are independent until the absorption: their
     // small SVDs share one launch
     if (!svd) CK(si_small_svd(c, Lyf));
+    // the projector step of each cut (recycled bases, P_l, P_r^H) runs on the
+    // cut's lane once the batched SVD is done; lane 0 absorbs after all of them
+    if (!svd && nw > 0) {
+      CTM_CUDA_OK(cudaEventRecord(c->lanes[0].ev, c->lanes[0].stream));
+      for (int l = 1; l < nl; ++l)
+        CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[l].stream, c->lanes[0].ev, 0));
+    }
     for (int y = 0; y < (svd ? 0 : Lyf); ++y) {
       const int cut = y * Lxf + x;
+      use_lane(c, lane_of(y));
       CK(si_finish(c, r, cut, y, at(c->Pl, y * NC, c), at(c->PrH, y * NC, c)));
       CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPl, cut * NC, c), at(c->Pl, y * NC, c), NC * c->es,
                                   cudaMemcpyDeviceToDevice, c->stream));
       CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPrH, cut * NC, c), at(c->PrH, y * NC, c),
                                   NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
     }
+    use_lane(c, 0);
+    if (!svd && nw > 0)
+      for (int l = 1; l < nl; ++l) {
+        CTM_CUDA_OK(cudaEventRecord(c->lanes[l].ev, c->lanes[l].stream));
+        CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[0].stream, c->lanes[l].ev, 0));
+      }
     {
       PhaseScope ps(c, PH_ABSORB);
       for (int y = 0; y < Lyf; ++y) CK(absorb_site(c, r, x, y, Lyf));
@@ -1371,6 +1390,11 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
     L0.dsc = c->dsc;
     L0.dead = c->dead;
     L0.chol_work = c->chol_work;
+    L0.Xn = c->Xn;
+    L0.Wn = c->Wn;
+    L0.Vs = c->Vs;
+    L0.Us = c->Us;
+    L0.ph = c->ph;
     if (cudaEventCreateWithFlags(&L0.ev, cudaEventDisableTiming) != cudaSuccess)
       return bail(fail(c, CTM_ECUDA, "cudaEventCreate failed"));
     c->lanes.push_back(L0);
@@ -1401,7 +1425,12 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
           (st = dalloc(c, &M.Linv, k * k * es)) != CTM_OK ||
           (st = dalloc(c, (void**)&M.dsc, k * sizeof(double))) != CTM_OK ||
           (st = dalloc(c, (void**)&M.dead, k * sizeof(int))) != CTM_OK ||
-          (st = dalloc(c, &M.chol_work, chol_coop_work_bytes((int)k, 1))) != CTM_OK)
+          (st = dalloc(c, &M.chol_work, chol_coop_work_bytes((int)k, 1))) != CTM_OK ||
+          (st = dalloc(c, &M.Xn, N * k * es)) != CTM_OK ||
+          (st = dalloc(c, &M.Wn, N * k * es)) != CTM_OK ||
+          (st = dalloc(c, &M.Vs, k * chi * es)) != CTM_OK ||
+          (st = dalloc(c, &M.Us, k * chi * es)) != CTM_OK ||
+          (st = dalloc(c, &M.ph, std::max(k, (size_t)chi) * es)) != CTM_OK)
         return bail(st);
       if (c->opts.prec != CTM_PREC_FP64 &&
           (st = split_create(&M.split, cx, c->opts.prec == CTM_PREC_SPLIT_TF32, (int)N, (int)k,
@@ -1667,7 +1696,8 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
     const bool fused = use_fused_absorb(cx, o->prec != CTM_PREC_FP64, *o, Dk, Db, d);
     const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
     size_t lane = 4 * NN * es + 4 * laneT * es + ((size_t)64 << 20) + 4 * N * k * es +
-                  2 * k * k * es + 12 * k + chol_coop_work_bytes((int)k, 1);
+                  2 * k * k * es + 12 * k + chol_coop_work_bytes((int)k, 1) +
+                  (2 * N * k + 2 * k * chi + std::max(k, (size_t)chi)) * es;   // si_finish
     if (o->prec != CTM_PREC_FP64) {
       const size_t Kp = ((cx ? 2 : 1) * N + 63) / 64 * 64;
       const size_t sb = o->prec == CTM_PREC_SPLIT_TF32 ? 8 : 6;

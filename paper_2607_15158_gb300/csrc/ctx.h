@@ -142,6 +142,12 @@ struct ctm_ctx {
     double* dsc = nullptr;
     int* dead = nullptr;
     void* chol_work = nullptr;   // cooperative Cholesky scratch (large k)
+    // projector step of a cut (si_finish): recycled bases, scaled v / u, phases
+    void* Xn = nullptr;
+    void* Wn = nullptr;
+    void* Vs = nullptr;
+    void* Us = nullptr;
+    void* ph = nullptr;
   };
   std::vector<Lane> lanes;   // lane 0 = the context's own buffers and stream
   int cur_lane = 0;

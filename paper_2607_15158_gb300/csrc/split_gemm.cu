@@ -512,16 +512,16 @@ __global__ void reduce_kernel(const float* part, int nks, int M, int N, int Np, 
     const size_t sstep = (size_t)M * Np;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     int s = 0;
-    // four splits' loads in flight at a time (the sum keeps the split order)
-    for (; s + 4 <= nks; s += 4) {
-      float a[4], b[4];
+    // eight splits' loads in flight at a time (the sum keeps the split order)
+    for (; s + 8 <= nks; s += 8) {
+      float a[8], b[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         a[u] = __ldcs(row + (s + u) * sstep);
         if constexpr (sizeof(T) == 16) b[u] = __ldcs(row + (s + u) * sstep + N);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         two_sum_acc(rh, rl, a[u]);
         if constexpr (sizeof(T) == 16) two_sum_acc(ih, il, b[u]);
       }
