@@ -111,6 +111,7 @@ __device__ __forceinline__ void apply_round(typename F32<CX>::T* M, const float4
     T* x = M + (size_t)p * k;
     T* y = M + (size_t)q * k;
     const float2 e = make_float2(rp.z, rp.w);
+    #pragma unroll 4
     for (int r = l8; r < k; r += 8) {
       T xv = x[r], yv = y[r];
       E::rot(xv, yv, rp.x, rp.y, e);
@@ -197,6 +198,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
             // exact squared norms and the overlap of the pair, every round
             float2 ga = make_float2(0.f, 0.f);
             float al = 0.f, be = 0.f;
+            #pragma unroll 4
             for (int r = l8; r < k; r += 8) {
               const T xv = x[r], yv = y[r];
               al += E::nrm2(xv);
@@ -216,6 +218,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(J32T, 1)
               const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
               const float c = 1.f / sqrtf(1.f + tt * tt), s = c * tt;
               const float2 e = make_float2(ga.x / gm, -ga.y / gm);   // conj(gamma) / |gamma|
+              #pragma unroll 4
               for (int r = l8; r < k; r += 8) {
                 T xv = x[r], yv = y[r];
                 E::rot(xv, yv, c, s, e);
