@@ -1007,16 +1007,26 @@ ctm_status move_impl(ctm_ctx* c, int r) {
       CTM_CUDA_OK(cudaMemcpyAsync(at(c->lastPrH, cut * NC, c), at(c->PrH, y * NC, c),
                                   NC * c->es, cudaMemcpyDeviceToDevice, c->stream));
     }
+    // the absorption of site y uses the projectors of cuts y and y - 1: every
+    // lane waits for all projector steps, then absorbs its own sites
+    if (!svd && nw > 0) {
+      for (int l = 1; l < nl; ++l)
+        CTM_CUDA_OK(cudaEventRecord(c->lanes[l].ev, c->lanes[l].stream));
+      for (int l = 1; l < nl; ++l)
+        for (int m = 1; m < nl; ++m)
+          if (m != l) CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[l].stream, c->lanes[m].ev, 0));
+    }
+    for (int y = 0; y < Lyf; ++y) {
+      use_lane(c, svd ? 0 : lane_of(y));
+      PhaseScope ps(c, PH_ABSORB);
+      CK(absorb_site(c, r, x, y, Lyf));
+    }
     use_lane(c, 0);
     if (!svd && nw > 0)
       for (int l = 1; l < nl; ++l) {
         CTM_CUDA_OK(cudaEventRecord(c->lanes[l].ev, c->lanes[l].stream));
         CTM_CUDA_OK(cudaStreamWaitEvent(c->lanes[0].stream, c->lanes[l].ev, 0));
       }
-    {
-      PhaseScope ps(c, PH_ABSORB);
-      for (int y = 0; y < Lyf; ++y) CK(absorb_site(c, r, x, y, Lyf));
-    }
     PhaseScope psn(c, PH_NORM);
     if (c->opts.normalize) {
       const size_t mark = c->scratch_off;
