@@ -450,8 +450,10 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
   // carry no information of the block, and the next QR orthonormalises them.
   // Three passes (shifted CholeskyQR3) on the Jacobi-scaled Gram (columns of
   // unit norm; much of the ill-conditioning of M^H M X is column scaling):
-  // fp64 Gram (lower triangle), Cholesky factor in shared memory, and Q by a
-  // row-parallel triangular solve.
+  // fp64-accurate Gram (an exact-digit tensor-core product in split
+  // contexts), the k x k Cholesky factor on a cluster of eight CTAs, and
+  // Q = Z D^-1 L^-H by the fp64 row solve or, in split contexts, as Z times
+  // the explicit D^-1 L^-H.
   ++c->qr_calls;
   const bool split = split_mode && c->split != nullptr;
   const int passes = 3;
