@@ -531,6 +531,19 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
         CTM_CUDA_OK(chol_qr_pass(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
                                  Zm, tmp, c->err, c->num_sms, c->stream, &c->launches));
       }
+    } else if (cl_chol) {
+      // the packed factor exceeds one CTA: the row-distributed cluster factor
+      // forms W = D^-1 L^-H; Q = Z W (fp64-accurate in the shifted first
+      // pass, whose W has norm up to shift^-1/2; split in the second)
+      CTM_CUDA_OK(chol_cluster(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, c->dsc, dead,
+                               c->G, c->err, c->stream, &c->launches));
+      if (split && pass > 0) {
+        const ctm_status st = split_gemm(c->split, OP_N, Zm, c->k, OP_N, c->G, c->k, c->N, c->k,
+                                         c->k, tmp, c->k, c->stream, &c->launches);
+        if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
+      } else {
+        CK(mm_exact(c, OP_N, OP_N, c->N, c->k, c->k, Zm, c->k, c->G, c->k, tmp, c->k));
+      }
     } else {
       CTM_CUDA_OK(chol_inv_coop(c->cx, c->k, c->N, pass == 0, true, c->G, c->Linv, 1, dead,
                                 c->chol_work, c->err, c->num_sms, c->stream, &c->launches));

@@ -115,8 +115,10 @@ cudaError_t trsm_rows(bool cx, int k, long rows, const void* L, const double* ds
 // The factor of chol_qr_pass / chol_factor_inv (same options and outputs:
 // L, dsc, dead; with W != null also W = D^-1 L^-H) computed by a cluster of
 // eight CTAs (rows dealt cyclically, one cluster barrier per column). W may
-// alias G. Supported when chol_cluster_supported(cx, k) (the packed factor
-// fits one CTA's shared memory: k <= 156 complex, 225 real).
+// alias G. Where the packed factor fits one CTA's shared memory (k <= 156
+// complex, 225 real) every CTA gathers it for the inverse; above that the
+// CTAs keep only their own rows and read the others through distributed
+// shared memory (chol_cluster_supported: up to k ~ 390 complex).
 bool chol_cluster_supported(bool cx, int k);
 cudaError_t chol_cluster(bool cx, int k, long rows, bool shift, bool scale, const void* G,
                          void* L, double* dsc, int* dead, void* W, int* err, cudaStream_t s,
