@@ -106,12 +106,17 @@ def test_single_moves_each_direction():
 
 @pytest.mark.parametrize("case", [
     # k = 175 complex: the packed Gram factor no longer fits one block's
-    # shared memory, so the QR passes take the cooperative Cholesky with an
-    # explicit inverse, and the Jacobi SVD nine columns per lane
+    # shared memory, so the QR passes take the row-distributed cluster
+    # Cholesky with an explicit inverse, and the Jacobi SVD nine columns per
+    # lane (fp64 sweeps only: the fp32 pre-solve needs k <= 169)
     (1, 1, 2, 2, 170, 5, True, 1),
     # the same block size on a 1 x 2 cell: two cuts per column on concurrent
-    # lanes, each with its own cooperative-Cholesky scratch
+    # lanes
     (1, 2, 2, 2, 170, 5, True, 1),
+    # k = 160 complex: the one-block factor still fits, the gathering cluster
+    # kernel does not, so the row-distributed cluster factor feeds the fp64
+    # row solve
+    (1, 1, 2, 2, 155, 5, True, 1),
     # D = 7 complex fp64: A, B and the 49 x 49 pair tiles exceed one block's
     # shared memory, so the absorption runs unfused (two GEMMs, permutes)
     (1, 1, 2, 7, 4, 3, True, 1),
