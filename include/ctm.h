@@ -67,7 +67,9 @@ typedef enum { CTM_F64 = 0, CTM_C128 = 1 } ctm_dtype;
  * with fp32 accumulation and fp64 reduction, the fused A / conj(A)
  * absorption in fp32. SPLIT_TF32: the same with 3xTF32 (two tf32 slices,
  * three products, the tensor cores' tf32 kind at half the bf16 rate). QR,
- * small SVD, rho, the projectors and s^-1/2 stay fp64 in both. */
+ * small SVD, rho, the projectors and s^-1/2 stay fp64-accurate in both (their
+ * products as exact fixed-point digit products on the tensor cores with
+ * opts.fp64_tc, see ctm_gemm_fp64tc). */
 typedef enum { CTM_PREC_FP64 = 0, CTM_PREC_SPLIT_BF16 = 1, CTM_PREC_SPLIT_TF32 = 2 } ctm_prec;
 
 typedef enum { CTM_LEFT = 0, CTM_UP = 1, CTM_RIGHT = 2, CTM_DOWN = 3 } ctm_dir;
