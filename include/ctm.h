@@ -127,6 +127,17 @@ typedef struct {
                              then the fp64 sweeps on rho V0 from V0 made
                              unitary in fp64 (same result to fp64 rounding,
                              fewer fp64 sweeps); 0 = fp64 sweeps only */
+  double split_refine;    /* split contexts: once the corner-spectrum change of
+                             ctm_converge falls below this value, the rest of
+                             that call runs every large product (corners,
+                             subspace products, QR, absorption) as an
+                             exact-digit fp64-accurate tensor-core product and
+                             the absorption without the fp32 fused kernel:
+                             mixed-precision refinement of the fixed point to
+                             fp64 accuracy. The observables of such a context
+                             (ctm_expect*, ctm_rdm2, ctm_free_energy,
+                             ctm_transfer_spectrum) use the same products.
+                             0 = off */
   void* stream;           /* cudaStream_t to run on, NULL = a private stream */
 } ctm_opts;
 
@@ -143,7 +154,7 @@ enum { CTM_INIT_RANDOM = 0, CTM_INIT_FROM_A = 1 };
  * FP64, cutoff 1e-12, normalize = 1, sign_fix = 1, seed = 0,
  * svd_max_sweeps = 80, init_mode = CTM_INIT_RANDOM, recycle_sin2 = 0 (always
  * update), min_si_steps = 3, absorb_tc = 0, si_coupled = 0, warmup_rsvd = 0,
- * fp64_tc = 1, svd_presolve = 1, stream = NULL. */
+ * fp64_tc = 1, svd_presolve = 1, split_refine = 0, stream = NULL. */
 void ctm_default_opts(ctm_opts* opts);
 
 /* Create a context for an iPEPS unit cell (paper: "iPEPS", Eq. ipeps_ansatz

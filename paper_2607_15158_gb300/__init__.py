@@ -35,7 +35,8 @@ class ctm_opts(C.Structure):
                 ("seed", C.c_uint64), ("svd_max_sweeps", C.c_int), ("init_mode", C.c_int),
                 ("recycle_sin2", C.c_double), ("min_si_steps", C.c_int),
                 ("absorb_tc", C.c_int), ("si_coupled", C.c_int), ("warmup_rsvd", C.c_int),
-                ("fp64_tc", C.c_int), ("svd_presolve", C.c_int), ("stream", C.c_void_p)]
+                ("fp64_tc", C.c_int), ("svd_presolve", C.c_int), ("split_refine", C.c_double),
+                ("stream", C.c_void_p)]
 
 
 class ctm_solve_spec(C.Structure):

@@ -356,8 +356,11 @@ ctm_status ein(ctm_ctx* c, const char* spec, const Tn& A, bool cA, const Tn& B, 
     const long ldb = (p.opB == OP_N || p.opB == OP_R) ? Nn : K;
     if (c->split && (double)M * Nn * K >= SPLIT_MIN_MNK) {
       // large contraction (enlarged corners, absorption): split precision on
-      // the tensor cores
-      const ctm_status st = split_gemm(c->split, p.opA, Am, lda, p.opB, Bm, ldb, (int)M, (int)Nn,
+      // the tensor cores (exact digits during the refinement)
+      const ctm_status st =
+          c->exact ? oz_gemm(c->split, p.opA, Am, lda, p.opB, Bm, ldb, (int)M, (int)Nn, (int)K,
+                             Cm, Nn, c->stream, &c->launches)
+                   : split_gemm(c->split, p.opA, Am, lda, p.opB, Bm, ldb, (int)M, (int)Nn,
                                        (int)K, Cm, Nn, c->stream, &c->launches);
       if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
     } else {
@@ -403,7 +406,7 @@ ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
   CK(ein(c, "pm,mnuv->pnuv", tn(Cc, {chi, chi}), false, tn(Ta, {chi, chi, Dk, Db}), false, CT));
   Tn CTT = tn(c->pipe[1], {chi, Dk, Db, chi, Dk, Db});
   CK(ein(c, "tplw,pnuv->tlwnuv", tn(Tb, {chi, chi, Dk, Db}), false, CT, false, CTT));
-  if (use_fused_absorb(c->cx, c->split != nullptr, c->opts, (int)Dk, (int)Db, (int)d)) {
+  if (!c->exact && use_fused_absorb(c->cx, c->split != nullptr, c->opts, (int)Dk, (int)Db, (int)d)) {
     // A and B in one pass over the block (fp32 arithmetic in split contexts)
     CTM_CUDA_OK(absorb_ab(c->cx, c->split != nullptr, (int)chi, (int)Dk, (int)Db, (int)d, CTT.p,
                           A, B, Qout, c->num_sms, c->stream, &c->launches));
@@ -421,8 +424,12 @@ ctm_status enlarged_corner(ctm_ctx* c, int r, int i, int x, int y, void* Qout) {
 ctm_status apply_corner(ctm_ctx* c, const void* Qm, bool herm, const void* Zin, void* Zout) {
   PhaseScope ps(c, PH_PROD);
   if (c->split) {
-    const ctm_status st = split_apply(c->split, Qm, herm, Zin, Zout, c->N, c->k, c->stream,
-                                      &c->launches);
+    const int opQ = herm ? (c->cx ? OP_C : OP_T) : OP_N;
+    const ctm_status st =
+        c->exact ? oz_gemm(c->split, opQ, Qm, c->N, OP_N, Zin, c->k, c->N, c->k, c->N, Zout,
+                           c->k, c->stream, &c->launches)
+                 : split_apply(c->split, Qm, herm, Zin, Zout, c->N, c->k, c->stream,
+                               &c->launches);
     if (st != CTM_OK) return fail(c, st, split_last_error(c->split));
     return CTM_OK;
   }
@@ -455,7 +462,7 @@ ctm_status qr_inplace(ctm_ctx* c, void* Zm, void* tmp, bool split_mode) {
   // Q = Z D^-1 L^-H by the fp64 row solve or, in split contexts, as Z times
   // the explicit D^-1 L^-H.
   ++c->qr_calls;
-  const bool split = split_mode && c->split != nullptr;
+  const bool split = split_mode && c->split != nullptr && !c->exact;
   const int passes = 3;
   const bool smem_chol = chol_smem_bytes(c->cx, c->k) <= (size_t)(226 * 1024);
   for (int pass = 0; pass < passes; ++pass) {
@@ -640,7 +647,7 @@ ctm_status si_rho(ctm_ctx* c, int r, int cut, int y) {
   if (track && rounds > 0)
     CTM_CUDA_OK(cudaMemcpyAsync(Z[3], X, Nk * c->es, cudaMemcpyDeviceToDevice, c->stream));
   // fp64 QR schedule in fp64 contexts and during warm-up, split afterwards
-  const bool split_qr = c->split != nullptr && !warm;
+  const bool split_qr = c->split != nullptr && !c->exact && !warm;
   // fp64: a QR after each application of M or M^H (the span of M^H M X
   // without squaring cond(M)); split: one QR per update on the Jacobi-scaled
   // block (the products themselves carry ~1e-7 errors)
@@ -787,7 +794,7 @@ ctm_status si_finish(ctm_ctx* c, int r, int cut, int y, void* Pl, void* PrH) {
   }
   // recycled bases X v, W u: the next update re-orthonormalises them, so in
   // split contexts they run on the tensor cores
-  if (c->split) {
+  if (c->split && !c->exact) {
     ctm_status st = split_gemm(c->split, OP_N, X, k, OP_N, v, k, (int)c->N, k, k, c->Xn, k,
                                c->stream, &c->launches);
     if (st == CTM_OK)
@@ -856,7 +863,7 @@ ctm_status absorb_site(ctm_ctx* c, int r, int x, int y, int Lyf) {
   CK(ein(c, "tndD,ndDc->tc", E4, false, tn(Pl_dn, {chi, Dk, Db, chi}), false,
          tn(oC4, {chi, chi})));
   // T4'
-  if (use_fused_absorb(c->cx, c->split != nullptr, c->opts, (int)Dk, (int)Db, (int)d)) {
+  if (!c->exact && use_fused_absorb(c->cx, c->split != nullptr, c->opts, (int)Dk, (int)Db, (int)d)) {
     Tn Y1 = tn(c->pipe[0], {chi, Dk, Db, chi, Dk, Db});
     CK(ein(c, "tqlw,quvc->tlwcuv", tn(T4, {chi, chi, Dk, Db}), false,
            tn(Pl_up, {chi, Dk, Db, chi}), false, Y1));
@@ -880,12 +887,16 @@ ctm_status absorb_site(ctm_ctx* c, int r, int x, int y, int Lyf) {
 }
 
 // C = op(A) op(B) for the large products of the standard-SVD path: the
-// tensor cores in split contexts, fp64 otherwise
+// tensor cores in split contexts (exact digits during the refinement), fp64
+// otherwise
 ctm_status mm_big(ctm_ctx* c, int opA, int opB, long M, long Nn, long K, const void* A, long lda,
                   const void* B, long ldb, void* Cm, long ldc) {
   if (c->split) {
-    const ctm_status st = split_gemm(c->split, opA, A, lda, opB, B, ldb, (int)M, (int)Nn, (int)K,
-                                     Cm, ldc, c->stream, &c->launches);
+    const ctm_status st =
+        c->exact ? oz_gemm(c->split, opA, A, lda, opB, B, ldb, (int)M, (int)Nn, (int)K, Cm, ldc,
+                           c->stream, &c->launches)
+                 : split_gemm(c->split, opA, A, lda, opB, B, ldb, (int)M, (int)Nn, (int)K, Cm,
+                              ldc, c->stream, &c->launches);
     return st == CTM_OK ? CTM_OK : fail(c, st, split_last_error(c->split));
   }
   return mm_small(c, opA, opB, M, Nn, K, A, lda, B, ldb, Cm, ldc);
@@ -966,7 +977,7 @@ ctm_status move_impl(ctm_ctx* c, int r) {
         for (int i = 0; i < 4; ++i)
           if (!(pre && (i == 1 || i == 2))) CK(enlarged_corner(c, r, i, x, y, c->Q[i]));
       }
-      if (c->split) {
+      if (c->split && !c->exact) {
         PhaseScope ps(c, PH_SLICE);
         const ctm_status st = split_prepare_corners(c->split, c->Q, c->N, pre ? 0x9u : 0xFu,
                                                     c->stream, &c->launches);
@@ -992,7 +1003,7 @@ ctm_status move_impl(ctm_ctx* c, int r) {
             CK(enlarged_corner(c, r, 1, x + 1, y, c->Q[1]));
             CK(enlarged_corner(c, r, 2, x + 1, y, c->Q[2]));
           }
-          if (c->split) {
+          if (c->split && !c->exact) {
             PhaseScope ps(c, PH_SLICE);
             const ctm_status st =
                 split_prepare_corners(c->split, c->Q, c->N, 0x6u, c->stream, &c->launches);
@@ -1238,12 +1249,12 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
       !(c->opts.recycle_sin2 >= 0.0) ||
       (c->opts.init_mode != CTM_INIT_RANDOM && c->opts.init_mode != CTM_INIT_FROM_A) ||
       (c->opts.svd_presolve != 0 && c->opts.svd_presolve != 1) ||
-      (c->opts.fp64_tc != 0 && c->opts.fp64_tc != 1)) {
+      (c->opts.fp64_tc != 0 && c->opts.fp64_tc != 1) || !(c->opts.split_refine >= 0.0)) {
     delete c;
     g_cur = nullptr;
     return fail(nullptr, CTM_EINVAL,
                 "p, si_rounds, warm-up counts and min_si_steps must be >= 0, svd_max_sweeps >= 1, "
-                "recycle_sin2 >= 0, init_mode, fp64_tc and svd_presolve 0 or 1");
+                "recycle_sin2, split_refine >= 0, init_mode, fp64_tc and svd_presolve 0 or 1");
   }
   c->N = chi * Dk * Db;
   c->k = std::min(chi + c->opts.p, c->N);
@@ -1432,9 +1443,10 @@ ctm_status create(ctm_ctx** out, int Lx, int Ly, int d, int Dk, int Db, int chi,
           cudaEventCreateWithFlags(&M.ev, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(c, CTM_ECUDA, "lane stream creation failed"));
       // a lane only builds corners and runs the SI round: its pipelines hold
-      // N^2 elements (d N^2 for the unfused absorption), not the d^2 N^2 of
-      // the two-site observables of lane 0
-      const bool fused = use_fused_absorb(cx, c->opts.prec != CTM_PREC_FP64, c->opts,
+      // N^2 elements (d N^2 for the unfused absorption, which the refinement
+      // uses), not the d^2 N^2 of the two-site observables of lane 0
+      const bool fused = !(c->opts.split_refine > 0.0) &&
+                         use_fused_absorb(cx, c->opts.prec != CTM_PREC_FP64, c->opts,
                                           (int)Dk, (int)Db, d);
       const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
       M.scratch_bytes = 2 * laneT * es + ((size_t)64 << 20);
@@ -1628,6 +1640,7 @@ void ctm_default_opts(ctm_opts* o) {
   o->warmup_rsvd = 0;
   o->fp64_tc = 1;
   o->svd_presolve = 1;
+  o->split_refine = 0.0;
   o->stream = nullptr;
 }
 
@@ -1715,10 +1728,18 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
     b += 2 * N * Kp * sb;                          // operand slices of general products
     b += split_partial_splits(N, cx) * N * ((cx ? 2 : 1) * k + 160) * 4;   // split-K partials
   }
+  // refinement: eight 2-byte digits per real component of the operands
+  // (complex B operands as 2 x 2 real blocks, K padded to at most twice) and
+  // fp32-pair partials, for operands of up to d N^2 elements on the lanes and
+  // d^2 N^2 for the two-site observables of lane 0
+  const bool refine = o->prec != CTM_PREC_FP64 && o->split_refine > 0.0;
+  const size_t oz_refine = refine ? 12 * (size_t)d * NN * es : 0;
+  b += (size_t)d * oz_refine;
   if (o->method == CTM_PROJ_SVD) b += 3 * NN * es + 2 * N * chi * es + (size_t)64 * N * es;
   if (o->method == CTM_PROJ_SI) {
     // lanes 1 .. nl-1: corners, pipes, scratch, N x k blocks, QR work, split state
-    const bool fused = use_fused_absorb(cx, o->prec != CTM_PREC_FP64, *o, Dk, Db, d);
+    const bool fused =
+        !(o->split_refine > 0.0) && use_fused_absorb(cx, o->prec != CTM_PREC_FP64, *o, Dk, Db, d);
     const size_t laneT = (size_t)(fused ? 1 : d) * NN + 64;
     size_t lane = 4 * NN * es + 4 * laneT * es + ((size_t)64 << 20) + 4 * N * k * es +
                   2 * k * k * es + 12 * k + chol_coop_work_bytes((int)k, 1) +
@@ -1728,6 +1749,7 @@ static size_t footprint_bytes(int Lx, int Ly, int d, int Dk, int Db, int chi, bo
       const size_t sb = o->prec == CTM_PREC_SPLIT_TF32 ? 8 : 6;
       lane += 10 * N * Kp * sb + split_partial_splits(N, cx) * N * ((cx ? 2 : 1) * k + 160) * 4;
     }
+    lane += oz_refine;
     b += (size_t)(lanes_for(Lx, Ly) - 1) * lane;
   }
   return b + b / 20 + ((size_t)64 << 20);
@@ -1862,6 +1884,17 @@ ctm_status ctm_move(ctm_ctx* c, ctm_dir dir) {
   return CTM_OK;
 }
 
+// Exact-digit products (c->exact) for the lifetime of the scope. Observables
+// of a context with the refinement (split_refine > 0) use them too: the
+// environment they contract is fp64-accurate, and split products would add
+// their ~1e-7 again.
+struct ExactScope {
+  ctm_ctx* c;
+  ExactScope(ctm_ctx* cc, bool on) : c(cc) { c->exact = on; }
+  ~ExactScope() { c->exact = false; }
+};
+bool refine_on(const ctm_ctx* c) { return c->split != nullptr && c->opts.split_refine > 0.0; }
+
 ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, double* delta_out) {
   if (!c) return fail(c, CTM_EINVAL, "ctx is NULL");
   if (max_iter < 0) return fail(c, CTM_EINVAL, "max_iter must be >= 0");
@@ -1876,9 +1909,13 @@ ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, do
     c->spectra_init = true;
     c->spectra_fresh = true;
   }
+  // refinement (split_refine): exact-digit products once the spectra have
+  // settled to that level, for the rest of this call only
+  ExactScope xs(c, false);
   double delta = INFINITY;
   int it = 0;
   while (it < max_iter) {
+    if (c->split && c->opts.split_refine > 0.0 && delta < c->opts.split_refine) c->exact = true;
     for (int r = 0; r < 4; ++r) CK(move_impl(c, r));
     ++it;
     CK(corner_spectra(c, c->spec_new));
@@ -1946,6 +1983,7 @@ ctm_status ctm_rdm2(ctm_ctx* c, int x, int y, int dir, double* rho_out) {
   if (!c || !rho_out) return fail(c, CTM_EINVAL, "NULL argument");
   if (!valid_site(c, x, y) || (dir != 0 && dir != 1)) return fail(c, CTM_EINVAL, "bad site or dir");
   Guard gd(c);
+  ExactScope xs(c, refine_on(c));
   const int d2 = c->d * c->d;
   CK(rho2_device(c, x, y, dir, nullptr, nullptr, c->rho2));
   std::vector<double> h((size_t)d2 * d2 * (c->cx ? 2 : 1));
@@ -1969,6 +2007,7 @@ ctm_status ctm_expect(ctm_ctx* c, const void* op, int x, int y, int dir, double 
   if (!c || !op || !out) return fail(c, CTM_EINVAL, "NULL argument");
   if (!valid_site(c, x, y) || (dir != 0 && dir != 1)) return fail(c, CTM_EINVAL, "bad site or dir");
   Guard gd(c);
+  ExactScope xs(c, refine_on(c));
   const int d2 = c->d * c->d;
   CTM_CUDA_OK(cudaMemcpyAsync(c->op, op, (size_t)d2 * d2 * c->es, cudaMemcpyHostToDevice, c->stream));
   CK(rho2_device(c, x, y, dir, nullptr, nullptr, c->rho2));
@@ -1987,6 +2026,7 @@ ctm_status ctm_expect_bond(ctm_ctx* c, const void* imp1, const void* imp2, int x
   if (!c || !imp1 || !imp2 || !out) return fail(c, CTM_EINVAL, "NULL argument");
   if (!valid_site(c, x, y) || (dir != 0 && dir != 1)) return fail(c, CTM_EINVAL, "bad site or dir");
   Guard gd(c);
+  ExactScope xs(c, refine_on(c));
   const int d2 = c->d * c->d;
   // identity operator: the traces of the two density matrices
   std::vector<double> eye((size_t)d2 * d2 * (c->cx ? 2 : 1), 0.0);
@@ -2009,6 +2049,7 @@ ctm_status ctm_expect_site(ctm_ctx* c, const void* imp, int x, int y, double out
   if (!c || !imp || !out) return fail(c, CTM_EINVAL, "NULL argument");
   if (!valid_site(c, x, y)) return fail(c, CTM_EINVAL, "bad site");
   Guard gd(c);
+  ExactScope xs(c, refine_on(c));
   const size_t nk = elems_ket(c);
   CTM_CUDA_OK(cudaMemcpyAsync(c->imp[0], imp, nk * c->es, cudaMemcpyHostToDevice, c->stream));
   const int site = y * c->Lx + x;
@@ -2028,6 +2069,7 @@ ctm_status ctm_free_energy(ctm_ctx* c, double* ln_kappa) {
   if (!c || !ln_kappa) return fail(c, CTM_EINVAL, "NULL argument");
   if (c->S != 1) return fail(c, CTM_EINVAL, "free energy per site needs a 1x1 cell");
   Guard gd(c);
+  ExactScope xs(c, refine_on(c));
   const long chi = c->chi, Dk = c->Dk, Db = c->Db;
   CK(one_site(c, 0, 0, KETp(c, 0, 0), false, c->dscal + 24));
   auto Ct = [&](int i) { return tn(Cp(c, i, 0), {chi, chi}); };
@@ -2124,6 +2166,7 @@ ctm_status ctm_transfer_spectrum(ctm_ctx* c, int dir, int row, int nvals, double
   if (nvals < 2 || nvals > 24 || nvals > n)
     return fail(c, CTM_EINVAL, "nvals must be in 2 .. min(24, chi^2)");
   Guard gd(c);
+  ExactScope xs(c, refine_on(c));
   use_lane(c, 0);
   // subspace iteration with m vectors, Rayleigh-Ritz every 5 applications
   const int m = (int)std::min<long>(n, std::max(nvals + 4, 8));

@@ -125,6 +125,8 @@ struct ctm_ctx {
   bool spectra_fresh = false;
   // split-precision state
   SplitCtx* split = nullptr;
+  // refinement (opts.split_refine): every large product exact-digit fp64-accurate
+  bool exact = false;
   // lanes: the cuts of a column are independent until their small SVDs, so
   // they run concurrently, each on its own stream with its own corners and
   // workspace; use_lane() points the fields above at lane i

@@ -44,13 +44,15 @@ def test_default_opts_without_gpu(lib):
     assert o.svd_rel_cutoff == 1e-12
     assert (o.svd_max_sweeps, o.init_mode, o.recycle_sin2, o.min_si_steps) == (80, 0, 0.0, 3)
     assert (o.absorb_tc, o.si_coupled, o.warmup_rsvd, o.svd_presolve, o.fp64_tc) == (0, 0, 0, 1, 1)
+    assert o.split_refine == 0.0
 
 
 def test_bad_options_are_rejected_before_device_work(lib):
     pkg.load()
     A = (ctypes.c_void_p * 1)(ctypes.c_void_p(16))
     for kw in (dict(svd_max_sweeps=0), dict(init_mode=2), dict(recycle_sin2=-1.0),
-               dict(min_si_steps=-1), dict(svd_presolve=2), dict(fp64_tc=-1)):
+               dict(min_si_steps=-1), dict(svd_presolve=2), dict(fp64_tc=-1),
+               dict(split_refine=-1e-6), dict(split_refine=float("nan"))):
         o = pkg.ctm_default_opts(**kw)
         ptr = ctypes.c_void_p()
         st = pkg._lib.ctm_init(ctypes.byref(ptr), 1, 1, A, None, 0, 2, 2, 4, ctypes.byref(o))
@@ -76,6 +78,10 @@ def test_footprint_is_host_arithmetic(lib):
     assert pkg._lib.ctm_footprint(1, 1, 2, 0, 8, 0, None, ctypes.byref(n)) == pkg.CTM_EINVAL
     # cfg3 (3x3, complex D = 6, chi = 144, three lanes) fits several times in the 280 GB
     assert pkg.ctm_footprint(3, 3, 2, 6, 144, True, split) < 60e9
+    # the refinement adds its exact-digit operands and the unfused lane pipelines
+    refine = pkg.ctm_default_opts(prec=pkg.CTM_PREC_SPLIT_BF16, split_refine=1e-5)
+    fr = pkg.ctm_footprint(3, 3, 2, 6, 144, True, refine)
+    assert pkg.ctm_footprint(3, 3, 2, 6, 144, True, split) < fr < 120e9
 
 
 def test_noalloc_rejects_oversize_before_device_work(lib):
