@@ -137,7 +137,9 @@ typedef struct {
                              fp64 accuracy. The observables of such a context
                              (ctm_expect*, ctm_rdm2, ctm_free_energy,
                              ctm_transfer_spectrum) use the same products.
-                             0 = off */
+                             +inf: every move (ctm_move, ctm_converge) runs
+                             them from the start, an fp64-accurate mode on
+                             the tensor cores. 0 = off */
   void* stream;           /* cudaStream_t to run on, NULL = a private stream */
 } ctm_opts;
 

@@ -1867,10 +1867,24 @@ ctm_status ctm_dims(const ctm_ctx* c, int* N, int* k) {
   return CTM_OK;
 }
 
+// Exact-digit products (c->exact) for the lifetime of the scope. Observables
+// of a context with the refinement (split_refine > 0) use them too: the
+// environment they contract is fp64-accurate, and split products would add
+// their ~1e-7 again. split_refine = +inf makes every move exact from the
+// start.
+struct ExactScope {
+  ctm_ctx* c;
+  ExactScope(ctm_ctx* cc, bool on) : c(cc) { c->exact = on; }
+  ~ExactScope() { c->exact = false; }
+};
+bool refine_on(const ctm_ctx* c) { return c->split != nullptr && c->opts.split_refine > 0.0; }
+bool exact_always(const ctm_ctx* c) { return refine_on(c) && std::isinf(c->opts.split_refine); }
+
 ctm_status ctm_move(ctm_ctx* c, ctm_dir dir) {
   if (!c) return fail(c, CTM_EINVAL, "ctx is NULL");
   if (dir < 0 || dir > 3) return fail(c, CTM_EINVAL, "direction must be 0..3");
   Guard gd(c);
+  ExactScope xs(c, exact_always(c));
   const long l0 = c->launches;
   CTM_CUDA_OK(cudaEventRecord(c->ev0, c->stream));
   CK(move_impl(c, (int)dir));
@@ -1883,17 +1897,6 @@ ctm_status ctm_move(ctm_ctx* c, ctm_dir dir) {
   c->last_launches = c->launches - l0;
   return CTM_OK;
 }
-
-// Exact-digit products (c->exact) for the lifetime of the scope. Observables
-// of a context with the refinement (split_refine > 0) use them too: the
-// environment they contract is fp64-accurate, and split products would add
-// their ~1e-7 again.
-struct ExactScope {
-  ctm_ctx* c;
-  ExactScope(ctm_ctx* cc, bool on) : c(cc) { c->exact = on; }
-  ~ExactScope() { c->exact = false; }
-};
-bool refine_on(const ctm_ctx* c) { return c->split != nullptr && c->opts.split_refine > 0.0; }
 
 ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, double* delta_out) {
   if (!c) return fail(c, CTM_EINVAL, "ctx is NULL");
@@ -1911,7 +1914,7 @@ ctm_status ctm_converge(ctm_ctx* c, double tol, int max_iter, int* iters_out, do
   }
   // refinement (split_refine): exact-digit products once the spectra have
   // settled to that level, for the rest of this call only
-  ExactScope xs(c, false);
+  ExactScope xs(c, exact_always(c));
   double delta = INFINITY;
   int it = 0;
   while (it < max_iter) {

@@ -21,7 +21,7 @@ TOL_SPLIT = 1e-6          # converged unit-normalised corner spectra, split vs f
 TOL_SPLIT_ENERGY = 1e-7   # converged bond energies, split vs fp64
 
 
-def _ctx(case, prec):
+def _ctx(case, prec, **kw):
     Lx, Ly, d, D, chi, p, cplx, rounds = case
     A = S.ipeps_tensors(Lx, Ly, d, D, complex_=cplx, seed=0)
     Cs, Ts = S.initial_env(Lx, Ly, chi, D, D, complex_=cplx, seed=1)
@@ -29,7 +29,7 @@ def _ctx(case, prec):
     k = min(chi + p, N)
     X0, W0 = S.initial_rangefinders(Lx, Ly, N, k, complex_=cplx, seed=2)
     ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx,
-                       opts=pkg.ctm_default_opts(p=p, si_rounds=rounds, prec=prec))
+                       opts=pkg.ctm_default_opts(p=p, si_rounds=rounds, prec=prec, **kw))
     ctx.ctm_set_env(Cs, Ts)
     ctx.ctm_set_rangefinders(X0, W0)
     return ctx, (A, Cs, Ts, X0, W0)
@@ -123,9 +123,10 @@ def test_converged_split_large_D_matches_oracle(case):
 
 
 @pytest.mark.parametrize("case", [
-    # Lx, Ly, d, D, chi, p, complex, rounds, bond decay
-    (2, 2, 2, 6, 8, 5, True, 1, 0.5),    # fused fp32 absorption until the switch
-    (1, 1, 2, 2, 8, 5, False, 2, 1.0),   # real
+    # Lx, Ly, d, D, chi, p, complex, rounds, bond decay, split_refine
+    (2, 2, 2, 6, 8, 5, True, 1, 0.5, 1e-5),        # fused fp32 absorption until the switch
+    (1, 1, 2, 2, 8, 5, False, 2, 1.0, 1e-5),       # real
+    (2, 2, 2, 6, 8, 5, True, 1, 0.5, float("inf")),  # exact-digit products from the start
 ])
 def test_split_refinement_reaches_fp64_accuracy(case):
     """Split precision with the refinement (split_refine = 1e-5): once the
@@ -136,9 +137,9 @@ def test_split_refinement_reaches_fp64_accuracy(case):
     tolerance, far inside the ~4e-7 (spectra) and ~5e-8 (energies) of the
     plain split iteration; the energies are evaluated with the same exact
     products. The measured differences are printed."""
-    Lx, Ly, d, D, chi, p, cplx, rounds, q = case
+    Lx, Ly, d, D, chi, p, cplx, rounds, q, refine = case
     ctx, ref = make_pair(Lx, Ly, d, D, chi, p, cplx, rounds, decay=q,
-                         prec=pkg.CTM_PREC_SPLIT_BF16, split_refine=1e-5)
+                         prec=pkg.CTM_PREC_SPLIT_BF16, split_refine=refine)
     it, delta, ok = ctx.ctm_converge(1e-11, 250)
     it_ref, d_ref = ref.converge(1e-11, 250)
     assert ok and d_ref < 1e-11
@@ -147,13 +148,39 @@ def test_split_refinement_reaches_fp64_accuracy(case):
              for lab in range(4) for y in range(Ly) for x in range(Lx))
     ee = max(abs(ctx.ctm_expect(HEIS, x, y, dr) - ref.expect2(HEIS, x, y, dr))
              for y in range(Ly) for x in range(Lx) for dr in (0, 1))
-    print(f"refined split D={D}: spectra {es:.2e}, energies {ee:.2e}, it {it} (oracle {it_ref})")
-    # measured: spectra 3.5e-13 / 1.8e-12, energies 2.1e-14 / 3.3e-14 (D = 6 / 2),
-    # in 19 / 53 iterations (the oracle: 19 / 61); the FP64 path's bound
+    print(f"refined split D={D} at {refine:g}: spectra {es:.2e}, energies {ee:.2e}, "
+          f"it {it} (oracle {it_ref})")
+    # measured: spectra 3.5e-13 / 1.8e-12 / 1.1e-14, energies 2.1e-14 / 3.3e-14 /
+    # 1.3e-15 (the three cases), in 19 / 53 / 19 iterations (the oracle: 19 / 61 /
+    # 19); the FP64 path's bound
     assert es < 1e-10 and ee < 1e-10
     # a later call without the switch runs split products again
     ctx.ctm_move(0)
     ctx.ctm_free()
+
+
+@pytest.mark.parametrize("case", [
+    (2, 1, 2, 3, 10, 5, True, 1),        # N = 90 complex: ragged tiles, two cuts on lanes
+    (1, 1, 2, 4, 12, 5, False, 1),       # real, N = 192
+])
+def test_exact_digit_moves_track_fp64(case):
+    """split_refine = +inf: every ctm_move of a split context runs the
+    exact-digit fp64-accurate products. Four moves from the same inputs agree
+    with the FP64 context far inside the 1e-5 of split-precision moves; the
+    measured difference is printed."""
+    a, _ = _ctx(case, pkg.CTM_PREC_FP64)
+    b, _ = _ctx(case, pkg.CTM_PREC_SPLIT_BF16, split_refine=float("inf"))
+    for r in range(4):
+        a.ctm_move(r)
+        b.ctm_move(r)
+    err = float(np.abs(_spectra(a) - _spectra(b)).max())
+    print(f"exact-digit moves vs fp64: spectra {err:.2e}")
+    # measured: 9.0e-14 (complex N = 90), 2.4e-14 (real N = 192)
+    assert err < 1e-10
+    Pl, PrH = b.ctm_get_projectors(3, 0, 0)
+    assert np.abs(PrH.conj().T @ Pl - np.eye(Pl.shape[1])).max() < 1e-9
+    a.ctm_free()
+    b.ctm_free()
 
 
 @pytest.mark.parametrize("case", [
