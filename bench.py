@@ -59,6 +59,9 @@ def parse():
                     help="small SVDs in fp64 sweeps only (no fp32 one-sided Jacobi first)")
     ap.add_argument("--no-fp64-tc", action="store_true",
                     help="split modes: Grams, rho and projectors as fp64 GEMMs on the CUDA cores")
+    ap.add_argument("--exact", action="store_true",
+                    help="split modes: every product an exact-digit fp64-accurate product on "
+                         "the tensor cores from the start (split_refine = +inf)")
     ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the plain-FP64 and standard-SVD comparison timings and the "
                          "split-error measurement")
@@ -266,6 +269,7 @@ def run_ours(args, rank, world, local_rank):
                                 warmup_rounds=WARM_ROUNDS, prec=prec, method=method,
                                 svd_presolve=0 if args.no_svd_presolve else 1,
                                 fp64_tc=0 if args.no_fp64_tc else 1,
+                                split_refine=float("inf") if args.exact else 0.0,
                                 stream=stream.cuda_stream)
     ctx = pkg.ctm_init(Lx, Ly, A, d, D, chi, cplx=cplx, opts=opts)
     ctx.ctm_set_env(Cs, Ts)
@@ -386,10 +390,13 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "c128" if cplx else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "cell": f"{Lx}x{Ly}", "d": d, "D": D, "chi": chi,
                    "p": p, "N": N, "k": k, "si_rounds": w["si_rounds"],
-                   "precision": {"split": "split-bf16x3 (6 slice products; s0 t0 and the rest "
-                                          "in separate fp32 accumulators), fp64 QR/SVD",
-                                 "tf32": "split-3xTF32 (3 slice products), fp64 QR/SVD",
-                                 "fp64": "fp64"}[args.prec],
+                   "precision": ("exact-digit fp64-accurate products on the tensor cores "
+                                 "(8 bf16 digits, 36 digit products), fp64 QR/SVD"
+                                 if args.exact and args.prec != "fp64" else
+                                 {"split": "split-bf16x3 (6 slice products; s0 t0 and the rest "
+                                           "in separate fp32 accumulators), fp64 QR/SVD",
+                                  "tf32": "split-3xTF32 (3 slice products), fp64 QR/SVD",
+                                  "fp64": "fp64"}[args.prec]),
                    "projectors": "subspace iteration" if args.method == "si"
                    else "standard truncated SVD (dense gesvd)",
                    "small_svd": "fp64 one-sided Jacobi" if args.no_svd_presolve
